@@ -1,0 +1,680 @@
+/*
+ * CPU oracle for the BANG search path (arXiv 2401.11324).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This is a plain, slow, obviously-correct
+ * restatement of what the search path computes, one query at a time, written
+ * from the paper.  Only the test suite, the smoke check and the CPU-baseline
+ * leg of the benchmark may load it.  The product path never links, imports or
+ * calls it, and it shares no code, header, table or constant generator with
+ * the CUDA implementation.
+ *
+ * Precision: the graph search decides integers (which node is expanded next)
+ * from floating-point comparisons, so those decisions are taken in FP32, the
+ * precision of the GPU kernel, with the summation orders stated below.  Ground
+ * truth (brute force) is FP64, or exact integers for integer data.
+ *
+ * Build with -ffp-contract=off: every fused multiply-add below is an explicit
+ * fmaf(); nothing else may be contracted.
+ *
+ * Functions, and the passage of the paper each one follows:
+ *   orc_chunk_offsets        §4 (PQ splits d into m contiguous subspaces)
+ *   orc_pq_train             §4 (independent k-means per subspace, 256 centroids)
+ *   orc_pq_encode            §4 (a point is the list of its per-subspace cluster ids)
+ *   orc_medoid               §6.3 (the search starts from the medoid)
+ *   orc_robust_prune         §2.2 (Vamana RobustPrune with the pruning parameter)
+ *   orc_vamana_build         §2.2, §6.3 (R, L, pruning parameter); parity unpinned
+ *                            beyond invariants: the paper takes the graph from
+ *                            DiskANN and does not state its construction
+ *   orc_adc_table_f32        §4.1 (PQDistTable: squared distance of each query
+ *                            sub-vector to each centroid)
+ *   orc_adc_dist_f32         §4.4 (asymmetric distance = sum of table entries)
+ *   orc_fnv1a32/_fnv1a64     §4.3, §6.3 (two FNV-1a hash functions)
+ *   orc_bloom_*              §4.3 (per-query Bloom filter of visited nodes)
+ *   orc_exact_dist           §4.8 (exact distance used by the re-rank)
+ *   orc_search               Alg. 1, Alg. 2, §4.3-§4.8
+ *   orc_bruteforce_knn       §6.3 (ground truth S for k-recall@k)
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#include "bang_oracle.h"
+
+#define ORC_NONE 0xFFFFFFFFu
+
+/* ---------------------------------------------------------------------- */
+/* element access                                                          */
+/* ---------------------------------------------------------------------- */
+
+static float elem_f(const void *v, int dtype, uint64_t i)
+{
+    if (dtype == ORC_U8) return (float)((const uint8_t *)v)[i];
+    if (dtype == ORC_I8) return (float)((const int8_t *)v)[i];
+    return ((const float *)v)[i];
+}
+
+static int32_t elem_i(const void *v, int dtype, uint64_t i)
+{
+    if (dtype == ORC_U8) return (int32_t)((const uint8_t *)v)[i];
+    return (int32_t)((const int8_t *)v)[i];
+}
+
+/* ---------------------------------------------------------------------- */
+/* PQ layout (§4): d dimensions split into M contiguous subspaces.  When M  */
+/* does not divide d (the paper's m=74 with d=128), the first d%M           */
+/* subspaces take one extra dimension.                                      */
+/* ---------------------------------------------------------------------- */
+
+void orc_chunk_offsets(uint32_t d, uint32_t M, uint32_t *off)
+{
+    uint32_t base = d / M, extra = d % M, s;
+    off[0] = 0;
+    for (s = 0; s < M; s++) off[s + 1] = off[s] + base + (s < extra ? 1u : 0u);
+}
+
+/* Codebook layout: subspace s owns the 256 * dsub_s floats starting at
+ * 256 * off[s]; centroid c of subspace s starts at 256*off[s] + c*dsub_s. */
+static const float *centroid(const float *cb, const uint32_t *off, uint32_t s, uint32_t c)
+{
+    uint32_t ds = off[s + 1] - off[s];
+    return cb + (size_t)256 * off[s] + (size_t)c * ds;
+}
+
+/* ---------------------------------------------------------------------- */
+/* PQ training (§4): k-means with 256 centroids in every subspace.          */
+/* The seeded choices (training sample, initial centroids) are inputs.     */
+/* Lloyd iterations with FP64 sums; an empty cluster keeps its centroid;   */
+/* assignment ties go to the smaller centroid id.  obj_trace (optional,    */
+/* M*iters entries) receives, for every subspace and iteration, the       */
+/* objective sum_i min_c ||x_i - c||^2 of the assignment step.            */
+/* ---------------------------------------------------------------------- */
+
+int orc_pq_train(const float *X, uint32_t d, uint32_t M, const uint32_t *off,
+                 const uint64_t *sample, uint64_t ns, const uint64_t *init,
+                 uint32_t iters, float *codebook, double *obj_trace)
+{
+    uint32_t s, it, c, j;
+    uint64_t i;
+    for (s = 0; s < M; s++) {
+        uint32_t o = off[s], ds = off[s + 1] - off[s];
+        double *cent = (double *)malloc(sizeof(double) * 256 * ds);
+        double *sums = (double *)malloc(sizeof(double) * 256 * ds);
+        uint64_t *cnt = (uint64_t *)malloc(sizeof(uint64_t) * 256);
+        if (!cent || !sums || !cnt) { free(cent); free(sums); free(cnt); return -1; }
+        for (c = 0; c < 256; c++)
+            for (j = 0; j < ds; j++)
+                cent[c * ds + j] = (double)X[init[c] * (uint64_t)d + o + j];
+        for (it = 0; it < iters; it++) {
+            double obj = 0.0;
+            memset(sums, 0, sizeof(double) * 256 * ds);
+            memset(cnt, 0, sizeof(uint64_t) * 256);
+            for (i = 0; i < ns; i++) {
+                const float *x = X + sample[i] * (uint64_t)d + o;
+                double best = INFINITY;
+                uint32_t bc = 0;
+                for (c = 0; c < 256; c++) {
+                    double acc = 0.0;
+                    for (j = 0; j < ds; j++) {
+                        double t = (double)x[j] - cent[c * ds + j];
+                        acc += t * t;
+                    }
+                    if (acc < best) { best = acc; bc = c; }
+                }
+                obj += best;
+                cnt[bc]++;
+                for (j = 0; j < ds; j++) sums[bc * ds + j] += (double)x[j];
+            }
+            if (obj_trace) obj_trace[(size_t)s * iters + it] = obj;
+            for (c = 0; c < 256; c++)
+                if (cnt[c])
+                    for (j = 0; j < ds; j++) cent[c * ds + j] = sums[c * ds + j] / (double)cnt[c];
+        }
+        for (c = 0; c < 256; c++)
+            for (j = 0; j < ds; j++)
+                codebook[(size_t)256 * o + (size_t)c * ds + j] = (float)cent[c * ds + j];
+        free(cent); free(sums); free(cnt);
+        init += 256;
+    }
+    return 0;
+}
+
+/* PQ encoding (§4): code[i][s] = argmin_c ||x_s - C[s][c]||^2 in FP64,
+ * ties to the smaller c. */
+void orc_pq_encode(const void *X, int dtype, uint64_t n, uint32_t d, uint32_t M,
+                   const uint32_t *off, const float *codebook, uint8_t *codes)
+{
+    uint64_t i;
+    uint32_t s, c, j;
+    for (i = 0; i < n; i++) {
+        for (s = 0; s < M; s++) {
+            uint32_t o = off[s], ds = off[s + 1] - off[s];
+            double best = INFINITY;
+            uint32_t bc = 0;
+            for (c = 0; c < 256; c++) {
+                const float *cc = centroid(codebook, off, s, c);
+                double acc = 0.0;
+                for (j = 0; j < ds; j++) {
+                    double t = (double)elem_f(X, dtype, i * d + o + j) - (double)cc[j];
+                    acc += t * t;
+                }
+                if (acc < best) { best = acc; bc = c; }
+            }
+            codes[i * M + s] = (uint8_t)bc;
+        }
+    }
+}
+
+/* Medoid (§6.3: the entry point fixed at construction): the point nearest,
+ * in FP64, to the mean of all points; ties to the smaller id. */
+uint32_t orc_medoid(const void *X, int dtype, uint64_t n, uint32_t d)
+{
+    double *mean = (double *)calloc(d, sizeof(double));
+    double best = INFINITY;
+    uint32_t bi = 0, j;
+    uint64_t i;
+    if (!mean) return ORC_NONE;
+    for (i = 0; i < n; i++)
+        for (j = 0; j < d; j++) mean[j] += (double)elem_f(X, dtype, i * d + j);
+    for (j = 0; j < d; j++) mean[j] /= (double)n;
+    for (i = 0; i < n; i++) {
+        double acc = 0.0;
+        for (j = 0; j < d; j++) {
+            double t = (double)elem_f(X, dtype, i * d + j) - mean[j];
+            acc += t * t;
+        }
+        if (acc < best) { best = acc; bi = (uint32_t)i; }
+    }
+    free(mean);
+    return bi;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Vamana construction (§2.2; parameters in §6.3).                          */
+/* ---------------------------------------------------------------------- */
+
+static double sqdist_f64(const float *X, uint32_t d, uint64_t a, const float *y)
+{
+    const float *x = X + a * d;
+    double acc = 0.0;
+    uint32_t j;
+    for (j = 0; j < d; j++) {
+        double t = (double)x[j] - (double)y[j];
+        acc += t * t;
+    }
+    return acc;
+}
+
+typedef struct { double dist; uint32_t id; } orc_dpair;
+
+static int dpair_cmp(const void *pa, const void *pb)
+{
+    const orc_dpair *a = (const orc_dpair *)pa, *b = (const orc_dpair *)pb;
+    if (a->dist < b->dist) return -1;
+    if (a->dist > b->dist) return 1;
+    return (a->id < b->id) ? -1 : (a->id > b->id);
+}
+
+/* RobustPrune(p, V, alpha, R): repeatedly keep the nearest remaining
+ * candidate p* and drop every candidate p' with alpha*d(p*,p') <= d(p,p')
+ * (Euclidean distances, compared here as alpha^2 * squared distances).
+ * cand may contain p itself and duplicates; both are ignored.  Returns the
+ * number of kept neighbours, written to out[0..R). */
+uint32_t orc_robust_prune(const float *X, uint32_t d, uint32_t p, const uint32_t *cand,
+                          uint32_t nc, float alpha, uint32_t R, uint32_t *out)
+{
+    orc_dpair *v = (orc_dpair *)malloc(sizeof(orc_dpair) * (nc ? nc : 1));
+    unsigned char *alive = (unsigned char *)malloc(nc ? nc : 1);
+    uint32_t nv = 0, i, j, nout = 0;
+    double a2 = (double)alpha * (double)alpha;
+    const float *xp = X + (uint64_t)p * d;
+    for (i = 0; i < nc; i++) {
+        uint32_t c = cand[i], dup = 0;
+        if (c == p || c == ORC_NONE) continue;
+        for (j = 0; j < nv; j++) if (v[j].id == c) { dup = 1; break; }
+        if (dup) continue;
+        v[nv].id = c;
+        v[nv].dist = sqdist_f64(X, d, c, xp);
+        nv++;
+    }
+    qsort(v, nv, sizeof(orc_dpair), dpair_cmp);
+    for (i = 0; i < nv; i++) alive[i] = 1;
+    for (i = 0; i < nv && nout < R; i++) {
+        if (!alive[i]) continue;
+        out[nout++] = v[i].id;
+        for (j = i + 1; j < nv; j++) {
+            if (!alive[j]) continue;
+            if (a2 * sqdist_f64(X, d, v[j].id, X + (uint64_t)v[i].id * d) <= v[j].dist) alive[j] = 0;
+        }
+    }
+    free(v); free(alive);
+    return nout;
+}
+
+/* GreedySearch used during construction (exact FP64 distances, worklist of
+ * Lb entries, every node inserted at most once).  Writes the expanded nodes
+ * to V and returns their number. */
+static uint32_t build_greedy(const float *X, uint32_t d, const uint32_t *adj, uint32_t R,
+                             uint32_t s, const float *xq, uint32_t Lb, unsigned char *seen,
+                             uint32_t *touched, uint32_t *ntouched, orc_dpair *Lst,
+                             unsigned char *exp, uint32_t *V, uint32_t vcap)
+{
+    uint32_t nl = 1, nv = 0, i, r;
+    Lst[0].id = s; Lst[0].dist = sqdist_f64(X, d, s, xq); exp[0] = 0;
+    seen[s] = 1; touched[(*ntouched)++] = s;
+    for (;;) {
+        uint32_t u = ORC_NONE;
+        for (i = 0; i < nl; i++) if (!exp[i]) { u = i; break; }
+        if (u == ORC_NONE || nv >= vcap) break;
+        exp[u] = 1;
+        {
+            uint32_t p = Lst[u].id;
+            V[nv++] = p;
+            for (r = 0; r < R; r++) {
+                uint32_t nb = adj[(uint64_t)p * R + r];
+                orc_dpair e;
+                uint32_t pos;
+                if (nb == ORC_NONE || seen[nb]) continue;
+                seen[nb] = 1; touched[(*ntouched)++] = nb;
+                e.id = nb; e.dist = sqdist_f64(X, d, nb, xq);
+                /* insert into the sorted worklist, keep Lb entries */
+                pos = nl;
+                while (pos > 0 && dpair_cmp(&Lst[pos - 1], &e) > 0) pos--;
+                if (pos >= Lb) continue;
+                if (nl < Lb) nl++;
+                for (i = nl - 1; i > pos; i--) { Lst[i] = Lst[i - 1]; exp[i] = exp[i - 1]; }
+                Lst[pos] = e; exp[pos] = 0;
+            }
+        }
+    }
+    return nv;
+}
+
+/* Vamana build: two passes over the points in the given order, pruning
+ * parameter 1 then alpha.  For every p: GreedySearch from the medoid,
+ * RobustPrune(p, visited U N_out(p)), then add p to every new neighbour's
+ * list, re-pruning a list that would exceed R.  The seeded random initial
+ * graph (n*R, unused slots 0xFFFFFFFF) and the visiting order are inputs. */
+int orc_vamana_build(const float *X, uint64_t n, uint32_t d, uint32_t R, uint32_t Lb,
+                     float alpha, uint32_t medoid, const uint32_t *init_adj,
+                     const uint32_t *order, uint32_t *adj)
+{
+    uint32_t vcap = 4 * Lb + 64;
+    unsigned char *seen = (unsigned char *)calloc(n, 1);
+    uint32_t *touched = (uint32_t *)malloc(sizeof(uint32_t) * ((size_t)vcap * R + Lb + 1));
+    orc_dpair *Lst = (orc_dpair *)malloc(sizeof(orc_dpair) * (Lb + 1));
+    unsigned char *exp = (unsigned char *)malloc(Lb + 1);
+    uint32_t *V = (uint32_t *)malloc(sizeof(uint32_t) * vcap);
+    uint32_t *cand = (uint32_t *)malloc(sizeof(uint32_t) * (vcap + R + 1));
+    uint32_t *pr = (uint32_t *)malloc(sizeof(uint32_t) * (R + 1));
+    int pass;
+    uint64_t t;
+    if (!seen || !touched || !Lst || !exp || !V || !cand || !pr) return -1;
+    memcpy(adj, init_adj, sizeof(uint32_t) * n * R);
+    for (pass = 0; pass < 2; pass++) {
+        float a = pass == 0 ? 1.0f : alpha;
+        for (t = 0; t < n; t++) {
+            uint32_t p = order[t], nv, nt = 0, nc = 0, r, np, i;
+            nv = build_greedy(X, d, adj, R, medoid, X + (uint64_t)p * d, Lb, seen, touched, &nt,
+                              Lst, exp, V, vcap);
+            for (i = 0; i < nt; i++) seen[touched[i]] = 0;
+            for (i = 0; i < nv; i++) cand[nc++] = V[i];
+            for (r = 0; r < R; r++) cand[nc++] = adj[(uint64_t)p * R + r];
+            np = orc_robust_prune(X, d, p, cand, nc, a, R, pr);
+            for (r = 0; r < R; r++) adj[(uint64_t)p * R + r] = r < np ? pr[r] : ORC_NONE;
+            for (i = 0; i < np; i++) {
+                uint32_t j = pr[i], deg = 0, has = 0;
+                uint32_t *lj = adj + (uint64_t)j * R;
+                for (r = 0; r < R; r++) {
+                    if (lj[r] == ORC_NONE) continue;
+                    deg++;
+                    if (lj[r] == p) has = 1;
+                }
+                if (has) continue;
+                if (deg < R) {
+                    for (r = 0; r < R; r++) if (lj[r] == ORC_NONE) { lj[r] = p; break; }
+                } else {
+                    uint32_t c2[1024], k2 = 0, nk;
+                    uint32_t kept[1024];
+                    for (r = 0; r < R; r++) c2[k2++] = lj[r];
+                    c2[k2++] = p;
+                    nk = orc_robust_prune(X, d, j, c2, k2, a, R, kept);
+                    for (r = 0; r < R; r++) lj[r] = r < nk ? kept[r] : ORC_NONE;
+                }
+            }
+        }
+    }
+    free(seen); free(touched); free(Lst); free(exp); free(V); free(cand); free(pr);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* PQDistTable (§4.1), FP32 form: T[s][c] = sum over the dimensions j of    */
+/* subspace s, in ascending j, of (q_j - C[s][c][j])^2, accumulated as      */
+/* acc = fmaf(diff, diff, acc) from acc = 0, diff rounded to FP32.          */
+/* ---------------------------------------------------------------------- */
+
+void orc_adc_table_f32(const float *q, uint32_t M, const uint32_t *off,
+                       const float *codebook, float *T)
+{
+    uint32_t s, c, j;
+    for (s = 0; s < M; s++) {
+        uint32_t o = off[s], ds = off[s + 1] - off[s];
+        for (c = 0; c < 256; c++) {
+            const float *cc = centroid(codebook, off, s, c);
+            float acc = 0.0f;
+            for (j = 0; j < ds; j++) {
+                float diff = q[o + j] - cc[j];
+                acc = fmaf(diff, diff, acc);
+            }
+            T[s * 256 + c] = acc;
+        }
+    }
+}
+
+/* Asymmetric distance (§4.4): the sum over subspaces of T[s][code[s]].
+ * The paper leaves the summation order to the reduction it uses; the order
+ * fixed here is: eight partial sums p_r over the subspaces s = r (mod 8),
+ * each added in ascending s from 0, then three butterfly rounds
+ * p_r += p_(r xor 4), p_r += p_(r xor 2), p_r += p_(r xor 1); result p_0. */
+float orc_adc_dist_f32(const float *T, uint32_t M, const uint8_t *code)
+{
+    float p[8], nx[8];
+    uint32_t s, r, h;
+    for (r = 0; r < 8; r++) p[r] = 0.0f;
+    for (s = 0; s < M; s++) p[s & 7] = p[s & 7] + T[s * 256 + code[s]];
+    for (h = 4; h >= 1; h >>= 1) {
+        for (r = 0; r < 8; r++) nx[r] = p[r] + p[r ^ h];
+        for (r = 0; r < 8; r++) p[r] = nx[r];
+    }
+    return p[0];
+}
+
+/* ---------------------------------------------------------------------- */
+/* Exact distance for the re-rank (§4.8).                                   */
+/* Integer data: exact integer sum of squared differences.                  */
+/* FP32 data: 32 partial sums p_r over the dimensions j with                */
+/* (j/4) mod 32 = r, each accumulated in ascending j with                   */
+/* fmaf(diff, diff, p_r) from 0; then five butterfly rounds                 */
+/* p_r += p_(r xor h) for h = 16, 8, 4, 2, 1; result p_0.                   */
+/* The returned key is exact in double (integer, or the FP32 value).       */
+/* ---------------------------------------------------------------------- */
+
+double orc_exact_dist(const void *q, const void *x, int dtype, uint32_t d)
+{
+    uint32_t j;
+    if (dtype != ORC_F32) {
+        int64_t acc = 0;
+        for (j = 0; j < d; j++) {
+            int64_t t = (int64_t)elem_i(q, dtype, j) - (int64_t)elem_i(x, dtype, j);
+            acc += t * t;
+        }
+        return (double)acc;
+    } else {
+        const float *qf = (const float *)q, *xf = (const float *)x;
+        float p[32], nx[32];
+        uint32_t r, h;
+        for (r = 0; r < 32; r++) p[r] = 0.0f;
+        for (j = 0; j < d; j++) {
+            float diff = qf[j] - xf[j];
+            r = (j >> 2) & 31u;
+            p[r] = fmaf(diff, diff, p[r]);
+        }
+        for (h = 16; h >= 1; h >>= 1) {
+            for (r = 0; r < 32; r++) nx[r] = p[r] + p[r ^ h];
+            for (r = 0; r < 32; r++) p[r] = nx[r];
+        }
+        return (double)p[0];
+    }
+}
+
+/* ---------------------------------------------------------------------- */
+/* Bloom filter of seen nodes (§4.3; two FNV-1a hashes, §6.3).              */
+/* z = 2^log2z bits.  h1 = FNV-1a 32-bit over the 4 little-endian bytes of  */
+/* the id; h2 = FNV-1a 64-bit over the same bytes, folded to 32 bits as     */
+/* (h >> 32) xor (h & 0xffffffff).  Bit positions: h1 mod z and h2 mod z.   */
+/* ---------------------------------------------------------------------- */
+
+uint32_t orc_fnv1a32_bytes(const unsigned char *b, uint32_t len)
+{
+    uint32_t h = 2166136261u, i;
+    for (i = 0; i < len; i++) { h ^= b[i]; h *= 16777619u; }
+    return h;
+}
+
+uint64_t orc_fnv1a64_bytes(const unsigned char *b, uint32_t len)
+{
+    uint64_t h = 14695981039346656037ull;
+    uint32_t i;
+    for (i = 0; i < len; i++) { h ^= b[i]; h *= 1099511628211ull; }
+    return h;
+}
+
+static void id_bytes(uint32_t id, unsigned char *b)
+{
+    b[0] = (unsigned char)(id & 0xff);
+    b[1] = (unsigned char)((id >> 8) & 0xff);
+    b[2] = (unsigned char)((id >> 16) & 0xff);
+    b[3] = (unsigned char)((id >> 24) & 0xff);
+}
+
+void orc_bloom_positions(uint32_t id, uint32_t log2z, uint32_t *pos2)
+{
+    unsigned char b[4];
+    uint64_t h2;
+    uint32_t mask = (log2z >= 32) ? 0xFFFFFFFFu : ((1u << log2z) - 1u);
+    id_bytes(id, b);
+    h2 = orc_fnv1a64_bytes(b, 4);
+    pos2[0] = orc_fnv1a32_bytes(b, 4) & mask;
+    pos2[1] = ((uint32_t)(h2 >> 32) ^ (uint32_t)(h2 & 0xFFFFFFFFu)) & mask;
+}
+
+int orc_bloom_test(const uint32_t *bits, uint32_t log2z, uint32_t id)
+{
+    uint32_t p[2];
+    orc_bloom_positions(id, log2z, p);
+    return ((bits[p[0] >> 5] >> (p[0] & 31)) & 1u) && ((bits[p[1] >> 5] >> (p[1] & 31)) & 1u);
+}
+
+void orc_bloom_insert(uint32_t *bits, uint32_t log2z, uint32_t id)
+{
+    uint32_t p[2];
+    orc_bloom_positions(id, log2z, p);
+    bits[p[0] >> 5] |= 1u << (p[0] & 31);
+    bits[p[1] >> 5] |= 1u << (p[1] & 31);
+}
+
+/* ---------------------------------------------------------------------- */
+/* Search (Alg. 1 run for each query of the batch as in Alg. 2).            */
+/* ---------------------------------------------------------------------- */
+
+typedef struct { float dist; uint32_t id; int visited; } orc_entry;
+
+static int entry_cmp(const void *pa, const void *pb)
+{
+    const orc_entry *a = (const orc_entry *)pa, *b = (const orc_entry *)pb;
+    if (a->dist < b->dist) return -1;
+    if (a->dist > b->dist) return 1;
+    return (a->id < b->id) ? -1 : (a->id > b->id);
+}
+
+static int dpair_cmp_stable(const void *pa, const void *pb) { return dpair_cmp(pa, pb); }
+
+/* One query.  Steps, in the order of Alg. 2 and §4:
+ *  - T <- PQDistTable row of the query (§4.1); the query is converted to FP32.
+ *  - worklist L <- [(ADC(s), s, unvisited)], s inserted into the Bloom filter.
+ *  - loop: u* <- first unvisited entry of L (L is kept sorted by (distance,
+ *    id)); stop when there is none, or after iter_cap expansions (status 1).
+ *    Mark u* visited; record it as a re-rank candidate with its exact
+ *    distance (§4.2, §4.8: the candidates' full vectors are fetched as they
+ *    are visited).  N <- adj(u*) in stored order, skipping 0xFFFFFFFF.
+ *    N' <- the ids of N whose Bloom test fails, all tested against the
+ *    filter as it was before this iteration; then insert all of N' (§4.3).
+ *    D[n] <- ADC(n) for n in N' (§4.4).  L <- the first L entries of
+ *    L u {(D[n], n, unvisited)} sorted by (distance, id) (§4.6, §4.7).
+ *  - re-rank (§4.8): sort the candidates by (exact distance, id); output
+ *    the first k; pad with id 0xFFFFFFFF and distance +inf.
+ * The eager choice of the next candidate (§4.5) is the first unvisited
+ * entry after the merge, so it does not appear as a separate step. */
+static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t Lsz,
+                       uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
+                       uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
+                       uint32_t *trace, uint32_t trace_cap)
+{
+    uint32_t d = ix->d, M = ix->M, R = ix->R, i, r;
+    float *qf = (float *)malloc(sizeof(float) * d);
+    float *T = (float *)malloc(sizeof(float) * (size_t)M * 256);
+    uint32_t nwords = (log2z >= 5) ? (1u << (log2z - 5)) : 1u;
+    uint32_t *bits = (uint32_t *)calloc(nwords, sizeof(uint32_t));
+    orc_entry *Lst = (orc_entry *)malloc(sizeof(orc_entry) * (Lsz + R + 1));
+    uint32_t *Np = (uint32_t *)malloc(sizeof(uint32_t) * (R + 1));
+    uint32_t ccap = iter_cap + 1, nc = 0, nl, iters = 0;
+    orc_dpair *C = (orc_dpair *)malloc(sizeof(orc_dpair) * ccap);
+    uint64_t ndist = 0;
+    int32_t status = 0;
+    size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
+
+    for (i = 0; i < d; i++) qf[i] = elem_f(q, ix->dtype, i);
+    orc_adc_table_f32(qf, M, ix->off, ix->codebook, T);
+
+    Lst[0].id = ix->medoid;
+    Lst[0].dist = orc_adc_dist_f32(T, M, ix->codes + (uint64_t)ix->medoid * M);
+    Lst[0].visited = 0;
+    ndist++;
+    nl = 1;
+    orc_bloom_insert(bits, log2z, ix->medoid);
+
+    for (;;) {
+        uint32_t u = ORC_NONE, nn = 0, nadd;
+        for (i = 0; i < nl; i++) if (!Lst[i].visited) { u = i; break; }
+        if (u == ORC_NONE) break;
+        if (iters >= iter_cap) { status = 1; break; }
+        Lst[u].visited = 1;
+        {
+            uint32_t us = Lst[u].id;
+            if (trace && iters < trace_cap) trace[iters] = us;
+            iters++;
+            C[nc].id = us;
+            C[nc].dist = orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)us * d * esz,
+                                        ix->dtype, d);
+            nc++;
+            for (r = 0; r < R; r++) {
+                uint32_t nb = ix->adj[(uint64_t)us * R + r];
+                if (nb == ORC_NONE) continue;
+                if (!orc_bloom_test(bits, log2z, nb)) Np[nn++] = nb;
+            }
+        }
+        for (i = 0; i < nn; i++) orc_bloom_insert(bits, log2z, Np[i]);
+        nadd = 0;
+        for (i = 0; i < nn; i++) {
+            Lst[nl + nadd].id = Np[i];
+            Lst[nl + nadd].dist = orc_adc_dist_f32(T, M, ix->codes + (uint64_t)Np[i] * M);
+            Lst[nl + nadd].visited = 0;
+            nadd++;
+        }
+        ndist += nn;
+        qsort(Lst, nl + nadd, sizeof(orc_entry), entry_cmp);
+        nl = (nl + nadd < Lsz) ? nl + nadd : Lsz;
+    }
+
+    qsort(C, nc, sizeof(orc_dpair), dpair_cmp_stable);
+    for (i = 0; i < k; i++) {
+        if (i < nc) { out_ids[i] = C[i].id; out_dist[i] = (float)C[i].dist; }
+        else { out_ids[i] = ORC_NONE; out_dist[i] = INFINITY; }
+    }
+    if (out_iters) *out_iters = iters;
+    if (out_status) *out_status = status;
+    if (out_ndist) *out_ndist = ndist;
+    free(qf); free(T); free(bits); free(Lst); free(Np); free(C);
+}
+
+int orc_search(const orc_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
+               uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
+               uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
+               uint32_t *trace, uint32_t trace_cap, int nthreads)
+{
+    int64_t qi;
+    size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
+    if (k == 0 || L < k || ix->M == 0 || ix->d == 0) return -1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#else
+    (void)nthreads;
+#endif
+    for (qi = 0; qi < (int64_t)nq; qi++) {
+        search_one(ix, (const unsigned char *)queries + (uint64_t)qi * ix->d * esz, k, L, log2z,
+                   iter_cap, out_ids + (uint64_t)qi * k, out_dist + (uint64_t)qi * k,
+                   out_iters ? out_iters + qi : NULL, out_status ? out_status + qi : NULL,
+                   out_ndist ? out_ndist + qi : NULL,
+                   trace ? trace + (uint64_t)qi * trace_cap : NULL, trace_cap);
+    }
+    return 0;
+}
+
+int orc_max_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* ---------------------------------------------------------------------- */
+/* Brute-force ground truth (§6.3, k-recall@k): exact distances in FP64    */
+/* (exact integers for integer data) to every point, sorted by             */
+/* (distance, id), first k.                                                */
+/* ---------------------------------------------------------------------- */
+
+void orc_bruteforce_knn(const void *base, const void *queries, int dtype, uint64_t n,
+                        uint32_t nq, uint32_t d, uint32_t k, uint32_t *ids, double *dists,
+                        int nthreads)
+{
+    int64_t qi;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#else
+    (void)nthreads;
+#endif
+    for (qi = 0; qi < (int64_t)nq; qi++) {
+        orc_dpair *top = (orc_dpair *)malloc(sizeof(orc_dpair) * (k + 1));
+        uint32_t nt = 0, j, t;
+        uint64_t i;
+        for (i = 0; i < n; i++) {
+            orc_dpair e;
+            double acc = 0.0;
+            if (dtype == ORC_F32) {
+                const float *qf = (const float *)queries + (uint64_t)qi * d;
+                const float *xf = (const float *)base + i * d;
+                for (j = 0; j < d; j++) {
+                    double t2 = (double)qf[j] - (double)xf[j];
+                    acc += t2 * t2;
+                }
+            } else {
+                int64_t ia = 0;
+                for (j = 0; j < d; j++) {
+                    int64_t t2 = (int64_t)elem_i(queries, dtype, (uint64_t)qi * d + j) -
+                                 (int64_t)elem_i(base, dtype, i * d + j);
+                    ia += t2 * t2;
+                }
+                acc = (double)ia;
+            }
+            e.dist = acc; e.id = (uint32_t)i;
+            if (nt == k && dpair_cmp(&e, &top[k - 1]) >= 0) continue;
+            t = (nt < k) ? nt++ : k - 1;
+            while (t > 0 && dpair_cmp(&top[t - 1], &e) > 0) { top[t] = top[t - 1]; t--; }
+            top[t] = e;
+        }
+        for (j = 0; j < k; j++) {
+            ids[(uint64_t)qi * k + j] = j < nt ? top[j].id : ORC_NONE;
+            dists[(uint64_t)qi * k + j] = j < nt ? top[j].dist : INFINITY;
+        }
+        free(top);
+    }
+}

@@ -1,0 +1,58 @@
+"""Plant plausible mistakes in copies of the oracle (CPU only) and check that
+the pins in test_oracle_pins.py catch every one of them."""
+import os
+import subprocess
+import sys
+import tempfile
+
+import pytest
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+ROOT = os.path.dirname(HERE)
+SRC = os.path.join(ROOT, "oracle", "bang_oracle.c")
+
+# (name, text to replace, replacement, which occurrence (0-based))
+MUTANTS = [
+    ("adc_table_sign", "float diff = q[o + j] - cc[j];", "float diff = q[o + j] + cc[j];", 0),
+    ("adc_table_drops_dim", "for (j = 0; j < ds; j++) {\n                float diff = q[o + j]",
+     "for (j = 1; j < ds; j++) {\n                float diff = q[o + j]", 0),
+    ("adc_dist_drops_round", "for (h = 4; h >= 1; h >>= 1)", "for (h = 4; h >= 2; h >>= 1)", 0),
+    ("adc_dist_wrong_subspace", "T[s * 256 + code[s]]", "T[s * 256 + code[s & ~1u]]", 0),
+    ("exact_tree", "r = (j >> 2) & 31u;", "r = j & 31u;", 0),
+    ("exact_transposed", "float diff = qf[j] - xf[j];", "float diff = qf[j] - xf[j ^ 1u];", 0),
+    ("fnv_prime", "h *= 16777619u;", "h *= 16777617u;", 0),
+    ("bloom_one_hash", "pos2[1] = ((uint32_t)(h2 >> 32)", "pos2[1] = pos2[0] | ((uint32_t)0 & (h2 >> 32)", 0),
+    ("search_keeps_extra", "nl = (nl + nadd < Lsz) ? nl + nadd : Lsz;",
+     "nl = (nl + nadd < Lsz + 1) ? nl + nadd : Lsz + 1;", 0),
+    ("rerank_uses_pq", "C[nc].dist = orc_exact_dist(", "C[nc].dist = Lst[u].dist + 0 * orc_exact_dist(", 0),
+    ("medoid_no_mean", "for (j = 0; j < d; j++) mean[j] /= (double)n;", "", 0),
+    ("kmeans_bad_mean", "sums[c * ds + j] / (double)cnt[c]", "sums[c * ds + j] / (double)(cnt[c] + 1)", 0),
+    ("encode_ties_high", "if (acc < best) { best = acc; bc = c; }", "if (acc <= best) { best = acc; bc = c; }", 1),
+    ("prune_alpha_unsquared", "double a2 = (double)alpha * (double)alpha;", "double a2 = (double)alpha;", 0),
+    ("bruteforce_l1", "ia += t2 * t2;", "ia += t2 < 0 ? -t2 : t2;", 0),
+]
+
+
+def _mutate(src, old, new, occ):
+    pos = -1
+    for _ in range(occ + 1):
+        pos = src.index(old, pos + 1)
+    return src[:pos] + new + src[pos + len(old):]
+
+
+@pytest.mark.parametrize("name,old,new,occ", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_pins_catch_planted_mistake(name, old, new, occ, tmp_path):
+    src = open(SRC).read()
+    mutated = _mutate(src, old, new, occ)
+    assert mutated != src
+    c = tmp_path / "mut.c"
+    c.write_text(mutated)
+    so = tmp_path / "libmut.so"
+    subprocess.check_call(["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fopenmp", "-I", os.path.join(ROOT, "oracle"), "-o", str(so), str(c),
+                           "-lm"])
+    env = dict(os.environ, ORACLE_LIB=str(so))
+    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
+                        os.path.join(HERE, "test_oracle_pins.py")], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0, "planted mistake %s was not caught:\n%s" % (name, r.stdout[-2000:])

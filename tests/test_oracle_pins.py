@@ -1,0 +1,500 @@
+"""Pins for the CPU oracle: each test checks it against something the paper or
+the mathematics fixes (closed forms, published hash vectors, the paper's
+worked example, invariants, brute force on tiny inputs), never against a
+retyped copy of itself."""
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+
+NONE = oracle.NONE
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ---------------------------------------------------------------- helpers
+
+def lossless_u8(X):
+    """PQ with one dimension per subspace and the codebook C[s][c] = c: the
+    codes are the points themselves and ADC equals the exact distance."""
+    n, d = X.shape
+    cb = np.tile(np.arange(256, dtype=np.float32), d)
+    return cb, X.astype(np.uint8).copy()
+
+
+def complete_graph(n):
+    adj = np.full((n, max(n - 1, 1)), NONE, np.uint32)
+    for i in range(n):
+        adj[i, :n - 1] = [j for j in range(n) if j != i]
+    return adj
+
+
+def brute_ids(X, q, k):
+    d = ((X.astype(np.int64) - q.astype(np.int64)) ** 2).sum(1)
+    order = np.lexsort((np.arange(len(d)), d))
+    return order[:k], d[order[:k]]
+
+
+# ---------------------------------------------------------------- FNV-1a, Bloom (§4.3, §6.3)
+
+def test_fnv1a_published_vectors():
+    # Test vectors published with the FNV hash definition.
+    assert oracle.fnv1a32(b"") == 0x811C9DC5
+    assert oracle.fnv1a32(b"a") == 0xE40C292C
+    assert oracle.fnv1a32(b"foobar") == 0xBF9CF968
+    assert oracle.fnv1a64(b"") == 0xCBF29CE484222325
+    assert oracle.fnv1a64(b"a") == 0xAF63DC4C8601EC8C
+    assert oracle.fnv1a64(b"foobar") == 0x85944171F73967E8
+
+
+def test_bloom_hashes_little_endian_id_bytes():
+    b = oracle.Bloom(20)
+    ident = int.from_bytes(b"abcd", "little")
+    h64 = oracle.fnv1a64(b"abcd")
+    p1, p2 = b.positions(ident)
+    assert p1 == oracle.fnv1a32(b"abcd") & ((1 << 20) - 1)
+    assert p2 == ((h64 >> 32) ^ (h64 & 0xFFFFFFFF)) & ((1 << 20) - 1)
+
+
+def test_bloom_no_false_negatives_and_fp_rate():
+    rng = np.random.default_rng(7)
+    log2z, n_ins, n_test = 14, 2000, 40000
+    ids = rng.choice(1 << 30, size=n_ins + n_test, replace=False)
+    b = oracle.Bloom(log2z)
+    for i in ids[:n_ins]:
+        b.insert(int(i))
+    assert all(b.test(int(i)) for i in ids[:n_ins])
+    fp = sum(b.test(int(i)) for i in ids[n_ins:]) / n_test
+    z = 1 << log2z
+    expect = (1 - math.exp(-2 * n_ins / z)) ** 2
+    sigma = math.sqrt(expect * (1 - expect) / n_test)
+    assert abs(fp - expect) < 3 * sigma + 0.15 * expect
+
+
+# ---------------------------------------------------------------- PQ (§4)
+
+def test_chunk_offsets_uneven_split():
+    off = oracle.chunk_offsets(128, 74)
+    sizes = np.diff(off)
+    assert off[-1] == 128 and len(sizes) == 74
+    assert (sizes[:54] == 2).all() and (sizes[54:] == 1).all()
+    assert (np.diff(oracle.chunk_offsets(96, 48)) == 2).all()
+
+
+def test_adc_table_closed_form():
+    d, M = 8, 2
+    c = np.arange(256, dtype=np.float64)
+    cb = np.concatenate([(c[:, None] + 0.25 * np.arange(4)[None, :] + 3 * s).ravel()
+                         for s in range(M)]).astype(np.float32)
+    q = np.array([0.5, -1.0, 2.0, 7.25, 100.0, 3.5, 0.0, 255.0], np.float32)
+    T = oracle.adc_table(q, M, cb)
+    for s in range(M):
+        for cc in (0, 1, 17, 128, 255):
+            exact = sum((Fraction(float(q[4 * s + j])) - Fraction(cc) - Fraction(j, 4) - 3 * s) ** 2
+                        for j in range(4))
+            assert Fraction(float(T[s, cc])) == exact
+
+
+def test_adc_dist_is_sum_of_selected_entries():
+    rng = np.random.default_rng(1)
+    M = 32
+    T = rng.integers(0, 2000, size=(M, 256)).astype(np.float32)
+    for _ in range(20):
+        code = rng.integers(0, 256, size=M).astype(np.uint8)
+        assert oracle.adc_dist(T, code) == float(sum(int(T[s, code[s]]) for s in range(M)))
+
+
+def test_adc_dist_summation_tree():
+    # Reading of §4.4 (order of the segment sums): 8 strided partials, then
+    # butterfly p_r += p_(r^4), p_r += p_(r^2), p_r += p_(r^1).  Values
+    # chosen so that any other order of the additions rounds differently.
+    M = 16
+    T = np.zeros((M, 256), np.float32)
+    vals = [1.0, 2.0 ** -24, 2.0 ** -24, 0.0, 0.0, 0.0, 0.0, 0.0,
+            2.0 ** -24, 2.0 ** -24, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0]
+    for s, v in enumerate(vals):
+        T[s, 0] = v
+    code = np.zeros(M, np.uint8)
+    f = np.float32
+    p = [f(0)] * 8
+    for s in range(M):
+        p[s & 7] = f(p[s & 7] + f(vals[s]))
+    for h in (4, 2, 1):
+        p = [f(p[r] + p[r ^ h]) for r in range(8)]
+    got = oracle.adc_dist(T, code)
+    assert got == float(p[0])
+    seq = f(0)
+    for v in vals:
+        seq = f(seq + f(v))
+    assert got != float(seq)          # plain left-to-right order would differ
+
+
+def test_pq_encode_closed_form_and_ties():
+    d, M = 8, 2
+    rng = np.random.default_rng(2)
+    cb = rng.integers(0, 200, size=256 * d).astype(np.float32)
+    cb[256 * 4 + 9 * 4: 256 * 4 + 10 * 4] = cb[256 * 4 + 3 * 4: 256 * 4 + 4 * 4]  # s=1: c9 == c3
+    X = np.zeros((3, d), np.float32)
+    X[0, :4] = cb[5 * 4:6 * 4]; X[0, 4:] = cb[256 * 4 + 200 * 4: 256 * 4 + 201 * 4]
+    X[1, :4] = cb[0:4]; X[1, 4:] = cb[256 * 4 + 9 * 4: 256 * 4 + 10 * 4]
+    X[2, :4] = cb[255 * 4:256 * 4]; X[2, 4:] = cb[256 * 4 + 255 * 4: 256 * 4 + 256 * 4]
+    codes = oracle.pq_encode(X, M, cb)
+    assert codes[0].tolist() == [5, 200]
+    assert codes[1].tolist() == [0, 3]          # tie between c3 and c9 -> smaller id
+    assert codes[2].tolist() == [255, 255]
+
+
+def test_kmeans_fixed_point_and_separated_clusters():
+    rng = np.random.default_rng(3)
+    d, M = 8, 2
+    # 256 distinct points, initialised at themselves: a fixed point, objective 0.
+    P = rng.permutation(256 * 256)[:256]
+    X = np.stack([(P // 256) % 256, P % 256, P % 7, P % 5, P % 11, P % 13, P % 3, P % 17], 1)
+    X = X.astype(np.float32)
+    _, uniq = np.unique(X[:, :4], axis=0, return_index=True)
+    _, uniq2 = np.unique(X[:, 4:], axis=0, return_index=True)
+    assert len(uniq) == 256
+    init = np.stack([np.arange(256), np.arange(256)])
+    cb, tr = oracle.pq_train(X, M, np.arange(256), init, 3, return_trace=True)
+    assert np.array_equal(cb[:256 * 4].reshape(256, 4), X[:, :4])
+    assert tr[0].tolist() == [0.0, 0.0, 0.0]
+    # 256 tight, well separated clusters of 6 points: after one Lloyd step
+    # every centroid is its cluster mean.
+    centres = rng.permutation(256 * 256)[:256]
+    C = np.stack([centres // 256, centres % 256, (centres * 7) % 251, (centres * 3) % 241], 1)
+    C = (C * 100.0).astype(np.float64)
+    off = rng.normal(0, 1.0, size=(256, 6, 4))
+    Y = (C[:, None, :] + off).reshape(-1, 4)
+    Y = np.concatenate([Y, Y], 1).astype(np.float32)
+    init = np.stack([np.arange(256) * 6, np.arange(256) * 6])
+    cb, tr = oracle.pq_train(Y, M, np.arange(len(Y)), init, 2, return_trace=True)
+    means = Y[:, :4].astype(np.float64).reshape(256, 6, 4).mean(1)
+    assert np.allclose(cb[:256 * 4].reshape(256, 4), means, rtol=0, atol=1e-3)
+    assert tr[0, 1] <= tr[0, 0]
+
+
+def test_kmeans_objective_non_increasing():
+    rng = np.random.default_rng(4)
+    X = rng.normal(size=(3000, 16)).astype(np.float32)
+    init = np.stack([rng.choice(3000, 256, replace=False) for _ in range(4)])
+    _, tr = oracle.pq_train(X, 4, np.arange(3000), init, 8, return_trace=True)
+    assert (np.diff(tr, axis=1) <= 1e-9 * tr[:, :-1]).all()
+
+
+def test_medoid_closed_form():
+    X = np.zeros((7, 3), np.float32)
+    X[:, 0] = [0, 1, 2, 10, 11, 12, 6]      # mean 6 -> point 6
+    assert oracle.medoid(X) == 6
+    Y = np.array([[0], [2], [4], [6]], np.uint8)   # mean 3: points 1 and 2 tie -> 1
+    assert oracle.medoid(Y) == 1
+
+
+# ---------------------------------------------------------------- exact distance (§4.8)
+
+def test_exact_dist_integer_types_exact():
+    rng = np.random.default_rng(5)
+    for dt, lo, hi in ((np.uint8, 0, 256), (np.int8, -128, 128)):
+        a = rng.integers(lo, hi, size=100).astype(dt)
+        b = rng.integers(lo, hi, size=100).astype(dt)
+        assert oracle.exact_dist(a, b) == float(((a.astype(np.int64) - b.astype(np.int64)) ** 2).sum())
+    a = np.full(128, 255, np.uint8)
+    b = np.zeros(128, np.uint8)
+    assert oracle.exact_dist(a, b) == 128 * 255 ** 2
+
+
+def test_exact_dist_f32_error_bound_and_order():
+    rng = np.random.default_rng(6)
+    for d in (96, 100, 128, 200):
+        a = rng.normal(size=d).astype(np.float32)
+        b = rng.normal(size=d).astype(np.float32)
+        ref = float(((a.astype(np.float64) - b.astype(np.float64)) ** 2).sum())
+        got = oracle.exact_dist(a, b)
+        assert abs(got - ref) <= (d + 2) * 2.0 ** -24 * ref
+    # Strided-partials tree (the order is a reading: the paper does not fix
+    # it).  Squared differences of 2^-24 are exact, so the only rounding is in
+    # the additions.  Case 1: dims 0..3 share partial 0, so three 2^-24 terms
+    # each vanish against 1.0 -> exactly 1.0 (a tree splitting them would
+    # give 1 + 2^-23).  Case 2: dims 4..6 share partial 1 (sum 3*2^-24), which
+    # meets 1.0 once -> 1 + 2^-22 by round-to-even (left-to-right gives 1.0).
+    b = np.zeros(8, np.float32)
+    a = np.zeros(8, np.float32)
+    a[0] = 1.0
+    a[1:4] = 2.0 ** -12
+    assert oracle.exact_dist(a, b) == 1.0
+    a = np.zeros(8, np.float32)
+    a[0] = 1.0
+    a[4:7] = 2.0 ** -12
+    assert oracle.exact_dist(a, b) == 1.0 + 2.0 ** -22
+
+
+# ---------------------------------------------------------------- the paper's worked example
+
+def _read_golden():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "toy_workflow.txt"))
+            if l.strip() and not l.startswith("#")]
+    g = {"b": {}, "d": []}
+    for r in rows:
+        if r[0] == "query":
+            g["q"] = (int(r[1]), int(r[2]))
+        elif r[0] == "table_b":
+            g["b"][int(r[1])] = int(r[3])
+        elif r[0] == "table_d":
+            g["d"].append((int(r[2]), int(r[3])))
+        elif r[0] == "sorted_candidates":
+            g["sorted"] = [int(x) for x in r[1:]]
+        elif r[0] == "top2":
+            g["top2"] = [int(x) for x in r[1:]]
+    return g
+
+
+def _point_at(q, dist):
+    """A 3-D integer point at the given squared distance from (q, 0)."""
+    for a in range(0, 90):
+        for b in range(0, a + 1):
+            for c in range(0, 8):
+                if a * a + b * b + c * c == dist:
+                    return (q[0] + a, q[1] + b, c)
+    raise AssertionError(dist)
+
+
+def test_worked_example_rerank():
+    g = _read_golden()
+    q = g["q"]
+    cand = [n for n, _ in g["d"]]
+    dist_d = dict(g["d"])
+    X = np.zeros((12, 3), np.uint8)
+    for node in range(12):
+        X[node] = _point_at(q, dist_d.get(node, g["b"][node]))
+    qv = np.array([q[0], q[1], 0], np.uint8)
+    for node, dd in g["d"]:
+        assert oracle.exact_dist(qv, X[node]) == dd
+    # The figure's graph is lost: search the subgraph of the eight candidates
+    # (complete among them) from the first candidate, with a worklist large
+    # enough to visit all of them, then re-rank.
+    adj = np.full((12, 7), NONE, np.uint32)
+    for i in cand:
+        adj[i] = [j for j in cand if j != i]
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, cand[0], 3)
+    r = ix.search(qv[None], k=8, L=8, log2z=16, trace_cap=16)
+    assert sorted(r["trace"][0][:r["iters"][0]].tolist()) == sorted(cand)
+    assert r["ids"][0].tolist() == g["sorted"]
+    r2 = ix.search(qv[None], k=2, L=8, log2z=16)
+    assert r2["ids"][0].tolist() == g["top2"]
+
+
+# ---------------------------------------------------------------- search (Alg. 1 / Alg. 2)
+
+def test_lossless_pq_equals_exact_distance():
+    rng = np.random.default_rng(8)
+    X = rng.integers(0, 256, size=(50, 128)).astype(np.uint8)
+    cb, codes = lossless_u8(X)
+    q = rng.integers(0, 256, size=128).astype(np.uint8)
+    T = oracle.adc_table(q.astype(np.float32), 128, cb)
+    for i in range(50):
+        assert oracle.adc_dist(T, codes[i]) == oracle.exact_dist(q, X[i])
+
+
+def test_chain_graph_visit_order():
+    # Points 0..20 on a line, chain graph i <-> i+1, entry 0, query 13.
+    # Worked by hand from Alg. 1 with the seen-set filter of Alg. 2:
+    # L=1 and L=2 expand 0..13 (14 is seen at 13 but never beats it);
+    # L=3 also expands 14, whose new neighbour 15 falls off the list.
+    n = 21
+    X = np.arange(n, dtype=np.uint8)[:, None]
+    adj = np.full((n, 2), NONE, np.uint32)
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        adj[i, :len(nb)] = nb
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, 0, 1)
+    q = np.array([[13]], np.uint8)
+    for L, last in ((1, 13), (2, 13), (3, 14)):
+        r = ix.search(q, k=1, L=L, log2z=16, trace_cap=64)
+        it = int(r["iters"][0])
+        assert r["trace"][0][:it].tolist() == list(range(last + 1))
+        assert r["ids"][0, 0] == 13 and r["dist"][0, 0] == 0.0
+    r = ix.search(q, k=3, L=3, log2z=16)
+    assert r["ids"][0].tolist() == [13, 12, 14]      # (distance, id) ties: 12 before 14
+
+
+def test_complete_graph_equals_bruteforce():
+    rng = np.random.default_rng(9)
+    for trial in range(5):
+        n = int(rng.integers(8, 40))
+        X = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+        cb, codes = lossless_u8(X)
+        med = int(rng.integers(0, n))
+        ix = oracle.Index(X, cb, codes, complete_graph(n), med, 16)
+        Q = rng.integers(0, 256, size=(6, 16)).astype(np.uint8)
+        for L in (3, 5, 8):
+            k = 3
+            r = ix.search(Q, k=k, L=L, log2z=18)
+            for qi in range(len(Q)):
+                ids, dd = brute_ids(X, Q[qi], k)
+                assert r["ids"][qi].tolist() == ids.tolist()
+                assert r["dist"][qi].tolist() == dd.astype(np.float32).tolist()
+                topL, _ = brute_ids(X, Q[qi], L)
+                assert r["iters"][qi] == (L if med in topL.tolist() else L + 1)
+
+
+def test_full_worklist_visits_every_reachable_node():
+    # With L >= n on a connected graph and a filter without false positives
+    # in practice (z = 2^22 bits for <= 64 ids), every node is expanded and
+    # the re-rank is exact k-NN.
+    rng = np.random.default_rng(10)
+    for trial in range(5):
+        n = 64
+        X = rng.integers(0, 256, size=(n, 8)).astype(np.uint8)
+        R = 4
+        adj = np.full((n, R), NONE, np.uint32)
+        perm = rng.permutation(n)
+        for t in range(n):                         # a cycle keeps it connected
+            adj[perm[t], 0] = perm[(t + 1) % n]
+        for i in range(n):
+            extra = [j for j in rng.choice(n, size=6, replace=False) if j != i and j != adj[i, 0]]
+            adj[i, 1:1 + min(3, len(extra))] = extra[:3]
+        cb, codes = lossless_u8(X)
+        ix = oracle.Index(X, cb, codes, adj, int(perm[0]), 8)
+        Q = rng.integers(0, 256, size=(4, 8)).astype(np.uint8)
+        r = ix.search(Q, k=10, L=n, log2z=22)
+        for qi in range(len(Q)):
+            ids, _ = brute_ids(X, Q[qi], 10)
+            assert r["ids"][qi].tolist() == ids.tolist()
+            assert r["iters"][qi] == n
+
+
+def test_padding_when_fewer_than_k_reachable():
+    X = np.array([[0], [5], [9], [200]], np.uint8)
+    adj = np.array([[1], [0], [NONE], [NONE]], np.uint32)
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, 0, 1)
+    r = ix.search(np.array([[4]], np.uint8), k=4, L=4, log2z=16)
+    assert r["ids"][0].tolist() == [1, 0, NONE, NONE]
+    assert r["dist"][0, 0] == 1.0 and r["dist"][0, 1] == 16.0 and np.isinf(r["dist"][0, 2:]).all()
+
+
+def test_iteration_cap_status():
+    n = 30
+    X = np.arange(n, dtype=np.uint8)[:, None] * 3
+    adj = np.full((n, 2), NONE, np.uint32)
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        adj[i, :len(nb)] = nb
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, 0, 1)
+    r = ix.search(np.array([[87]], np.uint8), k=1, L=2, log2z=16, iter_cap=5)
+    assert r["status"][0] == 1 and r["iters"][0] == 5
+    r = ix.search(np.array([[87]], np.uint8), k=1, L=2, log2z=16)
+    assert r["status"][0] == 0 and r["ids"][0, 0] == 29
+
+
+def test_rerank_uses_exact_distances():
+    # Lossy PQ: the re-rank (§4.8) must order by, and return, exact distances.
+    rng = np.random.default_rng(15)
+    n, d, M = 400, 16, 4
+    X = rng.integers(0, 256, size=(n, d)).astype(np.uint8)
+    cb = rng.integers(0, 256, size=256 * d).astype(np.float32)
+    codes = oracle.pq_encode(X, M, cb)
+    adj = np.stack([rng.choice(np.delete(np.arange(n), i), 10, replace=False) for i in range(n)])
+    ix = oracle.Index(X, cb, codes, adj.astype(np.uint32), 0, M)
+    Q = rng.integers(0, 256, size=(10, d)).astype(np.uint8)
+    r = ix.search(Q, k=8, L=16, log2z=18)
+    for qi in range(10):
+        ex = ((X[r["ids"][qi]].astype(np.int64) - Q[qi].astype(np.int64)) ** 2).sum(1)
+        assert r["dist"][qi].tolist() == ex.astype(np.float32).tolist()
+        assert all((ex[i], r["ids"][qi][i]) < (ex[i + 1], r["ids"][qi][i + 1]) for i in range(7))
+
+
+def test_rejects_L_below_k():
+    X = np.zeros((4, 1), np.uint8)
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, complete_graph(4), 0, 1)
+    with pytest.raises(ValueError):
+        ix.search(X[:1], k=3, L=2)
+
+
+def test_iterations_at_least_worklist_size():
+    # Every entry of the final worklist has been expanded (§7.7: I >= t).
+    rng = np.random.default_rng(11)
+    n = 300
+    X = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+    adj = np.stack([rng.choice(np.delete(np.arange(n), i), 12, replace=False) for i in range(n)])
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj.astype(np.uint32), 0, 16)
+    r = ix.search(rng.integers(0, 256, size=(20, 16)).astype(np.uint8), k=5, L=24, log2z=18)
+    assert (r["iters"] >= 24).all()
+
+
+# ---------------------------------------------------------------- brute force
+
+def test_bruteforce_matches_lexsort_with_ties():
+    rng = np.random.default_rng(12)
+    X = rng.integers(0, 4, size=(500, 4)).astype(np.uint8)       # many ties
+    Q = rng.integers(0, 4, size=(10, 4)).astype(np.uint8)
+    ids, dd = oracle.bruteforce_knn(X, Q, 20)
+    for qi in range(10):
+        e_ids, e_d = brute_ids(X, Q[qi], 20)
+        assert ids[qi].tolist() == e_ids.tolist()
+        assert dd[qi].tolist() == e_d.astype(float).tolist()
+    Xf = rng.normal(size=(300, 12)).astype(np.float32)
+    Qf = rng.normal(size=(5, 12)).astype(np.float32)
+    ids, dd = oracle.bruteforce_knn(Xf, Qf, 7)
+    ref = ((Xf[None].astype(np.float64) - Qf[:, None].astype(np.float64)) ** 2).sum(-1)
+    assert (ids == np.argsort(ref, 1)[:, :7]).all()
+
+
+# ---------------------------------------------------------------- Vamana (invariants only)
+
+def test_robust_prune_rule():
+    rng = np.random.default_rng(13)
+    X = rng.normal(size=(200, 8)).astype(np.float32)
+    p = 0
+    cand = rng.choice(np.arange(1, 200), 80, replace=False)
+    alpha, R = 1.2, 12
+    out = oracle.robust_prune(X, p, cand, alpha, R)
+    d = lambda a, b: float(((X[a].astype(np.float64) - X[b]) ** 2).sum())
+    order = sorted(cand.tolist(), key=lambda c: (d(p, c), c))
+    assert out[0] == order[0] and len(out) <= R
+    kept = out.tolist()
+    # kept in increasing distance; none is dominated by an earlier kept one
+    for i, a in enumerate(kept):
+        for b in kept[:i]:
+            assert not (alpha ** 2 * d(b, a) <= d(p, a))
+    # when fewer than R are kept, each dropped candidate is dominated by a
+    # kept one that precedes it
+    if len(kept) < R:
+        for c in order:
+            if c in kept:
+                continue
+            assert any(alpha ** 2 * d(b, c) <= d(p, c) for b in kept if (d(p, b), b) < (d(p, c), c))
+
+
+def test_vamana_invariants():
+    rng = np.random.default_rng(14)
+    n, d, R = 600, 16, 12
+    cen = rng.normal(0, 2, size=(6, d))
+    X = (cen[rng.integers(0, 6, n)] + rng.normal(size=(n, d))).astype(np.float32)
+    init = np.stack([rng.choice(np.delete(np.arange(n), i), R, replace=False) for i in range(n)])
+    med = oracle.medoid(X)
+    adj = oracle.vamana_build(X, R, 32, 1.2, med, init.astype(np.uint32),
+                              rng.permutation(n).astype(np.uint32))
+    for i in range(n):
+        row = adj[i]
+        ids = row[row != NONE]
+        assert len(ids) >= 1 and (row[len(ids):] == NONE).all()
+        assert i not in ids.tolist() and len(set(ids.tolist())) == len(ids)
+    seen = {med}
+    frontier = [med]
+    while frontier:
+        nxt = []
+        for u in frontier:
+            for v in adj[u]:
+                if v != NONE and int(v) not in seen:
+                    seen.add(int(v))
+                    nxt.append(int(v))
+        frontier = nxt
+    assert len(seen) / n >= 0.99

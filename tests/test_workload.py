@@ -1,0 +1,59 @@
+"""The synthetic workload generator (stand-in for the datasets and the
+prebuilt index): valid graph, deterministic across thread counts, ground
+truth and medoid equal to the oracle's independent brute force."""
+import os
+import subprocess
+import sys
+
+import numpy as np
+
+import oracle
+import workload
+
+NONE = workload.NONE
+
+
+def _small(tmp_path, monkeypatch):
+    monkeypatch.setenv("BANG_WORKLOAD_CACHE", str(tmp_path))
+    return workload.clustered_workload(2, n=6000, nq=50, ncomp=6, k=20)
+
+
+def test_graph_is_valid_and_navigable(tmp_path, monkeypatch):
+    w = _small(tmp_path, monkeypatch)
+    adj, n = w["adj"], w["base"].shape[0]
+    assert adj.shape == (n, 64)
+    for i in range(0, n, 7):
+        row = adj[i]
+        ids = row[row != NONE]
+        assert (row[len(ids):] == NONE).all()
+        assert (ids < n).all() and i not in ids.tolist() and len(set(ids.tolist())) == len(ids)
+    seen = np.zeros(n, bool)
+    seen[w["medoid"]] = True
+    fr = np.array([w["medoid"]])
+    while len(fr):
+        nb = adj[fr].ravel()
+        nb = np.unique(nb[nb != NONE])
+        nb = nb[~seen[nb]]
+        seen[nb] = True
+        fr = nb
+    assert seen.mean() > 0.99
+
+
+def test_ground_truth_and_medoid_match_oracle(tmp_path, monkeypatch):
+    w = _small(tmp_path, monkeypatch)
+    ids, dist = oracle.bruteforce_knn(w["base"], w["queries"], 20)
+    assert (ids == w["gt_ids"]).all() and (dist == w["gt_dist"]).all()
+    assert oracle.medoid(w["base"]) == w["medoid"]
+
+
+def test_deterministic_across_thread_counts(tmp_path):
+    code = ("import workload, hashlib, sys; "
+            "w = workload.clustered_workload(2, n=3000, nq=10, ncomp=3, k=10); "
+            "h = hashlib.sha1(); [h.update(w[f].tobytes()) for f in "
+            "('base','queries','codebook','codes','adj','gt_ids')]; print(h.hexdigest())")
+    out = []
+    for th, sub in (("1", "a"), ("3", "b")):
+        env = dict(os.environ, OMP_NUM_THREADS=th, BANG_WORKLOAD_CACHE=str(tmp_path / sub),
+                   PYTHONPATH=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+        out.append(subprocess.check_output([sys.executable, "-c", code], env=env, text=True))
+    assert out[0] == out[1]

@@ -1,0 +1,260 @@
+"""Seeded synthetic workloads for the BANG search path (arXiv 2401.11324).
+
+The paper measures on SIFT-1B (uint8, d=128), Deep-1B (float, d=96),
+MSSPACEV-1B (int8, d=100) and Text-to-Image-1B (§6.2), searched through a
+Vamana index and PQ codes built beforehand by DiskANN (§1, §6.3).  None of
+those files exist here, so this module stands in for them: seeded Gaussian
+mixtures with the datasets' element types and dimensions, the index the
+search consumes (PQ codebooks and codes, graph, medoid) and exact ground
+truth.  It holds none of the search's arithmetic; the oracle and the CUDA
+path both read what it writes.
+
+Configurations (the recipe of each is in ``CONFIGS``):
+  1  n=10,000 f32 d=128, 16 components, centres ~N(0, 4I), unit variance,
+     100 queries; PQ M=32; Vamana R=32 (built by the oracle in the tests).
+  2  n=1,000,000 u8 d=128, 256 components, centres ~U[0,255]^d; each component
+     low-rank like SIFT descriptors: x = c + A z + 4 e, A (d x 12) with
+     N(0, 20^2/12) entries, z ~ N(0, I_12), e ~ N(0, I_d); rounded and
+     clipped to 0..255; 10,000 queries; PQ M=32; clustered graph R=64.
+Seeds: data 1000+cfg, queries 2000+cfg, PQ 3000+cfg, graph 4000+cfg.
+"""
+import ctypes
+import hashlib
+import os
+import subprocess
+import time
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "indexgen.c")
+_LIB = os.path.join(_HERE, "libwlgen.so")
+NONE = 0xFFFFFFFF
+
+CONFIGS = {
+    1: dict(n=10_000, nq=100, d=128, dtype="f32", ncomp=16, centre="normal", centre_scale=2.0,
+            sigma=1.0, M=32, R=32, Lb=64, alpha=1.2, k=10, L=64),
+    2: dict(n=1_000_000, nq=10_000, d=128, dtype="u8", ncomp=256, centre="uniform255",
+            centre_scale=None, sigma=20.0, rank=12, noise=4.0, M=32, R=64, alpha=1.2, nx=4,
+            nh=32, k=10, L=64),
+}
+
+_DTN = {"u8": np.uint8, "i8": np.int8, "f32": np.float32}
+_DTC = {"u8": 0, "i8": 1, "f32": 2}
+
+
+def build(force=False):
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    subprocess.check_call(["gcc", "-std=c99", "-O3", "-fPIC", "-shared", "-ffp-contract=off",
+                           "-fopenmp", "-Wall", "-o", _LIB + ".tmp", _SRC, "-lm"], cwd=_HERE)
+    os.replace(_LIB + ".tmp", _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(_LIB)
+        vp, u32, u64, i32, f32 = (ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int,
+                                  ctypes.c_float)
+        L.wl_pq_train.argtypes = [vp, u64, u32, u32, vp, vp, u32, vp]
+        L.wl_pq_encode.argtypes = [vp, i32, u64, u32, u32, vp, vp, vp]
+        L.wl_medoids.argtypes = [vp, i32, u32, vp, vp, u32, vp]
+        L.wl_cluster_graph.argtypes = [vp, i32, u32, u64, vp, vp, u32, vp, u32, f32, u32, vp, u32,
+                                       vp, vp]
+        L.wl_cluster_graph.restype = i32
+        L.wl_bruteforce.argtypes = [vp, vp, i32, u64, u32, u32, u32, vp, vp]
+        L.wl_max_threads.restype = i32
+        _lib = L
+    return _lib
+
+
+def _p(a):
+    return ctypes.c_void_p(a.ctypes.data)
+
+
+def chunk_offsets(d, M):
+    """Contiguous PQ subspaces; the first d % M take one extra dimension."""
+    base, extra = divmod(d, M)
+    return np.concatenate([[0], np.cumsum([base + (s < extra) for s in range(M)])]).astype(
+        np.uint32)
+
+
+def _mixture(rng, n, d, centres, sigma, dtype, factors=None, noise=0.0, chunk=131072):
+    """Equal-weight Gaussian mixture; integer types are rounded and clipped.
+    Isotropic components (sigma per dimension), or, with ``factors``
+    (ncomp x d x r), low-rank components x = c + A z + noise*e with
+    z ~ N(0, I_r) and e ~ N(0, I_d)."""
+    lab = rng.integers(0, centres.shape[0], size=n).astype(np.uint32)
+    out = np.empty((n, d), dtype=_DTN[dtype])
+    for i in range(0, n, chunk):
+        j = min(n, i + chunk)
+        if factors is None:
+            x = centres[lab[i:j]] + sigma * rng.standard_normal((j - i, d), dtype=np.float32)
+        else:
+            z = rng.standard_normal((j - i, factors.shape[2]), dtype=np.float32)
+            x = centres[lab[i:j]] + np.einsum("ndr,nr->nd", factors[lab[i:j]], z)
+            x += noise * rng.standard_normal((j - i, d), dtype=np.float32)
+        if dtype == "u8":
+            out[i:j] = np.clip(np.rint(x), 0, 255).astype(np.uint8)
+        elif dtype == "i8":
+            out[i:j] = np.clip(np.rint(x), -128, 127).astype(np.int8)
+        else:
+            out[i:j] = x.astype(np.float32)
+    return out, lab
+
+
+def _centres(rng, c):
+    if c["centre"] == "normal":
+        cen = rng.standard_normal((c["ncomp"], c["d"]), dtype=np.float32) * c["centre_scale"]
+    elif c["centre"] == "uniform255":
+        cen = rng.uniform(0.0, 255.0, size=(c["ncomp"], c["d"])).astype(np.float32)
+    else:
+        raise ValueError(c["centre"])
+    return cen
+
+
+def make_data(cfg, n=None, nq=None, ncomp=None, **over):
+    """Base vectors, their mixture labels and the queries of a configuration
+    (optionally shrunk: n points, nq queries, ncomp components)."""
+    c = dict(CONFIGS[cfg])
+    if n is not None:
+        c["n"] = n
+    if nq is not None:
+        c["nq"] = nq
+    if ncomp is not None:
+        c["ncomp"] = ncomp
+    c.update(over)
+    rng = np.random.default_rng(1000 + cfg)
+    cen = _centres(rng, c)
+    fac = None
+    if c.get("rank", 0):
+        fac = (rng.standard_normal((c["ncomp"], c["d"], c["rank"]), dtype=np.float32) *
+               np.float32(c["sigma"] / np.sqrt(c["rank"])))
+    base, lab = _mixture(rng, c["n"], c["d"], cen, c["sigma"], c["dtype"], fac, c.get("noise", 0))
+    queries, _ = _mixture(np.random.default_rng(2000 + cfg), c["nq"], c["d"], cen, c["sigma"],
+                          c["dtype"], fac, c.get("noise", 0))
+    return dict(cfg=cfg, params=c, base=base, labels=lab, queries=queries)
+
+
+def pq_random_choices(cfg, n, M, train_n):
+    """The PQ training sample and the initial centroids (indices into the
+    sample), drawn with the PQ seed."""
+    rng = np.random.default_rng(3000 + cfg)
+    ns = min(n, train_n)
+    sample = np.sort(rng.choice(n, size=ns, replace=False)).astype(np.uint64)
+    init = np.stack([rng.choice(ns, size=256, replace=False) for _ in range(M)]).astype(np.uint64)
+    return sample, init
+
+
+def build_pq(base, M, sample, init, iters=10):
+    d = base.shape[1]
+    off = chunk_offsets(d, M)
+    Xs = np.ascontiguousarray(base[sample.astype(np.int64)], dtype=np.float32)
+    cb = np.zeros(256 * d, np.float32)
+    init = np.ascontiguousarray(init, np.uint64)
+    lib().wl_pq_train(_p(Xs), Xs.shape[0], d, M, _p(off), _p(init), iters, _p(cb))
+    codes = np.zeros((base.shape[0], M), np.uint8)
+    lib().wl_pq_encode(_p(base), _DTC[_dtname(base)], base.shape[0], d, M, _p(off), _p(cb),
+                       _p(codes))
+    return cb, codes
+
+
+def _dtname(a):
+    return {np.dtype(np.uint8): "u8", np.dtype(np.int8): "i8", np.dtype(np.float32): "f32"}[a.dtype]
+
+
+def medoids_of_groups(base, labels, ng):
+    order = np.argsort(labels, kind="stable").astype(np.uint32)
+    counts = np.bincount(labels, minlength=ng)
+    gstart = np.concatenate([[0], np.cumsum(counts)]).astype(np.uint64)
+    out = np.zeros(ng, np.uint32)
+    lib().wl_medoids(_p(base), _DTC[_dtname(base)], base.shape[1], _p(order), _p(gstart), ng,
+                     _p(out))
+    return order, gstart, out
+
+
+def build_cluster_graph(cfg, base, labels, ng, R, alpha, nx, nh):
+    """Clustered graph (per-cluster exact candidates -> RobustPrune -> reverse
+    edges; nx links per point and nh links per cluster medoid to other
+    clusters' medoids, those clusters drawn with the graph seed)."""
+    n, d = base.shape
+    order, gstart, meds = medoids_of_groups(base, labels, ng)
+    rng = np.random.default_rng(4000 + cfg)
+    own = labels.astype(np.int64)
+    xclu = (own[:, None] + 1 + rng.integers(0, ng - 1, size=(n, nx))) % ng
+    hclu = np.stack([(g + 1 + rng.choice(ng - 1, size=min(nh, ng - 1), replace=False)) % ng
+                     for g in range(ng)]) if nh else np.zeros((ng, 0), np.int64)
+    nh_eff = hclu.shape[1]
+    adj = np.zeros((n, R), np.uint32)
+    xclu = np.ascontiguousarray(xclu, np.uint32)
+    hclu = np.ascontiguousarray(hclu, np.uint32)
+    rc = lib().wl_cluster_graph(_p(base), _DTC[_dtname(base)], d, n, _p(order), _p(gstart), ng,
+                                _p(meds), R, alpha, nx, _p(xclu), nh_eff, _p(hclu), _p(adj))
+    if rc != 0:
+        raise MemoryError("cluster graph build failed (%d)" % rc)
+    _, _, gmed = medoids_of_groups(base, np.zeros(n, np.uint32), 1)
+    return adj, int(gmed[0])
+
+
+def ground_truth(base, queries, k):
+    nq = queries.shape[0]
+    ids = np.zeros((nq, k), np.uint32)
+    dist = np.zeros((nq, k), np.float64)
+    queries = np.ascontiguousarray(queries)
+    lib().wl_bruteforce(_p(base), _p(queries), _DTC[_dtname(base)],
+                        base.shape[0], nq, base.shape[1], k, _p(ids), _p(dist))
+    return ids, dist
+
+
+def cache_dir():
+    d = os.environ.get("BANG_WORKLOAD_CACHE", "/tmp/bang_workload_cache")
+    os.makedirs(d, exist_ok=True)
+    return d
+
+
+def clustered_workload(cfg=2, n=None, nq=None, ncomp=None, k=100, train_n=256_000, verbose=False,
+                       **over):
+    """Data, PQ index, clustered graph and ground truth (k nearest) of a
+    clustered configuration, cached on disk by its parameters."""
+    c = dict(CONFIGS[cfg])
+    c.update(over)
+    n = n or c["n"]
+    nq = nq or c["nq"]
+    ncomp = ncomp or c["ncomp"]
+    key = hashlib.sha1(repr((cfg, n, nq, ncomp, k, train_n, sorted(c.items()),
+                             os.path.getmtime(_SRC) // 1, 1)).encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir(), "cfg%d_%s.npz" % (cfg, key))
+    if os.path.exists(path):
+        z = np.load(path)
+        out = {f: z[f] for f in z.files}
+        out["medoid"] = int(out["medoid"])
+        out["params"] = dict(c, n=n, nq=nq, ncomp=ncomp)
+        return out
+    t0 = time.time()
+    w = make_data(cfg, n=n, nq=nq, ncomp=ncomp, **over)
+    t1 = time.time()
+    sample, init = pq_random_choices(cfg, n, c["M"], train_n)
+    cb, codes = build_pq(w["base"], c["M"], sample, init)
+    t2 = time.time()
+    adj, med = build_cluster_graph(cfg, w["base"], w["labels"], ncomp, c["R"], c["alpha"], c["nx"],
+                                   c["nh"])
+    t3 = time.time()
+    gt_ids, gt_dist = ground_truth(w["base"], w["queries"], k)
+    t4 = time.time()
+    if verbose:
+        print("workload cfg%d n=%d: data %.1fs pq %.1fs graph %.1fs gt %.1fs (threads %d)" % (
+            cfg, n, t1 - t0, t2 - t1, t3 - t2, t4 - t3, lib().wl_max_threads()), flush=True)
+    out = dict(base=w["base"], queries=w["queries"], labels=w["labels"], codebook=cb, codes=codes,
+               adj=adj, medoid=np.int64(med), gt_ids=gt_ids, gt_dist=gt_dist)
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, **out)
+    os.replace(tmp, path)
+    out["medoid"] = med
+    out["params"] = dict(c, n=n, nq=nq, ncomp=ncomp)
+    return out
