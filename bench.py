@@ -1,0 +1,341 @@
+"""Benchmark: queries/s at recall@10 >= 0.9 of the GB300 BANG search path.
+
+Workload: the mid-scale plain-method configuration (n = 1,000,000 uint8
+points, d = 128, 256-component mixture, 10,000 queries, PQ M = 32 on the
+device, clustered graph R = 64 and full vectors in page-locked host memory,
+k = 10).  The worklist size L is the smallest of the sweep
+{16, 24, 32, 48, 64, 96, 128, 160, 192, 256} whose mean recall@10 reaches 0.9
+(ground truth: exact k-NN); a step is one search of the whole batch at that L.
+
+Timed: `--steps` searches of the device-resident batch, each bracketed by CUDA
+events on the launching stream, an L2 flush (a 512 MB write) between them.
+`e2e`: the same search through the C ABI with pinned host queries and
+results (copies inside the timed region).  `cpu_baseline`: the CPU oracle on
+the host cores.  `--impl reference` times that oracle alone.
+
+Multi-GPU (torchrun): every rank searches its own replica (weak scaling, no
+data-path collective); the slowest rank's time is reported.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256)
+TARGET_RECALL = 0.9
+K = 10
+WORKLOAD = "mid-scale plain method: n=1M u8 d=128, 10k queries, PQ M=32, R=64, k=10"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
+    ap.add_argument("--n", type=int, default=None, help="shrink the workload (testing only)")
+    ap.add_argument("--nq", type=int, default=None)
+    ap.add_argument("--ncomp", type=int, default=None)
+    ap.add_argument("--L", type=int, default=None, help="fix L instead of sweeping")
+    ap.add_argument("--bloom-log2", type=int, default=16)
+    ap.add_argument("--cpu-sample", type=int, default=2000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def load_workload(args, rank, world, barrier):
+    import workload
+    kw = dict(n=args.n, nq=args.nq, ncomp=args.ncomp, k=100)
+    if rank == 0:
+        w = workload.clustered_workload(2, verbose=True, **kw)
+    barrier()
+    if rank != 0:
+        w = workload.clustered_workload(2, **kw)
+    return w
+
+
+def recall(found, truth, k=K):
+    f = np.asarray(found)[:, :k].astype(np.int64)
+    t = np.asarray(truth)[:, :k].astype(np.int64)
+    hits = (f[:, :, None] == t[:, None, :]).any(-1).sum()
+    return float(hits) / (k * len(f))
+
+
+class ClockSampler:
+    """nvidia-smi samples (200 ms) during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=subprocess.PIPE,
+                stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for l in self.lines:
+            p = [x.strip() for x in l.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return {}
+
+
+def cpu_baseline(w, L, sample, log2z):
+    """The oracle's search as it stands, OpenMP over queries on all host cores."""
+    import oracle
+    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
+    Q = w["queries"][:sample]
+    t0 = time.perf_counter()
+    r = ix.search(Q, K, L, log2z=log2z)
+    dt = time.perf_counter() - t0
+    return {"value": len(Q) / dt, "unit": "queries/s", "cores": oracle.max_threads(),
+            "kind": "oracle",
+            "sample": "%d of the %d queries at L=%d (same index, same Bloom size); recall@10 %.4f"
+                      % (len(Q), w["queries"].shape[0], L, recall(r["ids"], w["gt_ids"][:len(Q)]))}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import workload  # noqa: F401
+    w = load_workload(args, 0, 1, lambda: None)
+    import oracle
+    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
+    nq = w["queries"].shape[0]
+    L = args.L
+    if L is None:
+        L = L_SWEEP[-1]
+        for Lc in L_SWEEP:
+            r = ix.search(w["queries"][:1000], K, Lc, log2z=args.bloom_log2)
+            if recall(r["ids"], w["gt_ids"][:1000]) >= TARGET_RECALL:
+                L = Lc
+                break
+    sample = min(args.cpu_sample, nq)
+    Q = w["queries"][:sample]
+    for _ in range(args.warmup):
+        ix.search(Q[:200], K, L, log2z=args.bloom_log2)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ix.search(Q, K, L, log2z=args.bloom_log2)
+    dt = time.perf_counter() - t0
+    v = sample * args.steps / dt
+    line = {"metric": "queries/s at recall@10=0.9", "value": v, "unit": "queries/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L, "bloom_log2": args.bloom_log2,
+                       "step": "%d queries (bounded sample of the 10k batch)" % sample},
+            "impl": "reference",
+            "cpu_baseline": {"value": v, "unit": "queries/s", "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": "%d queries per step at L=%d" % (sample, L)},
+            "e2e": {"value": v, "unit": "queries/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    import torch
+    import torch.distributed as dist
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_2401_11324_gb300 as bang
+    w = load_workload(args, rank, world, barrier)
+    nq, d = w["queries"].shape
+    M = 32
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    sptr = stream.cuda_stream
+    q_dev = torch.from_numpy(w["queries"]).to(dev)
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dist_out = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    iters = torch.empty(nq, dtype=torch.int32, device=dev)
+    ndist = torch.empty(nq, dtype=torch.int32, device=dev)
+
+    def search(L, with_stats=False):
+        p = bang.make_params(bloom_log2=args.bloom_log2,
+                             out_iters=iters if with_stats else None,
+                             out_ndist=ndist if with_stats else None)
+        ix.search(q_dev, K, L, ids, dist_out, p, stream=sptr)
+
+    # ---- operating point: smallest L of the sweep with recall@10 >= 0.9
+    sweep = []
+    if args.L is not None:
+        L = args.L
+    else:
+        L = L_SWEEP[-1]
+        for Lc in L_SWEEP:
+            search(Lc)
+            stream.synchronize()
+            rc = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
+            sweep.append({"L": Lc, "recall@10": round(rc, 4)})
+            if rc >= TARGET_RECALL:
+                L = Lc
+                break
+    search(L, with_stats=True)
+    stream.synchronize()
+    rec = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
+    it = iters.cpu().numpy().astype(np.int64)
+    nd = ndist.cpu().numpy().astype(np.int64)
+
+    # ---- algorithmic bytes per launch (one launch = the whole batch)
+    R = w["adj"].shape[1]
+    host_bytes = int(it.sum()) * (R * 4 + d * 1)           # neighbour row + full vector per expansion
+    hbm_bytes = int(nd.sum()) * M + nq * d + nq * K * 8 + 256 * d * 4
+
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    for _ in range(args.warmup):
+        search(L)
+    stream.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_wall = time.perf_counter()
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(s & 0xFF)
+                starts[s].record(stream)
+            search(L)
+            ends[s].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall
+    torch.cuda.synchronize(dev)
+    barrier()
+    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = nq * world * args.steps / (total_ms / 1e3)
+    launch_s = statistics.mean(step_ms) / 1e3
+
+    # ---- end to end through the C ABI: pinned host queries and results
+    q_host = torch.from_numpy(w["queries"]).pin_memory()
+    ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
+    dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        ix.search(q_host, K, L, ids_h, dist_h, bang.make_params(bloom_log2=args.bloom_log2),
+                  stream=sptr)
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ix.search(q_host, K, L, ids_h, dist_h, bang.make_params(bloom_log2=args.bloom_log2),
+                  stream=sptr)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    assert (ids_h.numpy() == ids.cpu().numpy()).all()
+
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_gbs = hbm_bytes / launch_s / 1e9
+    line = {
+        "metric": "queries/s at recall@10=0.9", "value": value, "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "L": L, "recall@10": round(rec, 4), "k": K,
+                   "bloom_log2": args.bloom_log2, "sweep": sweep,
+                   "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
+                   "parallelism": "replica per GPU" if world > 1 else "single GPU",
+                   "l2": "512 MB flush written between timed steps",
+                   "n": int(w["base"].shape[0]), "nq": nq},
+        "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": hbm_gbs / hbm_peak, "traffic": None,
+                     "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                     "algorithmic_bytes_per_launch": hbm_bytes},
+        "host_link": {"achieved_gbs": host_bytes / launch_s / 1e9,
+                      "algorithmic_bytes_per_launch": host_bytes,
+                      "note": "neighbour rows and full vectors read in place from page-locked "
+                              "host memory"},
+        "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d,
+                "d2h_bytes_per_step": nq * K * 8},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": t_wall,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, L, min(args.cpu_sample, nq), args.bloom_log2)
+    ix.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,137 @@
+/*
+ * bang.h -- C ABI of the GB300 implementation of BANG's search path
+ * (Karthik V. et al., "BANG: Billion-Scale Approximate Nearest Neighbor
+ * Search using a Single GPU", arXiv 2401.11324).
+ *
+ * The paper states the problem as: given a graph index G, its medoid s, the
+ * PQ distance table of a batch of queries Q and a worklist size t >= k,
+ * return k approximate nearest neighbours of every query (Alg. 2).  The data
+ * placement follows the paper's schema (§4, first figure): PQ codes on the
+ * GPU; graph and full-precision vectors in host memory.  This ABI loads the
+ * PQ data, registers the host-resident graph and vectors, and searches.
+ *
+ * Conventions for every call:
+ *  - The return value is a bang_status; BANG_OK (0) on success.  On any
+ *    other value, bang_last_error() returns a message for the calling thread
+ *    (valid until that thread's next call into the library).
+ *  - Pointers are plain host or device addresses.  Arguments documented as
+ *    "host or device" are detected with cudaPointerGetAttributes.
+ *  - Outputs are allocated by the caller.
+ *  - A bang_index is not thread-safe: serialise calls on one index.
+ *  - Ids are uint32; 0xFFFFFFFF marks an absent id.  n < 2^31.
+ */
+#ifndef BANG_H
+#define BANG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bang_index bang_index;
+
+typedef enum { BANG_U8 = 0, BANG_I8 = 1, BANG_F32 = 2 } bang_dtype;
+
+typedef enum {
+    BANG_OK = 0,
+    BANG_EINVAL = -1,   /* an argument is out of range or inconsistent */
+    BANG_ENOMEM = -2,   /* a device or pinned-host allocation failed */
+    BANG_ECUDA = -3,    /* a CUDA call failed (message names it) */
+    BANG_ETIMEOUT = -4, /* a bounded device-side wait gave up */
+    BANG_ESTATE = -5    /* the index is missing a step (PQ, graph or vectors) */
+} bang_status;
+
+#define BANG_NONE 0xFFFFFFFFu
+
+/* Optional search settings and statistics.  Zero-initialise, then set what
+ * you need; a NULL pointer to the struct means all defaults. */
+typedef struct bang_search_params {
+    /* Bloom filter size z = 2^bloom_log2 bits per query (§4.3; the paper's
+     * z is a tuned size, §6.3).  10..20; 0 selects 16. */
+    uint32_t bloom_log2;
+    /* Safety cap on expansions per query; 0 selects 8*L + 64.  A query that
+     * reaches it stops, keeps its re-ranked candidates, and reports status
+     * 1 in out_status. */
+    uint32_t iter_cap;
+    /* Optional per-query outputs (nq entries each), host or device:
+     * expansions (the paper's iteration count I, §7.7), status (0 = converged,
+     * 1 = stopped by iter_cap), and PQ distances computed (§4.4). */
+    uint32_t *out_iters;
+    int32_t *out_status;
+    uint32_t *out_ndist;
+    /* Optional visit trace: the expanded node of every iteration, nq rows
+     * of trace_cap entries (host or device); rows are not padded. */
+    uint32_t *trace;
+    uint32_t trace_cap;
+} bang_search_params;
+
+/* Create an empty index bound to CUDA device `device`.  *out receives an
+ * opaque handle owned by the library; free it with bang_destroy. */
+int bang_create(int device, bang_index **out);
+
+/* Load the PQ codebooks and codes (§4: m subspaces of the d dimensions,
+ * 256 centroids each; a point is stored as its m centroid ids) to the device.
+ *   d, M      dimensions and subspaces, 1 <= M <= min(d, 128), d <= 512.
+ *             Subspace s covers dimensions [off_s, off_(s+1)) with
+ *             off_s = s*(d/M) + min(s, d%M): the first d%M subspaces take one
+ *             extra dimension.
+ *   codebook  host, 256*d floats: subspace s occupies the 256*dsub_s floats
+ *             starting at 256*off_s, centroid c at offset c*dsub_s in it.
+ *   codes     host, n*M bytes, row-major.
+ *   n         points, 1 <= n < 2^31.
+ * The library copies both; the caller may free them on return.  Replaces
+ * earlier PQ data and requires graph and vectors to be registered again. */
+int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
+                 const uint8_t *codes, uint64_t n);
+
+/* Register the graph (the Vamana index of §2.2, kept in host memory as in
+ * Alg. 2, where the CPU serves the neighbour lists).
+ *   adj     host, n*R ids (n from bang_load_pq), row i = out-neighbours of i;
+ *           unused slots hold 0xFFFFFFFF.  Ids must be < n, distinct within
+ *           a row and differ from the row's own id.
+ *   R       row width, 1..128.
+ *   medoid  entry point s of the search (§6.3), < n.
+ * Not copied: the memory must stay valid and unchanged until bang_destroy
+ * or the next bang_register_graph.  The library page-locks it with
+ * cudaHostRegister unless it is already page-locked, and the GPU reads it
+ * in place.  Invalid ids return BANG_EINVAL (checked here, not at search). */
+int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_t medoid);
+
+/* Register the full-precision vectors used by the re-rank (§4.8), host
+ * memory, n*d elements of `dtype`, row-major.  Same ownership rule as the
+ * graph.  Queries passed to bang_search have the same element type. */
+int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype);
+
+/* Search a batch of nq queries (Alg. 2; one query per warp): PQ distance
+ * table (§4.1), greedy search from the medoid with a Bloom-filter seen set
+ * (§4.3), PQ distances of new neighbours (§4.4), eager choice of the next
+ * node (§4.5), sorted merge into the worklist of L entries (§4.6, §4.7),
+ * and re-rank of every expanded node by exact squared L2 distance (§4.8).
+ *   queries   host or device, nq*d elements of the registered dtype.
+ *   k, L      1 <= k <= 256, k <= L <= 1024 (L is the paper's t).
+ *   params    may be NULL.
+ *   out_ids   host or device, nq*k ids sorted by (distance, id); padded
+ *             with 0xFFFFFFFF when fewer than k nodes were expanded.
+ *   out_dist  host or device, nq*k squared L2 distances (+inf padding).
+ *   stream    a cudaStream_t (NULL = the legacy default stream).
+ * Work is ordered on `stream`.  If every pointer argument is device memory
+ * the call returns after enqueueing; otherwise it copies through device
+ * staging buffers and returns after the stream has finished.
+ * Ties: distances are compared first, then ids. */
+int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
+                const bang_search_params *params, uint32_t *out_ids, float *out_dist,
+                void *stream);
+
+/* Release device memory, unregister host memory registered by the library
+ * and free the handle.  NULL is accepted. */
+int bang_destroy(bang_index *ix);
+
+/* Message for the last non-OK status returned to the calling thread. */
+const char *bang_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BANG_H */

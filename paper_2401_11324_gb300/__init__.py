@@ -1,0 +1,165 @@
+"""GB300-native BANG search path (arXiv 2401.11324): Python binding.
+
+Argument marshalling over the C ABI declared in ``include/bang.h``; every step
+of the search runs in the CUDA library ``csrc/libbang.so``.  There is no CPU
+fallback: importing this package without the compiled library raises.
+
+Functions carry the C names (``bang_create``, ``bang_load_pq``, ...).  Buffers
+may be numpy arrays (host) or torch tensors (host or CUDA); the library
+detects where each one lives.  ``Index`` is a thin convenience wrapper that
+keeps the host arrays the library reads in place alive.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+BANG_OK, BANG_EINVAL, BANG_ENOMEM, BANG_ECUDA, BANG_ETIMEOUT, BANG_ESTATE = 0, -1, -2, -3, -4, -5
+BANG_U8, BANG_I8, BANG_F32 = 0, 1, 2
+BANG_NONE = 0xFFFFFFFF
+
+_lib = None
+
+
+class BangError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (status %d)" % (msg, code))
+        self.code = code
+
+
+class bang_search_params(ctypes.Structure):
+    _fields_ = [("bloom_log2", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
+                ("out_iters", ctypes.c_void_p), ("out_status", ctypes.c_void_p),
+                ("out_ndist", ctypes.c_void_p), ("trace", ctypes.c_void_p),
+                ("trace_cap", ctypes.c_uint32)]
+
+
+def library_path():
+    return _build.LIB
+
+
+def _load():
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        raise ImportError("libbang.so is not built (%s); run "
+                          "`python -c 'import __graft_entry__ as g; g.build()'`" % _build.LIB)
+    L = ctypes.CDLL(_build.LIB)
+    vp, u32, u64, i32 = ctypes.c_void_p, ctypes.c_uint32, ctypes.c_uint64, ctypes.c_int
+    L.bang_create.argtypes = [i32, ctypes.POINTER(vp)]
+    L.bang_load_pq.argtypes = [vp, u32, u32, vp, vp, u64]
+    L.bang_register_graph.argtypes = [vp, vp, u32, u32]
+    L.bang_register_vectors.argtypes = [vp, vp, i32]
+    L.bang_search.argtypes = [vp, vp, u32, u32, u32, ctypes.POINTER(bang_search_params), vp, vp,
+                              vp]
+    L.bang_destroy.argtypes = [vp]
+    L.bang_last_error.restype = ctypes.c_char_p
+    for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
+              "bang_search", "bang_destroy"):
+        getattr(L, f).restype = i32
+    _lib = L
+    return L
+
+
+def lib():
+    return _load()
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays passed to the library must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    if isinstance(x, int):
+        return ctypes.c_void_p(x)
+    raise TypeError("unsupported buffer type %r" % type(x))
+
+
+def _check(rc):
+    if rc != BANG_OK:
+        raise BangError(rc, lib().bang_last_error().decode(errors="replace"))
+    return rc
+
+
+def bang_last_error():
+    return lib().bang_last_error().decode(errors="replace")
+
+
+def bang_create(device=0):
+    h = ctypes.c_void_p()
+    _check(lib().bang_create(device, ctypes.byref(h)))
+    return h
+
+
+def bang_load_pq(ix, d, M, codebook, codes, n):
+    return _check(lib().bang_load_pq(ix, d, M, _ptr(codebook), _ptr(codes), n))
+
+
+def bang_register_graph(ix, adj, R, medoid):
+    return _check(lib().bang_register_graph(ix, _ptr(adj), R, medoid))
+
+
+def bang_register_vectors(ix, base, dtype):
+    return _check(lib().bang_register_vectors(ix, _ptr(base), dtype))
+
+
+def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
+                trace=None, trace_cap=0):
+    return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
+                              _ptr(out_ndist), _ptr(trace), trace_cap)
+
+
+def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
+    p = ctypes.byref(params) if params is not None else None
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    return _check(lib().bang_search(ix, _ptr(queries), nq, k, L, p, _ptr(out_ids),
+                                    _ptr(out_dist), s))
+
+
+def bang_destroy(ix):
+    return _check(lib().bang_destroy(ix))
+
+
+_DTYPES = {np.dtype(np.uint8): BANG_U8, np.dtype(np.int8): BANG_I8,
+           np.dtype(np.float32): BANG_F32}
+
+
+class Index:
+    """Owns a bang_index and the host arrays it reads in place."""
+
+    def __init__(self, base, codebook, codes, adj, medoid, M, device=0):
+        self.base = np.ascontiguousarray(base)
+        self.n, self.d = self.base.shape
+        self.M = M
+        self._codebook = np.ascontiguousarray(codebook, np.float32)
+        self._codes = np.ascontiguousarray(codes, np.uint8).reshape(self.n, M)
+        self.adj = np.ascontiguousarray(adj, np.uint32).reshape(self.n, -1)
+        self.R = self.adj.shape[1]
+        self.medoid = int(medoid)
+        self.dtype = _DTYPES[self.base.dtype]
+        self.h = bang_create(device)
+        bang_load_pq(self.h, self.d, M, self._codebook, self._codes, self.n)
+        bang_register_graph(self.h, self.adj, self.R, self.medoid)
+        bang_register_vectors(self.h, self.base, self.dtype)
+
+    def search(self, queries, k, L, out_ids, out_dist, params=None, stream=None):
+        nq = queries.shape[0]
+        return bang_search(self.h, queries, nq, k, L, params, out_ids, out_dist, stream)
+
+    def close(self):
+        if self.h is not None:
+            bang_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,440 @@
+// C ABI of the GB300 BANG search path (declarations and contracts in
+// include/bang.h).  Host-side responsibilities: argument and index
+// validation, device copies of the PQ data, page-locking and mapping of the
+// host-resident graph and vectors (read in place by the kernel, Alg. 2's
+// FetchNeighbors), staging of host queries and results, and the launch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "bang.h"
+#include "search_kernel.cuh"
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CUDA_TRY(call)                                                                        \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            int code_ = (e_ == cudaErrorMemoryAllocation) ? BANG_ENOMEM : BANG_ECUDA;        \
+            return fail(code_, "%s failed: %s", #call, cudaGetErrorString(e_));             \
+        }                                                                                     \
+    } while (0)
+
+// A host range the GPU reads in place.  Registered by the library unless the
+// caller's memory is already page-locked (or device-accessible already).
+struct HostView {
+    const void *host = nullptr;
+    const void *dev = nullptr;
+    bool registered_here = false;
+
+    void release()
+    {
+        if (registered_here && host) cudaHostUnregister(const_cast<void *>(host));
+        host = dev = nullptr;
+        registered_here = false;
+    }
+};
+
+int map_host(const void *p, size_t bytes, HostView &out)
+{
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        at.type = cudaMemoryTypeUnregistered;
+    }
+    out.host = p;
+    out.registered_here = false;
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
+        out.dev = p;
+        return BANG_OK;
+    }
+    if (at.type == cudaMemoryTypeUnregistered) {
+        e = cudaHostRegister(const_cast<void *>(p), bytes,
+                             cudaHostRegisterMapped | cudaHostRegisterReadOnly);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            // some systems refuse the read-only flag; retry without it
+            e = cudaHostRegister(const_cast<void *>(p), bytes, cudaHostRegisterMapped);
+        }
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? BANG_ENOMEM : BANG_ECUDA,
+                        "cudaHostRegister of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        }
+        out.registered_here = true;
+    }
+    void *dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, const_cast<void *>(p), 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (out.registered_here) cudaHostUnregister(const_cast<void *>(p));
+        out.registered_here = false;
+        return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+    }
+    out.dev = dp;
+    return BANG_OK;
+}
+
+bool is_device_accessible(const void *p)
+{
+    if (!p) return false;
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+size_t elem_size(int dt) { return dt == BANG_F32 ? 4 : 1; }
+
+// Device buffer that only grows.
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+    cudaError_t ensure(size_t want)
+    {
+        if (want <= bytes) return cudaSuccess;
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+        cudaError_t e = cudaMalloc(&p, want);
+        if (e == cudaSuccess) bytes = want;
+        return e;
+    }
+    void release()
+    {
+        if (p) cudaFree(p);
+        p = nullptr;
+        bytes = 0;
+    }
+};
+
+}  // namespace
+
+struct bang_index {
+    int device = 0;
+    uint32_t d = 0, M = 0, Mpad = 0, R = 0, medoid = 0;
+    uint64_t n = 0;
+    int dtype = -1;
+    float *codebook = nullptr;
+    uint32_t *off = nullptr;
+    uint8_t *codes = nullptr;
+    HostView adj, base;
+    bool have_pq = false, have_graph = false, have_vectors = false;
+    DevBuf staging;
+};
+
+namespace {
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev)
+    {
+        if (cudaGetDevice(&prev) == cudaSuccess && cudaSetDevice(dev) == cudaSuccess) ok = true;
+        else cudaGetLastError();
+    }
+    ~DeviceGuard()
+    {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+std::vector<uint32_t> chunk_offsets(uint32_t d, uint32_t M)
+{
+    std::vector<uint32_t> off(M + 1);
+    uint32_t base = d / M, extra = d % M;
+    off[0] = 0;
+    for (uint32_t s = 0; s < M; ++s) off[s + 1] = off[s] + base + (s < extra ? 1u : 0u);
+    return off;
+}
+
+// Check every row of the adjacency: ids < n, no self loop, no duplicate.
+// Rows are split across host threads.
+bool validate_graph(const uint32_t *adj, uint64_t n, uint32_t R, uint64_t *bad_row)
+{
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<uint64_t> bad(nt, UINT64_MAX);
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t) {
+        th.emplace_back([&, t]() {
+            uint32_t tmp[bang::kMaxR];
+            uint64_t lo = n * t / nt, hi = n * (t + 1) / nt;
+            for (uint64_t i = lo; i < hi; ++i) {
+                const uint32_t *row = adj + i * R;
+                uint32_t m = 0;
+                for (uint32_t r = 0; r < R; ++r) {
+                    uint32_t v = row[r];
+                    if (v == bang::kNone) continue;
+                    if (v >= n || v == i) { bad[t] = i; return; }
+                    tmp[m++] = v;
+                }
+                std::sort(tmp, tmp + m);
+                for (uint32_t r = 1; r < m; ++r)
+                    if (tmp[r] == tmp[r - 1]) { bad[t] = i; return; }
+            }
+        });
+    }
+    for (auto &x : th) x.join();
+    for (unsigned t = 0; t < nt; ++t)
+        if (bad[t] != UINT64_MAX) { *bad_row = bad[t]; return false; }
+    return true;
+}
+
+template <int DT> int set_smem_attr()
+{
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, []() {
+        err = cudaFuncSetAttribute(bang::search_kernel<DT>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    });
+    return err == cudaSuccess ? BANG_OK
+                              : fail(BANG_ECUDA, "cudaFuncSetAttribute failed: %s",
+                                     cudaGetErrorString(err));
+}
+
+template <int DT> int launch(const bang::SearchArgs &a, size_t smem, cudaStream_t st)
+{
+    int rc = set_smem_attr<DT>();
+    if (rc) return rc;
+    bang::search_kernel<DT><<<a.nq, 32, smem, st>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(e));
+    return BANG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *bang_last_error(void) { return g_err.c_str(); }
+
+int bang_create(int device, bang_index **out)
+{
+    if (!out) return fail(BANG_EINVAL, "bang_create: out is NULL");
+    *out = nullptr;
+    int count = 0;
+    CUDA_TRY(cudaGetDeviceCount(&count));
+    if (device < 0 || device >= count)
+        return fail(BANG_EINVAL, "bang_create: device %d not in [0, %d)", device, count);
+    bang_index *ix = new (std::nothrow) bang_index();
+    if (!ix) return fail(BANG_ENOMEM, "bang_create: out of host memory");
+    ix->device = device;
+    *out = ix;
+    return BANG_OK;
+}
+
+int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
+                 const uint8_t *codes, uint64_t n)
+{
+    if (!ix || !codebook || !codes) return fail(BANG_EINVAL, "bang_load_pq: NULL argument");
+    if (d == 0 || d > (uint32_t)bang::kMaxD)
+        return fail(BANG_EINVAL, "bang_load_pq: d=%u outside 1..%d", d, bang::kMaxD);
+    if (M == 0 || M > d || M > (uint32_t)bang::kMaxM)
+        return fail(BANG_EINVAL, "bang_load_pq: M=%u outside 1..min(d, %d)", M, bang::kMaxM);
+    if (n == 0 || n >= (1ull << 31)) return fail(BANG_EINVAL, "bang_load_pq: n=%llu outside 1..2^31-1",
+                                                 (unsigned long long)n);
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    if (ix->codebook) cudaFree(ix->codebook);
+    if (ix->off) cudaFree(ix->off);
+    if (ix->codes) cudaFree(ix->codes);
+    ix->codebook = nullptr; ix->off = nullptr; ix->codes = nullptr;
+    ix->adj.release();
+    ix->base.release();
+    ix->have_pq = ix->have_graph = ix->have_vectors = false;
+
+    const uint32_t Mpad = (M + 15u) & ~15u;
+    std::vector<uint32_t> off = chunk_offsets(d, M);
+    CUDA_TRY(cudaMalloc(&ix->codebook, sizeof(float) * 256u * d));
+    CUDA_TRY(cudaMalloc(&ix->off, sizeof(uint32_t) * (M + 1)));
+    CUDA_TRY(cudaMalloc(&ix->codes, (size_t)n * Mpad));
+    CUDA_TRY(cudaMemcpy(ix->codebook, codebook, sizeof(float) * 256u * d, cudaMemcpyHostToDevice));
+    CUDA_TRY(cudaMemcpy(ix->off, off.data(), sizeof(uint32_t) * (M + 1), cudaMemcpyHostToDevice));
+    if (Mpad != M) CUDA_TRY(cudaMemset(ix->codes, 0, (size_t)n * Mpad));
+    CUDA_TRY(cudaMemcpy2D(ix->codes, Mpad, codes, M, M, n, cudaMemcpyHostToDevice));
+    ix->d = d; ix->M = M; ix->Mpad = Mpad; ix->n = n;
+    ix->have_pq = true;
+    return BANG_OK;
+}
+
+int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_t medoid)
+{
+    if (!ix || !adj) return fail(BANG_EINVAL, "bang_register_graph: NULL argument");
+    if (!ix->have_pq) return fail(BANG_ESTATE, "bang_register_graph: load the PQ data first");
+    if (R == 0 || R > (uint32_t)bang::kMaxR)
+        return fail(BANG_EINVAL, "bang_register_graph: R=%u outside 1..%d", R, bang::kMaxR);
+    if (medoid >= ix->n) return fail(BANG_EINVAL, "bang_register_graph: medoid %u >= n", medoid);
+    uint64_t bad = 0;
+    if (!validate_graph(adj, ix->n, R, &bad))
+        return fail(BANG_EINVAL, "bang_register_graph: row %llu has an id >= n, a self loop or a "
+                    "duplicate", (unsigned long long)bad);
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    ix->adj.release();
+    ix->have_graph = false;
+    int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->adj);
+    if (rc) return rc;
+    ix->R = R;
+    ix->medoid = medoid;
+    ix->have_graph = true;
+    return BANG_OK;
+}
+
+int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype)
+{
+    if (!ix || !base) return fail(BANG_EINVAL, "bang_register_vectors: NULL argument");
+    if (!ix->have_pq) return fail(BANG_ESTATE, "bang_register_vectors: load the PQ data first");
+    if (dtype != BANG_U8 && dtype != BANG_I8 && dtype != BANG_F32)
+        return fail(BANG_EINVAL, "bang_register_vectors: unknown dtype %d", (int)dtype);
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    ix->base.release();
+    ix->have_vectors = false;
+    int rc = map_host(base, (size_t)ix->n * ix->d * elem_size(dtype), ix->base);
+    if (rc) return rc;
+    ix->dtype = dtype;
+    ix->have_vectors = true;
+    return BANG_OK;
+}
+
+int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
+                const bang_search_params *params, uint32_t *out_ids, float *out_dist,
+                void *stream)
+{
+    if (!ix) return fail(BANG_EINVAL, "bang_search: index is NULL");
+    if (!ix->have_pq || !ix->have_graph || !ix->have_vectors)
+        return fail(BANG_ESTATE, "bang_search: PQ data, graph and vectors must all be set");
+    if (k == 0 || k > (uint32_t)bang::kMaxK)
+        return fail(BANG_EINVAL, "bang_search: k=%u outside 1..%d", k, bang::kMaxK);
+    if (L < k || L > (uint32_t)bang::kMaxL)
+        return fail(BANG_EINVAL, "bang_search: L=%u must satisfy k <= L <= %d", L, bang::kMaxL);
+    if (nq == 0) return BANG_OK;
+    if (!queries || !out_ids || !out_dist) return fail(BANG_EINVAL, "bang_search: NULL buffer");
+    bang_search_params p;
+    std::memset(&p, 0, sizeof p);
+    if (params) p = *params;
+    uint32_t log2z = p.bloom_log2 ? p.bloom_log2 : 16u;
+    if (log2z < 10 || log2z > 20)
+        return fail(BANG_EINVAL, "bang_search: bloom_log2=%u outside 10..20", log2z);
+    uint32_t cap = p.iter_cap ? p.iter_cap : 8u * L + 64u;
+    if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search: trace_cap is 0");
+
+    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d);
+    if (lay.total > 227u * 1024u)
+        return fail(BANG_EINVAL, "bang_search: %u bytes of shared memory per query exceed 227 KB "
+                    "(reduce L, k, M or bloom_log2)", lay.total);
+
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+    // Host buffers are staged through one device allocation.
+    const size_t qbytes = (size_t)nq * ix->d * elem_size(ix->dtype);
+    struct Slot { const void *user; size_t bytes; bool in; size_t off; bool dev; };
+    Slot slots[8] = {
+        {queries, qbytes, true, 0, false},
+        {out_ids, (size_t)nq * k * 4, false, 0, false},
+        {out_dist, (size_t)nq * k * 4, false, 0, false},
+        {p.out_iters, (size_t)nq * 4, false, 0, false},
+        {p.out_status, (size_t)nq * 4, false, 0, false},
+        {p.out_ndist, (size_t)nq * 4, false, 0, false},
+        {p.trace, (size_t)nq * p.trace_cap * 4, false, 0, false},
+        {nullptr, 0, false, 0, false}};
+    size_t need = 0;
+    bool any_host = false;
+    for (int i = 0; i < 7; ++i) {
+        Slot &s = slots[i];
+        if (!s.user) continue;
+        s.dev = is_device_accessible(s.user);
+        if (!s.dev) {
+            s.off = need;
+            need += (s.bytes + 255) & ~size_t(255);
+            any_host = true;
+        }
+    }
+    if (need) CUDA_TRY(ix->staging.ensure(need));
+    auto dptr = [&](int i) -> void * {
+        Slot &s = slots[i];
+        if (!s.user) return nullptr;
+        return s.dev ? const_cast<void *>(s.user) : static_cast<char *>(ix->staging.p) + s.off;
+    };
+    if (!slots[0].dev) CUDA_TRY(cudaMemcpyAsync(dptr(0), queries, qbytes, cudaMemcpyHostToDevice, st));
+
+    bang::SearchArgs a;
+    a.queries = dptr(0);
+    a.codebook = ix->codebook;
+    a.off = ix->off;
+    a.codes = ix->codes;
+    a.adj = static_cast<const uint32_t *>(ix->adj.dev);
+    a.base = ix->base.dev;
+    a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
+    a.medoid = ix->medoid;
+    a.nq = nq; a.k = k; a.L = L; a.log2z = log2z; a.iter_cap = cap;
+    a.out_ids = static_cast<uint32_t *>(dptr(1));
+    a.out_dist = static_cast<float *>(dptr(2));
+    a.out_iters = static_cast<uint32_t *>(dptr(3));
+    a.out_status = static_cast<int32_t *>(dptr(4));
+    a.out_ndist = static_cast<uint32_t *>(dptr(5));
+    a.trace = static_cast<uint32_t *>(dptr(6));
+    a.trace_cap = p.trace_cap;
+
+    int rc;
+    switch (ix->dtype) {
+    case BANG_U8: rc = launch<0>(a, lay.total, st); break;
+    case BANG_I8: rc = launch<1>(a, lay.total, st); break;
+    default: rc = launch<2>(a, lay.total, st); break;
+    }
+    if (rc) return rc;
+    for (int i = 1; i < 7; ++i) {
+        Slot &s = slots[i];
+        if (s.user && !s.dev)
+            CUDA_TRY(cudaMemcpyAsync(const_cast<void *>(s.user), dptr(i), s.bytes,
+                                     cudaMemcpyDeviceToHost, st));
+    }
+    if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
+    return BANG_OK;
+}
+
+int bang_destroy(bang_index *ix)
+{
+    if (!ix) return BANG_OK;
+    {
+        DeviceGuard g(ix->device);
+        if (ix->codebook) cudaFree(ix->codebook);
+        if (ix->off) cudaFree(ix->off);
+        if (ix->codes) cudaFree(ix->codes);
+        ix->adj.release();
+        ix->base.release();
+        ix->staging.release();
+    }
+    delete ix;
+    return BANG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,58 @@
+"""The C-ABI library builds, loads and exports every entry point declared in
+include/bang.h; argument checks that need no GPU behave as documented."""
+import ctypes
+import os
+import re
+import subprocess
+
+import pytest
+
+import paper_2401_11324_gb300 as bang
+from paper_2401_11324_gb300 import build as bbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for f in os.listdir(os.path.join(ROOT, "include")):
+        if f.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", f)).read()
+            names |= set(re.findall(r"^\s*(?:int|const char \*)\s*(bang_\w+)\s*\(", src, re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    bbuild.build()
+    return bang.lib()
+
+
+def test_header_declares_the_api():
+    assert {"bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
+            "bang_search", "bang_destroy", "bang_last_error"} <= declared_symbols()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    out = subprocess.check_output(["nm", "-D", "--defined-only", bbuild.LIB], text=True)
+    exported = {l.split()[-1] for l in out.splitlines() if l.strip()}
+    missing = declared_symbols() - exported
+    assert not missing, missing
+    for name in declared_symbols():
+        assert hasattr(lib, name)
+
+
+def test_built_for_sm_103a(lib):
+    out = subprocess.check_output(["cuobjdump", "--list-elf", bbuild.LIB], text=True)
+    assert "sm_103a" in out
+
+
+def test_null_and_range_checks_without_gpu(lib):
+    ids = (ctypes.c_uint32 * 4)()
+    dist = (ctypes.c_float * 4)()
+    q = (ctypes.c_float * 4)()
+    assert lib.bang_search(None, q, 1, 1, 1, None, ids, dist, None) == bang.BANG_EINVAL
+    assert b"NULL" in lib.bang_last_error()
+    assert lib.bang_destroy(None) == bang.BANG_OK
+    assert lib.bang_create(0, None) == bang.BANG_EINVAL
+    assert lib.bang_load_pq(None, 4, 2, None, None, 1) == bang.BANG_EINVAL

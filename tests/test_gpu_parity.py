@@ -1,0 +1,174 @@
+"""GPU path against the oracle, element by element, through the C ABI.
+
+FP32 form: ids, visit sequence, iteration counts and distance-computation
+counts are bit-exact; distances agree within 1e-5 relative (they are in fact
+computed in the same order and compared exactly where the test says so)."""
+import numpy as np
+import pytest
+
+import oracle
+from tests import cases
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2401_11324_gb300 as bang  # noqa: E402
+
+RTOL = 1e-5
+
+
+def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None):
+    M = M or w["M"]
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
+    nq = Q.shape[0]
+    dev = "cpu" if host else "cuda"
+    if host:
+        q = np.ascontiguousarray(Q)
+    else:
+        q = torch.from_numpy(np.ascontiguousarray(Q)).to(dev)
+    ids = torch.empty((nq, k), dtype=torch.int32, device=dev)
+    dist = torch.empty((nq, k), dtype=torch.float32, device=dev)
+    iters = torch.empty(nq, dtype=torch.int32, device=dev)
+    status = torch.empty(nq, dtype=torch.int32, device=dev)
+    ndist = torch.empty(nq, dtype=torch.int32, device=dev)
+    trace = torch.zeros((nq, max(trace_cap, 1)), dtype=torch.int32, device=dev)
+    p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
+                         out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap)
+    ix.search(q, k, L, ids, dist, p)
+    torch.cuda.synchronize()
+    out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
+               iters=iters.cpu().numpy().view(np.uint32), status=status.cpu().numpy(),
+               ndist=ndist.cpu().numpy().view(np.uint32), trace=trace.cpu().numpy().view(np.uint32))
+    ix.close()
+    return out
+
+
+def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None):
+    M = M or w["M"]
+    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
+    return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap)
+
+
+def assert_parity(g, o, trace_cap=0, exact_dist=True):
+    assert (g["ids"] == o["ids"]).all(), np.argwhere(g["ids"] != o["ids"])[:5]
+    assert (g["iters"] == o["iters"]).all()
+    assert (g["status"] == o["status"]).all()
+    assert (g["ndist"].astype(np.uint64) == o["ndist"]).all()
+    fin = np.isfinite(o["dist"])
+    assert (np.isfinite(g["dist"]) == fin).all()
+    if exact_dist:
+        assert (g["dist"][fin] == o["dist"][fin]).all()
+    else:
+        np.testing.assert_allclose(g["dist"][fin], o["dist"][fin], rtol=RTOL)
+    if trace_cap:
+        for i in range(len(g["iters"])):
+            m = min(int(o["iters"][i]), trace_cap)
+            assert (g["trace"][i, :m] == o["trace"][i, :m]).all()
+
+
+@pytest.fixture(scope="module")
+def cfg1():
+    return cases.config1()
+
+
+def test_config1_fp32_bit_exact(cfg1):
+    Q = cfg1["queries"]
+    g = gpu_search(cfg1, Q, 10, 64, trace_cap=1024)
+    o = oracle_search(cfg1, Q, 10, 64, trace_cap=1024)
+    assert_parity(g, o, trace_cap=1024)
+
+
+@pytest.mark.parametrize("k,L,log2z", [(1, 1, 16), (10, 16, 12), (10, 64, 16), (32, 200, 18),
+                                       (100, 256, 20)])
+def test_config1_sweep(cfg1, k, L, log2z):
+    Q = cfg1["queries"][:37]                           # ragged batch
+    assert_parity(gpu_search(cfg1, Q, k, L, log2z), oracle_search(cfg1, Q, k, L, log2z))
+
+
+@pytest.fixture(scope="module")
+def u8small():
+    return cases.clustered(n=20_000, nq=300, ncomp=8)
+
+
+def test_clustered_u8_bit_exact(u8small):
+    Q = u8small["queries"]
+    for k, L in ((10, 32), (10, 128)):
+        g = gpu_search(u8small, Q, k, L, trace_cap=600)
+        o = oracle_search(u8small, Q, k, L, trace_cap=600)
+        assert_parity(g, o, trace_cap=600)
+        assert oracle.recall_at_k(g["ids"], u8small["gt_ids"], 10) > 0.5
+
+
+def test_host_buffers_match_device_buffers(u8small):
+    Q = u8small["queries"][:65]
+    g_dev = gpu_search(u8small, Q, 10, 48)
+    g_host = gpu_search(u8small, Q, 10, 48, host=True)
+    for f in ("ids", "dist", "iters", "status", "ndist"):
+        assert (g_dev[f] == g_host[f]).all()
+
+
+def test_int8_uneven_subspaces():
+    w = cases.clustered(n=8_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40,
+                        centre="uniform100")
+    Q = w["queries"]
+    assert_parity(gpu_search(w, Q, 10, 40, trace_cap=200), oracle_search(w, Q, 10, 40, trace_cap=200),
+                  trace_cap=200)
+
+
+def test_f32_d96_M48_R68():
+    w = cases.clustered(n=6_000, nq=50, ncomp=4, dtype="f32", d=96, M=48, R=68,
+                        centre="uniform255")
+    Q = w["queries"]
+    assert_parity(gpu_search(w, Q, 10, 64, trace_cap=300), oracle_search(w, Q, 10, 64, trace_cap=300),
+                  trace_cap=300)
+
+
+def test_iteration_cap_and_single_query(u8small):
+    Q = u8small["queries"][:1]
+    g = gpu_search(u8small, Q, 5, 64, iter_cap=7)
+    o = oracle_search(u8small, Q, 5, 64, iter_cap=7)
+    assert g["status"][0] == 1 and g["iters"][0] == 7
+    assert_parity(g, o)
+
+
+def test_isolated_medoid_pads_results(u8small):
+    w = dict(u8small)
+    adj = w["adj"].copy()
+    adj[w["medoid"]] = bang.BANG_NONE
+    w["adj"] = adj
+    Q = w["queries"][:3]
+    g = gpu_search(w, Q, 4, 8)
+    assert (g["ids"][:, 0] == w["medoid"]).all() and (g["ids"][:, 1:] == bang.BANG_NONE).all()
+    assert np.isinf(g["dist"][:, 1:]).all() and (g["iters"] == 1).all()
+
+
+def test_rejects_bad_arguments(u8small):
+    w = u8small
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    q = torch.from_numpy(w["queries"][:2]).cuda()
+    ids = torch.empty((2, 10), dtype=torch.int32, device="cuda")
+    dist = torch.empty((2, 10), dtype=torch.float32, device="cuda")
+    with pytest.raises(bang.BangError) as e:
+        ix.search(q, 10, 5, ids, dist)              # L < k
+    assert e.value.code == bang.BANG_EINVAL
+    with pytest.raises(bang.BangError):
+        ix.search(q, 10, 64, ids, dist, bang.make_params(bloom_log2=30))
+    bad = w["adj"].copy()
+    bad[5, 0] = w["base"].shape[0] + 3
+    h = bang.bang_create(0)
+    bang.bang_load_pq(h, w["base"].shape[1], w["M"], w["codebook"], w["codes"], w["base"].shape[0])
+    with pytest.raises(bang.BangError) as e:
+        bang.bang_register_graph(h, bad, bad.shape[1], w["medoid"])
+    assert e.value.code == bang.BANG_EINVAL
+    bang.bang_destroy(h)
+    ix.close()
+
+
+def test_empty_batch(u8small):
+    w = u8small
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    q = torch.empty((0, w["base"].shape[1]), dtype=torch.uint8, device="cuda")
+    ids = torch.empty((0, 10), dtype=torch.int32, device="cuda")
+    dist = torch.empty((0, 10), dtype=torch.float32, device="cuda")
+    ix.search(q, 10, 32, ids, dist)
+    ix.close()

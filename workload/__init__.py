@@ -114,6 +114,8 @@ def _centres(rng, c):
         cen = rng.standard_normal((c["ncomp"], c["d"]), dtype=np.float32) * c["centre_scale"]
     elif c["centre"] == "uniform255":
         cen = rng.uniform(0.0, 255.0, size=(c["ncomp"], c["d"])).astype(np.float32)
+    elif c["centre"] == "uniform100":
+        cen = rng.uniform(-100.0, 100.0, size=(c["ncomp"], c["d"])).astype(np.float32)
     else:
         raise ValueError(c["centre"])
     return cen
