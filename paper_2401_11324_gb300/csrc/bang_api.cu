@@ -205,27 +205,31 @@ bool validate_graph(const uint32_t *adj, uint64_t n, uint32_t R, uint64_t *bad_r
     return true;
 }
 
-template <int DT> int set_smem_attr()
+template <int DT, int RPL, int DCH> int launch_one(const bang::SearchArgs &a, size_t smem,
+                                                  cudaStream_t st)
 {
     static std::once_flag once;
     static cudaError_t err = cudaSuccess;
     std::call_once(once, []() {
-        err = cudaFuncSetAttribute(bang::search_kernel<DT>,
+        err = cudaFuncSetAttribute(bang::search_kernel<DT, RPL, DCH>,
                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     });
-    return err == cudaSuccess ? BANG_OK
-                              : fail(BANG_ECUDA, "cudaFuncSetAttribute failed: %s",
-                                     cudaGetErrorString(err));
-}
-
-template <int DT> int launch(const bang::SearchArgs &a, size_t smem, cudaStream_t st)
-{
-    int rc = set_smem_attr<DT>();
-    if (rc) return rc;
-    bang::search_kernel<DT><<<a.nq, 32, smem, st>>>(a);
+    if (err != cudaSuccess)
+        return fail(BANG_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(err));
+    bang::search_kernel<DT, RPL, DCH><<<a.nq, 32, smem, st>>>(a);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(e));
     return BANG_OK;
+}
+
+// Neighbours per lane (R <= 32, 64, 128) and 128-dimension chunks per lane
+// (d <= 128, 512) are compile-time, so no lane works on padding.
+template <int DT> int launch_dt(const bang::SearchArgs &a, size_t smem, cudaStream_t st)
+{
+    const bool narrow = a.d <= 128;
+    if (a.R <= 32) return narrow ? launch_one<DT, 1, 1>(a, smem, st) : launch_one<DT, 1, 4>(a, smem, st);
+    if (a.R <= 64) return narrow ? launch_one<DT, 2, 1>(a, smem, st) : launch_one<DT, 2, 4>(a, smem, st);
+    return narrow ? launch_one<DT, 4, 1>(a, smem, st) : launch_one<DT, 4, 4>(a, smem, st);
 }
 
 }  // namespace
@@ -404,11 +408,17 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.trace = static_cast<uint32_t *>(dptr(6));
     a.trace_cap = p.trace_cap;
 
+    {
+        // 4-element vector loads need rows that start on 16-byte boundaries
+        const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
+        const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
+        a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) && (ba % 16 == 0) ? 1u : 0u;
+    }
     int rc;
     switch (ix->dtype) {
-    case BANG_U8: rc = launch<0>(a, lay.total, st); break;
-    case BANG_I8: rc = launch<1>(a, lay.total, st); break;
-    default: rc = launch<2>(a, lay.total, st); break;
+    case BANG_U8: rc = launch_dt<0>(a, lay.total, st); break;
+    case BANG_I8: rc = launch_dt<1>(a, lay.total, st); break;
+    default: rc = launch_dt<2>(a, lay.total, st); break;
     }
     if (rc) return rc;
     for (int i = 1; i < 7; ++i) {

@@ -3,26 +3,27 @@
 // One warp (a 32-thread CTA) runs the whole search of one query: the PQ
 // distance table (§4.1), the Bloom-filter seen set (§4.3), the worklist and
 // the re-rank candidates all live in shared memory, so the only global
-// traffic per iteration is the neighbour list and full vector of the expanded
+// traffic per iteration is the neighbour row and full vector of the expanded
 // node (read in place from page-locked host memory, Alg. 2 "FetchNeighbors")
 // and one PQ code row per new neighbour (HBM, §4.4).
 //
 // The paper splits every iteration into separate kernels with one CTA per
 // query and keeps the table and filter in global memory; here the iteration
-// loop stays inside one CTA, and the eager next-node choice of §4.5 becomes
+// loop stays inside one warp, and the eager next-node choice of §4.5 becomes
 // a software prefetch: the next node's lists are requested right after the
-// distances are known, and arrive while the warp merges the worklist.
+// distances are known and arrive while the warp merges the worklist.
 //
 // Arithmetic order (fixed so that results are reproducible bit for bit):
 //  - table entry T[s][c]: fmaf(q_j - C_j, q_j - C_j, acc) over the subspace's
 //    dimensions in ascending j, from 0;
 //  - PQ distance: eight partial sums over subspaces s = r (mod 8), in
 //    ascending s, then p_r += p_(r^4), p_r += p_(r^2), p_r += p_(r^1);
-//  - exact distance: 32 partial sums, one per lane, lane r owning the
-//    dimensions j with (j/4) mod 32 = r in ascending j (fmaf), then a
-//    butterfly over xor distances 16, 8, 4, 2, 1; integer data sums exactly;
-//  - ordering keys are (distance, id), distance compared as FP32 (integer
-//    exact distances as unsigned integers).
+//  - exact distance: 32 partial sums, lane r owning the dimensions j with
+//    (j/4) mod 32 = r, each in ascending j (fmaf), then a butterfly over xor
+//    distances 16, 8, 4, 2, 1; integer data is summed exactly;
+//  - ordering keys are (distance, id): FP32 distances compared through their
+//    bit patterns (all distances are >= +0), integer exact distances as
+//    unsigned integers.
 #pragma once
 
 #include <cstdint>
@@ -32,13 +33,12 @@ namespace bang {
 
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 constexpr int kWarp = 32;
-constexpr int kMaxR = 128;        // neighbours per row: 4 per lane
-constexpr int kMaxRPL = kMaxR / kWarp;
-constexpr int kMaxD = 512;        // dimensions: 16 per lane for the exact distance
-constexpr int kMaxDPL = kMaxD / kWarp;
+constexpr int kMaxR = 128;        // neighbours per row: up to 4 per lane
+constexpr int kMaxD = 512;        // dimensions: up to 16 per lane for the exact distance
 constexpr int kMaxM = 128;
 constexpr int kMaxK = 256;
 constexpr int kMaxL = 1024;
+constexpr int kRegK = 32;         // k up to this keeps the re-rank top-k in registers
 
 struct SearchArgs {
     const void *queries;      // device, nq*d elements
@@ -49,6 +49,7 @@ struct SearchArgs {
     const void *base;         // device-accessible (mapped host), n*d
     uint32_t n, d, M, Mpad, R, medoid;
     uint32_t nq, k, L, log2z, iter_cap;
+    uint32_t vec_ok;          // rows of `base` and `queries` allow 4-element vector loads
     uint32_t *out_ids;        // device, nq*k
     float *out_dist;          // device, nq*k
     uint32_t *out_iters;      // device or null
@@ -60,20 +61,18 @@ struct SearchArgs {
 
 // Shared-memory carve-up, in bytes, shared by host (sizing) and device.
 struct SmemLayout {
-    uint32_t off_T, off_bloom, off_L0, off_L1, off_Nk, off_Nid, off_cnt, off_Ck, off_q, off_offs,
-        total;
+    uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_cnt, off_Ck, off_q, off_offs, total;
     __host__ __device__ static uint32_t up16(uint32_t x) { return (x + 15u) & ~15u; }
     __host__ __device__ SmemLayout(uint32_t M, uint32_t log2z, uint32_t L, uint32_t k, uint32_t d)
     {
         uint32_t o = 0;
         off_T = o;      o += up16(M * 256u * 4u);
         off_bloom = o;  o += up16(((1u << log2z) / 8u) < 4u ? 4u : (1u << log2z) / 8u);
-        off_L0 = o;     o += up16(L * 8u);
-        off_L1 = o;     o += up16(L * 8u);
+        off_L = o;      o += up16(L * 8u);
         off_Nk = o;     o += up16(kMaxR * 8u);
         off_Nid = o;    o += up16(kMaxR * 4u);
         off_cnt = o;    o += up16((L + 1u) * 4u);
-        off_Ck = o;     o += up16(k * 8u);
+        off_Ck = o;     o += up16(k > (uint32_t)kRegK ? k * 8u : 0u);
         off_q = o;      o += up16(d * 4u);
         off_offs = o;   o += up16((M + 1u) * 4u);
         total = o;
@@ -92,7 +91,7 @@ __device__ __forceinline__ uint64_t make_key(uint32_t dbits, uint32_t id)
 __device__ __forceinline__ uint32_t key_id(uint64_t key) { return static_cast<uint32_t>(key) >> 1; }
 
 // FNV-1a over the four little-endian bytes of the id (32-bit, and 64-bit
-// folded to 32 bits), the two hash functions of the per-query Bloom filter.
+// folded to 32 bits): the two hash functions of the per-query Bloom filter.
 __device__ __forceinline__ uint32_t fnv1a32_id(uint32_t id)
 {
     uint32_t h = 2166136261u;
@@ -114,26 +113,27 @@ __device__ __forceinline__ uint32_t fnv1a64_id_folded(uint32_t id)
     return static_cast<uint32_t>(h >> 32) ^ static_cast<uint32_t>(h);
 }
 
-__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int m)
+// Minimum of a 64-bit key over the warp: high words first, then the low
+// words of the lanes that hold the minimal high word.
+__device__ __forceinline__ uint64_t warp_min_key(uint64_t v)
 {
-    uint32_t lo = __shfl_xor_sync(0xFFFFFFFFu, static_cast<uint32_t>(v), m);
-    uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 32), m);
+    uint32_t hi = __reduce_min_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 32));
+    uint32_t lo = __reduce_min_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 32) == hi
+                                                     ? static_cast<uint32_t>(v) : 0xFFFFFFFFu);
     return (static_cast<uint64_t>(hi) << 32) | lo;
 }
-__device__ __forceinline__ uint64_t warp_min_u64(uint64_t v)
+
+__device__ __forceinline__ uint64_t shfl_u64(uint64_t v, int src)
 {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) {
-        uint64_t o = shfl_xor_u64(v, m);
-        v = o < v ? o : v;
-    }
-    return v;
+    uint32_t lo = __shfl_sync(0xFFFFFFFFu, static_cast<uint32_t>(v), src);
+    uint32_t hi = __shfl_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 32), src);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
 }
-__device__ __forceinline__ uint32_t warp_sum_u32(uint32_t v)
+__device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int delta)
 {
-#pragma unroll
-    for (int m = 16; m >= 1; m >>= 1) v += __shfl_xor_sync(0xFFFFFFFFu, v, m);
-    return v;
+    uint32_t lo = __shfl_up_sync(0xFFFFFFFFu, static_cast<uint32_t>(v), delta);
+    uint32_t hi = __shfl_up_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 32), delta);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
 // PQ distance of one code row (§4.4), in the fixed order described above.
@@ -148,11 +148,16 @@ __device__ __forceinline__ float adc_distance(const float *__restrict__ T,
     for (uint32_t c16 = 0; c16 < Mpad / 16u; ++c16) {
         uint4 v = __ldg(row16 + c16);
         uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        const float *Tc = T + c16 * 16u * 256u;
+        if (c16 * 16u + 16u <= M) {
 #pragma unroll
-        for (int b = 0; b < 16; ++b) {
-            uint32_t s = c16 * 16u + static_cast<uint32_t>(b);
-            uint32_t code = (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
-            if (s < M) p[b & 7] = __fadd_rn(p[b & 7], T[s * 256u + code]);
+            for (int b = 0; b < 16; ++b)
+                p[b & 7] = __fadd_rn(p[b & 7], Tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < 16; ++b)
+                if (c16 * 16u + b < M)
+                    p[b & 7] = __fadd_rn(p[b & 7], Tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)]);
         }
     }
 #pragma unroll
@@ -166,37 +171,148 @@ __device__ __forceinline__ float adc_distance(const float *__restrict__ T,
     return p[0];
 }
 
-// The expanded node's neighbour ids and this lane's share of its vector.
-template <int DT> struct NodeData {
-    uint32_t nb[kMaxRPL];
-    float xf[kMaxDPL];
-    int32_t xi[kMaxDPL];
+// This lane's share of a vector for the exact distance: dimensions
+// 128*t + 4*lane + i, i < 4, t < DCH.  Integer data is packed four bytes per
+// word (int8 biased by 0x80 so that byte differences are unsigned).
+template <int DT, int DCH> struct VecShare {
+    float f[DT == 2 ? 4 * DCH : 1];
+    uint32_t w[DT == 2 ? 1 : DCH];
 };
 
-template <int DT>
-__device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int lane,
-                                          NodeData<DT> &nd)
+template <int DT, int DCH>
+__device__ __forceinline__ void load_share(const typename Elem<DT>::T *x, uint32_t d, bool vec,
+                                           int lane, VecShare<DT, DCH> &v)
 {
-    using E = typename Elem<DT>::T;
-    const uint32_t *row = a.adj + static_cast<uint64_t>(u) * a.R;
 #pragma unroll
-    for (int r = 0; r < kMaxRPL; ++r) {
-        uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
-        nd.nb[r] = i < a.R ? row[i] : kNone;
-    }
-    const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
+    for (int t = 0; t < DCH; ++t) {
+        const uint32_t j0 = 128u * t + 4u * lane;
+        if (DT == 2) {
+            if (vec) {
+                float4 f4 = j0 < d ? *reinterpret_cast<const float4 *>(x + j0)
+                                   : make_float4(0.f, 0.f, 0.f, 0.f);
+                v.f[4 * t + 0] = f4.x; v.f[4 * t + 1] = f4.y;
+                v.f[4 * t + 2] = f4.z; v.f[4 * t + 3] = f4.w;
+            } else {
 #pragma unroll
-    for (int t = 0; t < kMaxDPL / 4; ++t) {
+                for (int i = 0; i < 4; ++i)
+                    v.f[4 * t + i] = (j0 + i < d) ? static_cast<float>(x[j0 + i]) : 0.0f;
+            }
+        } else {
+            uint32_t w = 0;
+            if (vec) {
+                w = j0 < d ? *reinterpret_cast<const uint32_t *>(x + j0) : 0u;
+            } else {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            uint32_t j = 128u * t + 4u * lane + i;
-            if (DT == 2) nd.xf[4 * t + i] = j < a.d ? static_cast<float>(x[j]) : 0.0f;
-            else nd.xi[4 * t + i] = j < a.d ? static_cast<int32_t>(x[j]) : 0;
+                for (int i = 0; i < 4; ++i)
+                    if (j0 + i < d) w |= static_cast<uint32_t>(static_cast<uint8_t>(x[j0 + i])) << (8 * i);
+            }
+            if (DT == 1) {
+                // bias only the dimensions that exist, so padding stays equal on both sides
+                uint32_t m = 0;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) if (j0 + i < d) m |= 0x80u << (8 * i);
+                w ^= m;
+            }
+            v.w[t] = w;
         }
     }
 }
 
-template <int DT>
+template <int DT, int DCH>
+__device__ __forceinline__ uint32_t exact_distance_bits(const VecShare<DT, DCH> &q,
+                                                        const VecShare<DT, DCH> &x)
+{
+    if (DT == 2) {
+        float p = 0.0f;
+#pragma unroll
+        for (int t = 0; t < 4 * DCH; ++t) {
+            float df = __fsub_rn(q.f[t], x.f[t]);
+            p = __fmaf_rn(df, df, p);
+        }
+#pragma unroll
+        for (int m = 16; m >= 1; m >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xFFFFFFFFu, p, m));
+        return __float_as_uint(p);
+    } else {
+        uint32_t acc = 0;
+#pragma unroll
+        for (int t = 0; t < DCH; ++t) {
+            uint32_t df = __vabsdiffu4(q.w[t], x.w[t]);
+            acc = __dp4a(df, df, acc);
+        }
+        return __reduce_add_sync(0xFFFFFFFFu, acc);
+    }
+}
+
+// The expanded node's neighbour ids and this lane's share of its vector.
+template <int DT, int RPL, int DCH> struct NodeData {
+    uint32_t nb[RPL];
+    VecShare<DT, DCH> x;
+};
+
+template <int DT, int RPL, int DCH>
+__device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int lane,
+                                          NodeData<DT, RPL, DCH> &nd)
+{
+    using E = typename Elem<DT>::T;
+    const uint32_t *row = a.adj + static_cast<uint64_t>(u) * a.R;
+#pragma unroll
+    for (int r = 0; r < RPL; ++r) {
+        uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
+        nd.nb[r] = i < a.R ? row[i] : kNone;
+    }
+    const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
+    load_share<DT, DCH>(x, a.d, a.vec_ok != 0, lane, nd.x);
+}
+
+// PQ distance table of one query into shared memory (§4.1).
+__device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv,
+                                            const uint32_t *offs, float *T, int lane)
+{
+    for (uint32_t s = 0; s < a.M; ++s) {
+        const uint32_t o = offs[s], ds = offs[s + 1] - o;
+        const float *cb = a.codebook + 256u * o;
+        float *Ts = T + s * 256u;
+        if (ds == 4 && (o & 3u) == 0) {
+            const float4 q4 = *reinterpret_cast<const float4 *>(qv + o);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t c = lane + kWarp * t;
+                const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cb) + c);
+                float acc = 0.0f, df;
+                df = __fsub_rn(q4.x, c4.x); acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(q4.y, c4.y); acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(q4.z, c4.z); acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(q4.w, c4.w); acc = __fmaf_rn(df, df, acc);
+                Ts[c] = acc;
+            }
+        } else if (ds == 2 && (o & 1u) == 0) {
+            const float2 q2 = *reinterpret_cast<const float2 *>(qv + o);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t c = lane + kWarp * t;
+                const float2 c2 = __ldg(reinterpret_cast<const float2 *>(cb) + c);
+                float acc = 0.0f, df;
+                df = __fsub_rn(q2.x, c2.x); acc = __fmaf_rn(df, df, acc);
+                df = __fsub_rn(q2.y, c2.y); acc = __fmaf_rn(df, df, acc);
+                Ts[c] = acc;
+            }
+        } else {
+#pragma unroll 2
+            for (int t = 0; t < 8; ++t) {
+                const uint32_t c = lane + kWarp * t;
+                const float *cc = cb + c * ds;
+                float acc = 0.0f;
+                for (uint32_t j = 0; j < ds; ++j) {
+                    float df = __fsub_rn(qv[o + j], __ldg(cc + j));
+                    acc = __fmaf_rn(df, df, acc);
+                }
+                Ts[c] = acc;
+            }
+        }
+    }
+}
+
+template <int DT, int RPL, int DCH>
 __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 {
     using E = typename Elem<DT>::T;
@@ -205,8 +321,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d);
     float *T = reinterpret_cast<float *>(smem + lay.off_T);
     uint32_t *bloom = reinterpret_cast<uint32_t *>(smem + lay.off_bloom);
-    uint64_t *Lbuf0 = reinterpret_cast<uint64_t *>(smem + lay.off_L0);
-    uint64_t *Lbuf1 = reinterpret_cast<uint64_t *>(smem + lay.off_L1);
+    uint64_t *Lk = reinterpret_cast<uint64_t *>(smem + lay.off_L);
     uint64_t *Nk = reinterpret_cast<uint64_t *>(smem + lay.off_Nk);
     uint32_t *Nid = reinterpret_cast<uint32_t *>(smem + lay.off_Nid);
     uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + lay.off_cnt);
@@ -214,115 +329,75 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     float *qv = reinterpret_cast<float *>(smem + lay.off_q);
     uint32_t *offs = reinterpret_cast<uint32_t *>(smem + lay.off_offs);
 
-    const uint32_t M = a.M, d = a.d, L = a.L, k = a.k;
+    const uint32_t d = a.d, L = a.L, k = a.k;
     const uint32_t zmask = (1u << a.log2z) - 1u;
     const uint32_t nwords = (1u << a.log2z) >= 32u ? (1u << a.log2z) / 32u : 1u;
+    const bool regk = k <= static_cast<uint32_t>(kRegK);
 
-    for (uint32_t i = lane; i <= M; i += kWarp) offs[i] = a.off[i];
+    for (uint32_t i = lane; i <= a.M; i += kWarp) offs[i] = a.off[i];
 
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
         // ---- query: FP32 copy in shared memory, this lane's share in registers
         const E *qp = static_cast<const E *>(a.queries) + static_cast<uint64_t>(q) * d;
         for (uint32_t j = lane; j < d; j += kWarp) qv[j] = static_cast<float>(qp[j]);
-        float qf[kMaxDPL];
-        int32_t qi[kMaxDPL];
-#pragma unroll
-        for (int t = 0; t < kMaxDPL / 4; ++t)
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                uint32_t j = 128u * t + 4u * lane + i;
-                qf[4 * t + i] = j < d ? static_cast<float>(qp[j]) : 0.0f;
-                qi[4 * t + i] = j < d ? static_cast<int32_t>(qp[j]) : 0;
-            }
+        VecShare<DT, DCH> qs;
+        load_share<DT, DCH>(qp, d, a.vec_ok != 0, lane, qs);
         for (uint32_t w = lane; w < nwords; w += kWarp) bloom[w] = 0u;
         __syncwarp();
-
-        // ---- PQ distance table, §4.1
-        for (uint32_t idx = lane; idx < M * 256u; idx += kWarp) {
-            uint32_t s = idx >> 8, c = idx & 255u;
-            uint32_t o = offs[s], ds = offs[s + 1] - o;
-            const float *cc = a.codebook + 256u * o + c * ds;
-            float acc = 0.0f;
-            for (uint32_t j = 0; j < ds; ++j) {
-                float df = __fsub_rn(qv[o + j], __ldg(cc + j));
-                acc = __fmaf_rn(df, df, acc);
-            }
-            T[idx] = acc;
-        }
+        build_table(a, qv, offs, T, lane);
         __syncwarp();
 
         // ---- start: worklist = {medoid}, medoid marked seen
-        uint64_t *Lcur = Lbuf0, *Lnext = Lbuf1;
         if (lane == 0) {
-            uint32_t s = a.medoid;
-            float dm = adc_distance(T, a.codes + static_cast<uint64_t>(s) * a.Mpad, M, a.Mpad);
-            Lcur[0] = make_key(__float_as_uint(dm), s);
+            const uint32_t s = a.medoid;
+            float dm = adc_distance(T, a.codes + static_cast<uint64_t>(s) * a.Mpad, a.M, a.Mpad);
+            Lk[0] = make_key(__float_as_uint(dm), s);
             uint32_t p1 = fnv1a32_id(s) & zmask, p2 = fnv1a64_id_folded(s) & zmask;
             bloom[p1 >> 5] |= 1u << (p1 & 31u);
             bloom[p2 >> 5] |= 1u << (p2 & 31u);
         }
-        uint32_t nl = 1, nc = 0, iters = 0, ndist = 1;
+        uint32_t nl = 1, nc = 0, iters = 0, ndist = 1, first = 0;
+        bool have_next = true;
         int32_t status = 0;
+        uint64_t ck = ~0ull;               // register top-k (k <= kRegK): lane i holds rank i
         uint32_t cur = a.medoid;
-        NodeData<DT> nd;
-        load_node<DT>(a, cur, lane, nd);
+        NodeData<DT, RPL, DCH> nd;
+        load_node<DT, RPL, DCH>(a, cur, lane, nd);
         __syncwarp();
 
-        for (;;) {
-            // u* = first unvisited entry of the sorted worklist (Alg. 1)
-            int first = -1;
-            for (uint32_t b0 = 0; b0 < nl; b0 += kWarp) {
-                uint32_t i = b0 + lane;
-                bool v = i < nl && !(Lcur[i] & 1ull);
-                uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
-                if (bal) {
-                    first = static_cast<int>(b0 + __ffs(bal) - 1);
-                    break;
-                }
-            }
-            if (first < 0) break;
+        while (have_next) {
             if (iters >= a.iter_cap) {
                 status = 1;
                 break;
             }
-            const uint64_t ukey = Lcur[first];
+            // u* = first unvisited entry of the sorted worklist (Alg. 1); its
+            // position comes out of the previous merge
+            const uint64_t ukey = Lk[first];
             const uint32_t u = key_id(ukey);
             __syncwarp();
             if (lane == 0) {
-                Lcur[first] = ukey | 1ull;
+                Lk[first] = ukey | 1ull;
                 if (a.trace && iters < a.trace_cap)
                     a.trace[static_cast<uint64_t>(q) * a.trace_cap + iters] = u;
             }
             ++iters;
             if (u != cur) {  // the prefetched node is always u*; reload if not
                 cur = u;
-                load_node<DT>(a, cur, lane, nd);
+                load_node<DT, RPL, DCH>(a, cur, lane, nd);
             }
 
             // ---- re-rank candidate: exact distance of u* (§4.8)
-            uint32_t ebits;
-            if (DT == 2) {
-                float p = 0.0f;
-#pragma unroll
-                for (int t = 0; t < kMaxDPL; ++t) {
-                    float df = __fsub_rn(qf[t], nd.xf[t]);
-                    p = __fmaf_rn(df, df, p);
-                }
-#pragma unroll
-                for (int m = 16; m >= 1; m >>= 1) p = __fadd_rn(p, __shfl_xor_sync(0xFFFFFFFFu, p, m));
-                ebits = __float_as_uint(p);
-            } else {
-                int32_t p = 0;
-#pragma unroll
-                for (int t = 0; t < kMaxDPL; ++t) {
-                    int32_t df = qi[t] - nd.xi[t];
-                    p += df * df;
-                }
-                ebits = warp_sum_u32(static_cast<uint32_t>(p));
-            }
             {
-                const uint64_t e = make_key(ebits, u);
-                if (!(nc == k && e >= Ck[k - 1])) {
+                const uint64_t e = make_key(exact_distance_bits<DT, DCH>(qs, nd.x), u);
+                if (regk) {
+                    const uint32_t pos = __popc(__ballot_sync(0xFFFFFFFFu, ck < e));
+                    if (pos < k) {
+                        const uint64_t up = shfl_up_u64(ck, 1);
+                        if (static_cast<uint32_t>(lane) == pos) ck = e;
+                        else if (static_cast<uint32_t>(lane) > pos) ck = up;
+                    }
+                    nc = nc + 1 < k ? nc + 1 : k;
+                } else if (!(nc == k && e >= Ck[k - 1])) {
                     uint32_t less = 0;
                     uint64_t keep[kMaxK / kWarp];
 #pragma unroll
@@ -331,7 +406,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                         keep[t] = i < nc ? Ck[i] : 0ull;
                         less += (i < nc && keep[t] < e) ? 1u : 0u;
                     }
-                    const uint32_t pos = warp_sum_u32(less);
+                    const uint32_t pos = __reduce_add_sync(0xFFFFFFFFu, less);
                     __syncwarp();
 #pragma unroll
                     for (int t = 0; t < kMaxK / kWarp; ++t) {
@@ -345,29 +420,30 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             }
 
             // ---- filter seen neighbours, §4.3: test all, then insert all
-            bool fresh[kMaxRPL];
-            uint32_t p1[kMaxRPL], p2[kMaxRPL];
+            bool fresh[RPL];
+            uint32_t p1[RPL], p2[RPL];
 #pragma unroll
-            for (int r = 0; r < kMaxRPL; ++r) {
-                uint32_t id = nd.nb[r];
+            for (int r = 0; r < RPL; ++r) {
+                const uint32_t id = nd.nb[r];
                 fresh[r] = false;
+                p1[r] = p2[r] = 0;
                 if (id != kNone) {
                     p1[r] = fnv1a32_id(id) & zmask;
                     p2[r] = fnv1a64_id_folded(id) & zmask;
-                    bool hit = ((bloom[p1[r] >> 5] >> (p1[r] & 31u)) & 1u) &&
-                               ((bloom[p2[r] >> 5] >> (p2[r] & 31u)) & 1u);
+                    const bool hit = ((bloom[p1[r] >> 5] >> (p1[r] & 31u)) & 1u) &&
+                                     ((bloom[p2[r] >> 5] >> (p2[r] & 31u)) & 1u);
                     fresh[r] = !hit;
                 }
             }
             __syncwarp();
             uint32_t nn = 0;
 #pragma unroll
-            for (int r = 0; r < kMaxRPL; ++r) {
+            for (int r = 0; r < RPL; ++r) {
                 if (fresh[r]) {
                     atomicOr(&bloom[p1[r] >> 5], 1u << (p1[r] & 31u));
                     atomicOr(&bloom[p2[r] >> 5], 1u << (p2[r] & 31u));
                 }
-                uint32_t bal = __ballot_sync(0xFFFFFFFFu, fresh[r]);
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fresh[r]);
                 if (fresh[r]) Nid[nn + __popc(bal & ((1u << lane) - 1u))] = nd.nb[r];
                 nn += __popc(bal);
             }
@@ -375,92 +451,152 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 
             // ---- PQ distances of the new neighbours, §4.4
             for (uint32_t j = lane; j < nn; j += kWarp) {
-                uint32_t id = Nid[j];
-                float dj = adc_distance(T, a.codes + static_cast<uint64_t>(id) * a.Mpad, M, a.Mpad);
+                const uint32_t id = Nid[j];
+                const float dj = adc_distance(T, a.codes + static_cast<uint64_t>(id) * a.Mpad, a.M,
+                                              a.Mpad);
                 Nk[j] = make_key(__float_as_uint(dj), id);
             }
             ndist += nn;
             __syncwarp();
 
-            // ---- eager next node, §4.5: best of the new neighbours and the
-            // first unvisited worklist entry after u*; prefetch its lists
+            // ---- eager next node, §4.5: the best of the new neighbours and
+            // the first unvisited worklist entry after u*; prefetch its lists
+            uint64_t best = ~0ull, lkey = ~0ull;
+            int lnext = -1;                  // index of that worklist entry
             {
-                uint64_t best = ~0ull;
                 for (uint32_t j = lane; j < nn; j += kWarp) best = Nk[j] < best ? Nk[j] : best;
-                for (uint32_t b0 = static_cast<uint32_t>(first) + 1; b0 < nl; b0 += kWarp) {
-                    uint32_t i = b0 + lane;
-                    bool v = i < nl && !(Lcur[i] & 1ull);
-                    uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
+                for (uint32_t b0 = first + 1; b0 < nl; b0 += kWarp) {
+                    const uint32_t i = b0 + lane;
+                    const bool v = i < nl && !(Lk[i] & 1ull);
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
                     if (bal) {
-                        uint32_t f = b0 + __ffs(bal) - 1;
-                        uint64_t lk = Lcur[f];
-                        best = lk < best ? lk : best;
+                        lnext = static_cast<int>(b0 + __ffs(bal) - 1);
+                        lkey = Lk[lnext];
+                        best = lkey < best ? lkey : best;
                         break;
                     }
                 }
-                best = warp_min_u64(best);
+                best = warp_min_key(best);
+                // the best new neighbour can still fall off the end of a full
+                // worklist of expanded entries; whether a next node exists is
+                // settled by the merge below
                 if (best != ~0ull) {
                     cur = key_id(best);
-                    load_node<DT>(a, cur, lane, nd);
+                    load_node<DT, RPL, DCH>(a, cur, lane, nd);
                 }
             }
 
-            // ---- merge the new neighbours into the worklist, §4.6-§4.7:
-            // every element's output position is its index plus its rank in
-            // the other list; keys are unique, so ranks are exact
-            for (uint32_t i = lane; i <= nl; i += kWarp) cnt[i] = 0u;
-            __syncwarp();
-            for (uint32_t j = lane; j < nn; j += kWarp) {
-                const uint64_t x = Nk[j];
-                uint32_t lo = 0, hi = nl;          // rank in the worklist
-                while (lo < hi) {
-                    uint32_t mid = (lo + hi) >> 1;
-                    if ((Lcur[mid] >> 1) < (x >> 1)) lo = mid + 1;
-                    else hi = mid;
+            // ---- merge the new neighbours into the worklist, §4.6-§4.7.
+            // Output position = own index + rank in the other list (keys are
+            // unique).  New keys: binary search in the worklist plus a count
+            // among the new keys.  Worklist keys only move right, by the number
+            // of new keys ranked before them; they are updated in place, chunk
+            // by chunk from the end, starting at the chunk of the first
+            // insertion point.
+            uint32_t npos = 0;               // new position of `best`, plus one
+            if (nn > 0) {
+                uint64_t xk[RPL];
+                uint32_t xlo[RPL], xpos[RPL];
+                uint32_t rmin = 0xFFFFFFFFu;
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    const uint32_t j = lane + kWarp * t;
+                    xk[t] = 0;
+                    xlo[t] = xpos[t] = 0xFFFFFFFFu;
+                    if (j < nn) {
+                        const uint64_t x = Nk[j];
+                        uint32_t lo = 0, hi = nl;
+                        while (lo < hi) {
+                            const uint32_t mid = (lo + hi) >> 1;
+                            if ((Lk[mid] >> 1) < (x >> 1)) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        uint32_t rn = 0;
+                        uint32_t tt = 0;
+                        for (; tt + 4 <= nn; tt += 4) {
+                            rn += (Nk[tt] < x) + (Nk[tt + 1] < x) + (Nk[tt + 2] < x) + (Nk[tt + 3] < x);
+                        }
+                        for (; tt < nn; ++tt) rn += Nk[tt] < x;
+                        xk[t] = x;
+                        xlo[t] = lo;
+                        xpos[t] = lo + rn;
+                        rmin = lo < rmin ? lo : rmin;
+                    }
                 }
-                uint32_t rn = 0;                   // rank among the new ones
-                for (uint32_t t = 0; t < nn; ++t) rn += Nk[t] < x ? 1u : 0u;
-                const uint32_t pos = lo + rn;
-                if (pos < L) Lnext[pos] = x;
-                atomicAdd(&cnt[lo], 1u);
-            }
-            __syncwarp();
-            {
-                uint32_t carry = 0;
-                for (uint32_t b0 = 0; b0 < nl; b0 += kWarp) {
-                    uint32_t i = b0 + lane;
-                    uint32_t v = i < nl ? cnt[i] : 0u;
+                rmin = __reduce_min_sync(0xFFFFFFFFu, rmin);
+                const uint32_t c0 = rmin & ~31u;
+                for (uint32_t i = c0 + lane; i <= nl; i += kWarp) cnt[i] = 0u;
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < RPL; ++t)
+                    if (xlo[t] != 0xFFFFFFFFu) atomicAdd(&cnt[xlo[t]], 1u);
+                __syncwarp();
+                // shift(i) = #{new: lo <= i} = nn - #{new: lo > i}
+                uint32_t carry = 0;          // #{new: lo > top of the current chunk}
+                for (int32_t cb = static_cast<int32_t>((nl - 1) & ~31u);
+                     cb >= static_cast<int32_t>(c0); cb -= kWarp) {
+                    const uint32_t i = static_cast<uint32_t>(cb) + lane;
+                    uint32_t s = (i + 1 <= nl) ? cnt[i + 1] : 0u;   // inclusive suffix over lanes
 #pragma unroll
                     for (int m = 1; m < kWarp; m <<= 1) {
-                        uint32_t o = __shfl_up_sync(0xFFFFFFFFu, v, m);
-                        if (lane >= m) v += o;
+                        const uint32_t o = __shfl_down_sync(0xFFFFFFFFu, s, m);
+                        if (lane + m < kWarp) s += o;
                     }
-                    v += carry;
+                    s += carry;
+                    carry = __shfl_sync(0xFFFFFFFFu, s, 0);
+                    uint64_t key = 0;
+                    uint32_t pos = 0xFFFFFFFFu;
                     if (i < nl) {
-                        uint32_t pos = i + v;
-                        if (pos < L) Lnext[pos] = Lcur[i];
+                        key = Lk[i];
+                        pos = i + (nn - s);
+                        if (key == best && pos < L) npos = pos + 1;
                     }
-                    carry = __shfl_sync(0xFFFFFFFFu, v, kWarp - 1);
+                    __syncwarp();
+                    if (pos < L) Lk[pos] = key;
+                    __syncwarp();
                 }
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    if (xpos[t] < L) Lk[xpos[t]] = xk[t];
+                    if (xlo[t] != 0xFFFFFFFFu && xk[t] == best && xpos[t] < L) npos = xpos[t] + 1;
+                }
+                __syncwarp();
+                nl = nl + nn < L ? nl + nn : L;
+                npos = __reduce_max_sync(0xFFFFFFFFu, npos);
+                if (npos == 0 && lnext >= 0 && best == lkey)      // in the untouched prefix
+                    npos = static_cast<uint32_t>(lnext) + 1;
+            } else if (lnext >= 0) {
+                npos = static_cast<uint32_t>(lnext) + 1;
             }
-            nl = nl + nn < L ? nl + nn : L;
-            uint64_t *tmp = Lcur;
-            Lcur = Lnext;
-            Lnext = tmp;
-            __syncwarp();
+            have_next = npos != 0;
+            first = npos - 1;
         }
 
         // ---- output: re-ranked top-k (§4.8), padded
-        for (uint32_t i = lane; i < k; i += kWarp) {
-            uint64_t o = static_cast<uint64_t>(q) * k + i;
-            if (i < nc) {
-                uint64_t key = Ck[i];
-                uint32_t bits = static_cast<uint32_t>(key >> 32);
-                a.out_ids[o] = key_id(key);
-                a.out_dist[o] = DT == 2 ? __uint_as_float(bits) : static_cast<float>(bits);
-            } else {
-                a.out_ids[o] = kNone;
-                a.out_dist[o] = __uint_as_float(0x7F800000u);
+        if (regk) {
+            if (static_cast<uint32_t>(lane) < k) {
+                const uint64_t o = static_cast<uint64_t>(q) * k + lane;
+                if (static_cast<uint32_t>(lane) < nc) {
+                    const uint32_t bits = static_cast<uint32_t>(ck >> 32);
+                    a.out_ids[o] = key_id(ck);
+                    a.out_dist[o] = DT == 2 ? __uint_as_float(bits) : static_cast<float>(bits);
+                } else {
+                    a.out_ids[o] = kNone;
+                    a.out_dist[o] = __uint_as_float(0x7F800000u);
+                }
+            }
+        } else {
+            for (uint32_t i = lane; i < k; i += kWarp) {
+                const uint64_t o = static_cast<uint64_t>(q) * k + i;
+                if (i < nc) {
+                    const uint64_t key = Ck[i];
+                    const uint32_t bits = static_cast<uint32_t>(key >> 32);
+                    a.out_ids[o] = key_id(key);
+                    a.out_dist[o] = DT == 2 ? __uint_as_float(bits) : static_cast<float>(bits);
+                } else {
+                    a.out_ids[o] = kNone;
+                    a.out_dist[o] = __uint_as_float(0x7F800000u);
+                }
             }
         }
         if (lane == 0) {

@@ -123,6 +123,30 @@ def test_f32_d96_M48_R68():
                   trace_cap=300)
 
 
+def test_long_worklist(cfg1):
+    Q = cfg1["queries"][:20]
+    assert_parity(gpu_search(cfg1, Q, 64, 512, 17, trace_cap=900),
+                  oracle_search(cfg1, Q, 64, 512, 17, trace_cap=900), trace_cap=900)
+
+
+def test_f32_d200_wide_vectors():
+    # d > 128: four 128-dimension chunks per lane in the exact distance
+    w = cases.clustered(n=5_000, nq=30, ncomp=4, dtype="f32", d=200, M=50, R=48,
+                        centre="uniform255")
+    Q = w["queries"]
+    assert_parity(gpu_search(w, Q, 10, 48, trace_cap=200), oracle_search(w, Q, 10, 48, trace_cap=200),
+                  trace_cap=200)
+
+
+def test_u8_d130_unaligned_rows():
+    # d % 4 != 0: rows are not 4-byte aligned, scalar loads; 5 dims per subspace
+    w = cases.clustered(n=5_000, nq=30, ncomp=4, dtype="u8", d=130, M=26, R=32,
+                        centre="uniform255")
+    Q = w["queries"]
+    assert_parity(gpu_search(w, Q, 10, 40, trace_cap=200), oracle_search(w, Q, 10, 40, trace_cap=200),
+                  trace_cap=200)
+
+
 def test_iteration_cap_and_single_query(u8small):
     Q = u8small["queries"][:1]
     g = gpu_search(u8small, Q, 5, 64, iter_cap=7)
