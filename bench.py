@@ -39,7 +39,7 @@ WORKLOAD = "mid-scale plain method: n=1M u8 d=128, 10k queries, PQ M=32, R=64, k
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=("gb300", "reference"))
     ap.add_argument("--n", type=int, default=None, help="shrink the workload (testing only)")
@@ -250,6 +250,16 @@ def main():
     it = iters.cpu().numpy().astype(np.int64)
     nd = ndist.cpu().numpy().astype(np.int64)
 
+    # ---- per-phase SM cycles of the fused kernel (one untimed launch): the
+    # counterpart of the paper's per-kernel share of GPU time
+    phase = torch.zeros((nq, len(bang.PHASES)), dtype=torch.int64, device=dev)
+    ix.search(q_dev, K, L, ids, dist_out, bang.make_params(bloom_log2=args.bloom_log2,
+                                                           out_phase_cycles=phase), stream=sptr)
+    stream.synchronize()
+    ph = phase.cpu().numpy().astype(np.float64).sum(0)
+    phases = {name: round(float(ph[i] / ph[-1]), 4) for i, name in enumerate(bang.PHASES[:-1])}
+    phases["cycles_per_expansion"] = round(float(ph[-1] / max(1, it.sum())), 1)
+
     # ---- algorithmic bytes per launch (one launch = the whole batch)
     R = w["adj"].shape[1]
     host_bytes = int(it.sum()) * (R * 4 + d * 1)           # neighbour row + full vector per expansion
@@ -299,6 +309,7 @@ def main():
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
 
+    link = bang.bang_probe_host_link(local, 1 << 30, R * 4)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_gbs = hbm_bytes / launch_s / 1e9
@@ -310,6 +321,7 @@ def main():
         "config": {"workload": WORKLOAD, "L": L, "recall@10": round(rec, 4), "k": K,
                    "bloom_log2": args.bloom_log2, "sweep": sweep,
                    "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
+                   "phase_share": phases,
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "l2": "512 MB flush written between timed steps",
                    "n": int(w["base"].shape[0]), "nq": nq},
@@ -318,6 +330,12 @@ def main():
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "algorithmic_bytes_per_launch": hbm_bytes},
         "host_link": {"achieved_gbs": host_bytes / launch_s / 1e9,
+                      "peak_gbs": link["gather_gbs"],
+                      "frac": host_bytes / launch_s / 1e9 / link["gather_gbs"],
+                      "peak_source": "measured in this run: random %d-byte row gathers in place "
+                                     "from mapped host memory" % link["gather_row_bytes"],
+                      "copy_engine_gbs": link["h2d_copy_gbs"],
+                      "load_latency_ns": link["latency_ns"],
                       "algorithmic_bytes_per_launch": host_bytes,
                       "note": "neighbour rows and full vectors read in place from page-locked "
                               "host memory"},

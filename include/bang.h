@@ -64,6 +64,13 @@ typedef struct bang_search_params {
      * of trace_cap entries (host or device); rows are not padded. */
     uint32_t *trace;
     uint32_t trace_cap;
+    /* Optional per-query profile, nq rows of 10 SM-cycle counts (host or
+     * device): PQ table (§4.1), choice of u*, seen filter (§4.3), PQ
+     * distances (§4.4), next-node choice and prefetch (§4.5), re-rank
+     * candidate (§4.8), merge remainder, merge ranking of the new keys and
+     * merge shifting of the worklist (§4.6-§4.7), and the query's total: the
+     * paper's per-kernel GPU-time breakdown (§7.3) for the fused kernel. */
+    unsigned long long *out_phase_cycles;
 } bang_search_params;
 
 /* Create an empty index bound to CUDA device `device`.  *out receives an
@@ -126,6 +133,21 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
 /* Release device memory, unregister host memory registered by the library
  * and free the handle.  NULL is accepted. */
 int bang_destroy(bang_index *ix);
+
+/* Measured figures of the link between the GPU and host memory (the paper's
+ * PCIe 4.0 link, 32 GB/s peak, §6.1; NVLink-C2C on a Grace-hosted GB300). */
+typedef struct bang_link_probe {
+    double h2d_copy_gbs;        /* copy engine: page-locked host -> device, best of 3 */
+    double gather_gbs;          /* kernel reads of random rows in place from mapped host memory */
+    double latency_ns;          /* one dependent 4-byte load from mapped host memory */
+    uint32_t gather_row_bytes;  /* row size used for gather_gbs */
+} bang_link_probe;
+
+/* Measure the host link of `device` with a page-locked buffer of `bytes`
+ * (>= 1 MiB) that the call allocates and frees; `row_bytes` (16..512, a
+ * multiple of 16) is the gathered row size, e.g. R*4 for a neighbour row.
+ * Blocks until done; takes about bytes/10 GB/s plus a few milliseconds. */
+int bang_probe_host_link(int device, uint64_t bytes, uint32_t row_bytes, bang_link_probe *out);
 
 /* Message for the last non-OK status returned to the calling thread. */
 const char *bang_last_error(void);

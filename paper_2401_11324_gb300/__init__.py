@@ -33,7 +33,19 @@ class bang_search_params(ctypes.Structure):
     _fields_ = [("bloom_log2", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("out_iters", ctypes.c_void_p), ("out_status", ctypes.c_void_p),
                 ("out_ndist", ctypes.c_void_p), ("trace", ctypes.c_void_p),
-                ("trace_cap", ctypes.c_uint32)]
+                ("trace_cap", ctypes.c_uint32), ("out_phase_cycles", ctypes.c_void_p)]
+
+
+class bang_link_probe(ctypes.Structure):
+    _fields_ = [("h2d_copy_gbs", ctypes.c_double), ("gather_gbs", ctypes.c_double),
+                ("latency_ns", ctypes.c_double), ("gather_row_bytes", ctypes.c_uint32)]
+
+
+def bang_probe_host_link(device=0, nbytes=1 << 30, row_bytes=256):
+    out = bang_link_probe()
+    _check(lib().bang_probe_host_link(device, nbytes, row_bytes, ctypes.byref(out)))
+    return dict(h2d_copy_gbs=out.h2d_copy_gbs, gather_gbs=out.gather_gbs,
+                latency_ns=out.latency_ns, gather_row_bytes=out.gather_row_bytes)
 
 
 def library_path():
@@ -56,6 +68,8 @@ def _load():
     L.bang_search.argtypes = [vp, vp, u32, u32, u32, ctypes.POINTER(bang_search_params), vp, vp,
                               vp]
     L.bang_destroy.argtypes = [vp]
+    L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
+    L.bang_probe_host_link.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
               "bang_search", "bang_destroy"):
@@ -110,10 +124,14 @@ def bang_register_vectors(ix, base, dtype):
     return _check(lib().bang_register_vectors(ix, _ptr(base), dtype))
 
 
+PHASES = ("table", "select", "filter", "distance", "next", "rerank", "merge", "merge_rank",
+          "merge_shift", "total")
+
+
 def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
-                trace=None, trace_cap=0):
+                trace=None, trace_cap=0, out_phase_cycles=None):
     return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
-                              _ptr(out_ndist), _ptr(trace), trace_cap)
+                              _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles))
 
 
 def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):

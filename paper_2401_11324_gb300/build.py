@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libbang.so")
-SOURCES = ["bang_api.cu"]
+SOURCES = ["bang_api.cu", "link_probe.cu"]
 HEADERS = ["search_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -369,10 +369,10 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
         {p.out_status, (size_t)nq * 4, false, 0, false},
         {p.out_ndist, (size_t)nq * 4, false, 0, false},
         {p.trace, (size_t)nq * p.trace_cap * 4, false, 0, false},
-        {nullptr, 0, false, 0, false}};
+        {p.out_phase_cycles, (size_t)nq * bang::kPhases * 8, false, 0, false}};
     size_t need = 0;
     bool any_host = false;
-    for (int i = 0; i < 7; ++i) {
+    for (int i = 0; i < 8; ++i) {
         Slot &s = slots[i];
         if (!s.user) continue;
         s.dev = is_device_accessible(s.user);
@@ -407,6 +407,7 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.out_ndist = static_cast<uint32_t *>(dptr(5));
     a.trace = static_cast<uint32_t *>(dptr(6));
     a.trace_cap = p.trace_cap;
+    a.phase_cycles = static_cast<unsigned long long *>(dptr(7));
 
     {
         // 4-element vector loads need rows that start on 16-byte boundaries
@@ -421,7 +422,7 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     default: rc = launch_dt<2>(a, lay.total, st); break;
     }
     if (rc) return rc;
-    for (int i = 1; i < 7; ++i) {
+    for (int i = 1; i < 8; ++i) {
         Slot &s = slots[i];
         if (s.user && !s.dev)
             CUDA_TRY(cudaMemcpyAsync(const_cast<void *>(s.user), dptr(i), s.bytes,

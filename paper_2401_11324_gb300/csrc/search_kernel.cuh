@@ -57,11 +57,16 @@ struct SearchArgs {
     uint32_t *out_ndist;      // device or null
     uint32_t *trace;          // device or null
     uint32_t trace_cap;
+    unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
 };
+
+// Phases timed when SearchArgs::phase_cycles is set.
+enum Phase { kPhTable = 0, kPhSelect, kPhFilter, kPhDistance, kPhNext, kPhRerank, kPhMerge,
+             kPhMergeRank, kPhMergeShift, kPhTotal, kPhases };
 
 // Shared-memory carve-up, in bytes, shared by host (sizing) and device.
 struct SmemLayout {
-    uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_cnt, off_Ck, off_q, off_offs, total;
+    uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_Ck, off_q, off_offs, total;
     __host__ __device__ static uint32_t up16(uint32_t x) { return (x + 15u) & ~15u; }
     __host__ __device__ SmemLayout(uint32_t M, uint32_t log2z, uint32_t L, uint32_t k, uint32_t d)
     {
@@ -71,7 +76,6 @@ struct SmemLayout {
         off_L = o;      o += up16(L * 8u);
         off_Nk = o;     o += up16(kMaxR * 8u);
         off_Nid = o;    o += up16(kMaxR * 4u);
-        off_cnt = o;    o += up16((L + 1u) * 4u);
         off_Ck = o;     o += up16(k > (uint32_t)kRegK ? k * 8u : 0u);
         off_q = o;      o += up16(d * 4u);
         off_offs = o;   o += up16((M + 1u) * 4u);
@@ -312,6 +316,25 @@ __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv
     }
 }
 
+struct PhaseClock {
+    bool on;
+    unsigned long long t, acc[kPhases];
+    __device__ __forceinline__ explicit PhaseClock(bool enabled) : on(enabled), t(0)
+    {
+#pragma unroll
+        for (int i = 0; i < kPhases; ++i) acc[i] = 0;
+        if (on) t = clock64();
+    }
+    __device__ __forceinline__ void mark(int ph)
+    {
+        if (on) {
+            const unsigned long long now = clock64();
+            acc[ph] += now - t;
+            t = now;
+        }
+    }
+};
+
 template <int DT, int RPL, int DCH>
 __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 {
@@ -324,7 +347,6 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     uint64_t *Lk = reinterpret_cast<uint64_t *>(smem + lay.off_L);
     uint64_t *Nk = reinterpret_cast<uint64_t *>(smem + lay.off_Nk);
     uint32_t *Nid = reinterpret_cast<uint32_t *>(smem + lay.off_Nid);
-    uint32_t *cnt = reinterpret_cast<uint32_t *>(smem + lay.off_cnt);
     uint64_t *Ck = reinterpret_cast<uint64_t *>(smem + lay.off_Ck);
     float *qv = reinterpret_cast<float *>(smem + lay.off_q);
     uint32_t *offs = reinterpret_cast<uint32_t *>(smem + lay.off_offs);
@@ -337,6 +359,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     for (uint32_t i = lane; i <= a.M; i += kWarp) offs[i] = a.off[i];
 
     for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+        PhaseClock clk(a.phase_cycles != nullptr);
+        const unsigned long long t_start = clk.t;
         // ---- query: FP32 copy in shared memory, this lane's share in registers
         const E *qp = static_cast<const E *>(a.queries) + static_cast<uint64_t>(q) * d;
         for (uint32_t j = lane; j < d; j += kWarp) qv[j] = static_cast<float>(qp[j]);
@@ -346,6 +370,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         __syncwarp();
         build_table(a, qv, offs, T, lane);
         __syncwarp();
+        clk.mark(kPhTable);
 
         // ---- start: worklist = {medoid}, medoid marked seen
         if (lane == 0) {
@@ -385,39 +410,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 cur = u;
                 load_node<DT, RPL, DCH>(a, cur, lane, nd);
             }
-
-            // ---- re-rank candidate: exact distance of u* (§4.8)
-            {
-                const uint64_t e = make_key(exact_distance_bits<DT, DCH>(qs, nd.x), u);
-                if (regk) {
-                    const uint32_t pos = __popc(__ballot_sync(0xFFFFFFFFu, ck < e));
-                    if (pos < k) {
-                        const uint64_t up = shfl_up_u64(ck, 1);
-                        if (static_cast<uint32_t>(lane) == pos) ck = e;
-                        else if (static_cast<uint32_t>(lane) > pos) ck = up;
-                    }
-                    nc = nc + 1 < k ? nc + 1 : k;
-                } else if (!(nc == k && e >= Ck[k - 1])) {
-                    uint32_t less = 0;
-                    uint64_t keep[kMaxK / kWarp];
-#pragma unroll
-                    for (int t = 0; t < kMaxK / kWarp; ++t) {
-                        uint32_t i = lane + kWarp * t;
-                        keep[t] = i < nc ? Ck[i] : 0ull;
-                        less += (i < nc && keep[t] < e) ? 1u : 0u;
-                    }
-                    const uint32_t pos = __reduce_add_sync(0xFFFFFFFFu, less);
-                    __syncwarp();
-#pragma unroll
-                    for (int t = 0; t < kMaxK / kWarp; ++t) {
-                        uint32_t i = lane + kWarp * t;
-                        if (i < nc && i >= pos && i + 1 < k) Ck[i + 1] = keep[t];
-                    }
-                    if (lane == 0) Ck[pos] = e;
-                    nc = nc + 1 < k ? nc + 1 : k;
-                    __syncwarp();
-                }
-            }
+            const VecShare<DT, DCH> xu = nd.x;   // u*'s vector, for the re-rank below
+            clk.mark(kPhSelect);
 
             // ---- filter seen neighbours, §4.3: test all, then insert all
             bool fresh[RPL];
@@ -448,6 +442,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 nn += __popc(bal);
             }
             __syncwarp();
+            clk.mark(kPhFilter);
 
             // ---- PQ distances of the new neighbours, §4.4
             for (uint32_t j = lane; j < nn; j += kWarp) {
@@ -458,6 +453,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             }
             ndist += nn;
             __syncwarp();
+            clk.mark(kPhDistance);
 
             // ---- eager next node, §4.5: the best of the new neighbours and
             // the first unvisited worklist entry after u*; prefetch its lists
@@ -485,24 +481,62 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     load_node<DT, RPL, DCH>(a, cur, lane, nd);
                 }
             }
+            clk.mark(kPhNext);
+            // ---- re-rank candidate: exact distance of u* (§4.8), off the
+            // critical path: the next node's lists are already requested
+            {
+                const uint64_t e = make_key(exact_distance_bits<DT, DCH>(qs, xu), u);
+                if (regk) {
+                    const uint32_t pos = __popc(__ballot_sync(0xFFFFFFFFu, ck < e));
+                    if (pos < k) {
+                        const uint64_t up = shfl_up_u64(ck, 1);
+                        if (static_cast<uint32_t>(lane) == pos) ck = e;
+                        else if (static_cast<uint32_t>(lane) > pos) ck = up;
+                    }
+                    nc = nc + 1 < k ? nc + 1 : k;
+                } else if (!(nc == k && e >= Ck[k - 1])) {
+                    uint32_t less = 0;
+                    uint64_t keep[kMaxK / kWarp];
+#pragma unroll
+                    for (int t = 0; t < kMaxK / kWarp; ++t) {
+                        uint32_t i = lane + kWarp * t;
+                        keep[t] = i < nc ? Ck[i] : 0ull;
+                        less += (i < nc && keep[t] < e) ? 1u : 0u;
+                    }
+                    const uint32_t pos = __reduce_add_sync(0xFFFFFFFFu, less);
+                    __syncwarp();
+#pragma unroll
+                    for (int t = 0; t < kMaxK / kWarp; ++t) {
+                        uint32_t i = lane + kWarp * t;
+                        if (i < nc && i >= pos && i + 1 < k) Ck[i + 1] = keep[t];
+                    }
+                    if (lane == 0) Ck[pos] = e;
+                    nc = nc + 1 < k ? nc + 1 : k;
+                    __syncwarp();
+                }
+            }
+            clk.mark(kPhRerank);
 
             // ---- merge the new neighbours into the worklist, §4.6-§4.7.
             // Output position = own index + rank in the other list (keys are
-            // unique).  New keys: binary search in the worklist plus a count
-            // among the new keys.  Worklist keys only move right, by the number
-            // of new keys ranked before them; they are updated in place, chunk
-            // by chunk from the end, starting at the chunk of the first
+            // unique).  A new key's rank in the worklist comes from a binary
+            // search, its rank among the new keys from a count; the insertion
+            // points, stored in the order of the new keys, are nondecreasing,
+            // so a worklist entry's shift is one more binary search among
+            // them.  Entries move right only: groups of up to 8 chunks are
+            // read, then written, from the end of the list down to the first
             // insertion point.
             uint32_t npos = 0;               // new position of `best`, plus one
             if (nn > 0) {
+                uint32_t *ins = Nid;         // ids are in the keys now; reuse
                 uint64_t xk[RPL];
-                uint32_t xlo[RPL], xpos[RPL];
+                uint32_t xpos[RPL];
                 uint32_t rmin = 0xFFFFFFFFu;
 #pragma unroll
                 for (int t = 0; t < RPL; ++t) {
                     const uint32_t j = lane + kWarp * t;
                     xk[t] = 0;
-                    xlo[t] = xpos[t] = 0xFFFFFFFFu;
+                    xpos[t] = 0xFFFFFFFFu;
                     if (j < nn) {
                         const uint64_t x = Nk[j];
                         uint32_t lo = 0, hi = nl;
@@ -511,54 +545,54 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                             if ((Lk[mid] >> 1) < (x >> 1)) lo = mid + 1;
                             else hi = mid;
                         }
-                        uint32_t rn = 0;
-                        uint32_t tt = 0;
-                        for (; tt + 4 <= nn; tt += 4) {
+                        uint32_t rn = 0, tt = 0;
+                        for (; tt + 4 <= nn; tt += 4)
                             rn += (Nk[tt] < x) + (Nk[tt + 1] < x) + (Nk[tt + 2] < x) + (Nk[tt + 3] < x);
-                        }
                         for (; tt < nn; ++tt) rn += Nk[tt] < x;
+                        ins[rn] = lo;
                         xk[t] = x;
-                        xlo[t] = lo;
                         xpos[t] = lo + rn;
                         rmin = lo < rmin ? lo : rmin;
                     }
                 }
                 rmin = __reduce_min_sync(0xFFFFFFFFu, rmin);
-                const uint32_t c0 = rmin & ~31u;
-                for (uint32_t i = c0 + lane; i <= nl; i += kWarp) cnt[i] = 0u;
                 __syncwarp();
+                clk.mark(kPhMergeRank);
+                const int32_t cmin = static_cast<int32_t>(rmin >> 5);
+                for (int32_t gtop = static_cast<int32_t>((nl - 1) >> 5); gtop >= cmin; gtop -= 8) {
+                    uint64_t key[8];
+                    uint32_t pos[8];
 #pragma unroll
-                for (int t = 0; t < RPL; ++t)
-                    if (xlo[t] != 0xFFFFFFFFu) atomicAdd(&cnt[xlo[t]], 1u);
-                __syncwarp();
-                // shift(i) = #{new: lo <= i} = nn - #{new: lo > i}
-                uint32_t carry = 0;          // #{new: lo > top of the current chunk}
-                for (int32_t cb = static_cast<int32_t>((nl - 1) & ~31u);
-                     cb >= static_cast<int32_t>(c0); cb -= kWarp) {
-                    const uint32_t i = static_cast<uint32_t>(cb) + lane;
-                    uint32_t s = (i + 1 <= nl) ? cnt[i + 1] : 0u;   // inclusive suffix over lanes
-#pragma unroll
-                    for (int m = 1; m < kWarp; m <<= 1) {
-                        const uint32_t o = __shfl_down_sync(0xFFFFFFFFu, s, m);
-                        if (lane + m < kWarp) s += o;
-                    }
-                    s += carry;
-                    carry = __shfl_sync(0xFFFFFFFFu, s, 0);
-                    uint64_t key = 0;
-                    uint32_t pos = 0xFFFFFFFFu;
-                    if (i < nl) {
-                        key = Lk[i];
-                        pos = i + (nn - s);
-                        if (key == best && pos < L) npos = pos + 1;
+                    for (int g = 0; g < 8; ++g) {
+                        const int32_t c = gtop - g;
+                        const uint32_t i = static_cast<uint32_t>(c) * 32u + lane;
+                        key[g] = 0;
+                        pos[g] = 0xFFFFFFFFu;
+                        if (c >= cmin && i < nl && i >= rmin) {
+                            key[g] = Lk[i];
+                            uint32_t lo = 0, hi = nn;    // #{new: insertion point <= i}
+                            while (lo < hi) {
+                                const uint32_t mid = (lo + hi) >> 1;
+                                if (ins[mid] <= i) lo = mid + 1;
+                                else hi = mid;
+                            }
+                            pos[g] = i + lo;
+                            if (key[g] == best && pos[g] < L) npos = pos[g] + 1;
+                        }
                     }
                     __syncwarp();
-                    if (pos < L) Lk[pos] = key;
+#pragma unroll
+                    for (int g = 0; g < 8; ++g)
+                        if (pos[g] < L) Lk[pos[g]] = key[g];
                     __syncwarp();
                 }
+                clk.mark(kPhMergeShift);
 #pragma unroll
                 for (int t = 0; t < RPL; ++t) {
-                    if (xpos[t] < L) Lk[xpos[t]] = xk[t];
-                    if (xlo[t] != 0xFFFFFFFFu && xk[t] == best && xpos[t] < L) npos = xpos[t] + 1;
+                    if (xpos[t] < L) {
+                        Lk[xpos[t]] = xk[t];
+                        if (xk[t] == best) npos = xpos[t] + 1;
+                    }
                 }
                 __syncwarp();
                 nl = nl + nn < L ? nl + nn : L;
@@ -570,6 +604,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             }
             have_next = npos != 0;
             first = npos - 1;
+            clk.mark(kPhMerge);
         }
 
         // ---- output: re-ranked top-k (§4.8), padded
@@ -598,6 +633,12 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     a.out_dist[o] = __uint_as_float(0x7F800000u);
                 }
             }
+        }
+        if (clk.on && lane == 0) {
+            clk.acc[kPhTotal] = clock64() - t_start;
+#pragma unroll
+            for (int i = 0; i < kPhases; ++i)
+                a.phase_cycles[static_cast<uint64_t>(q) * kPhases + i] = clk.acc[i];
         }
         if (lane == 0) {
             if (a.out_iters) a.out_iters[q] = iters;
