@@ -194,6 +194,15 @@ def run_reference(args):
     return 0
 
 
+FORMS = {
+    # name: (distance mode, placement flags, what it is)
+    "fp32": (0, 0, "plain method: FP32 PQ table, graph and vectors in host memory (Alg. 2)"),
+    "bf16": (1, 0, "reduced precision: BF16 PQ table summed in FP32, host graph and vectors"),
+    "in_memory": (0, 3, "In-memory variant (§5.1): FP32 PQ table, graph and vectors in HBM"),
+    "exact": (2, 3, "Exact-distance variant (§5.2): exact distances, graph and vectors in HBM"),
+}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -215,6 +224,7 @@ def main():
     w = load_workload(args, rank, world, barrier)
     nq, d = w["queries"].shape
     M = 32
+    R = w["adj"].shape[1]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M, device=local)
     stream = torch.cuda.Stream(device=dev)
     sptr = stream.cuda_stream
@@ -223,108 +233,142 @@ def main():
     dist_out = torch.empty((nq, K), dtype=torch.float32, device=dev)
     iters = torch.empty(nq, dtype=torch.int32, device=dev)
     ndist = torch.empty(nq, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    placement = [None]
 
-    def search(L, with_stats=False):
-        p = bang.make_params(bloom_log2=args.bloom_log2,
+    def place(flags):
+        if placement[0] != flags:
+            ix.set_placement(flags)
+            placement[0] = flags
+
+    def search(L, mode, with_stats=False, phase=None):
+        p = bang.make_params(bloom_log2=args.bloom_log2, mode=mode,
                              out_iters=iters if with_stats else None,
-                             out_ndist=ndist if with_stats else None)
+                             out_ndist=ndist if with_stats else None, out_phase_cycles=phase)
         ix.search(q_dev, K, L, ids, dist_out, p, stream=sptr)
 
-    # ---- operating point: smallest L of the sweep with recall@10 >= 0.9
-    sweep = []
-    if args.L is not None:
-        L = args.L
-    else:
-        L = L_SWEEP[-1]
+    def operating_point(mode):
+        """Smallest L of the sweep with recall@10 >= 0.9 (or --L)."""
+        sweep = []
+        if args.L is not None:
+            return args.L, sweep
         for Lc in L_SWEEP:
-            search(Lc)
+            search(Lc, mode)
             stream.synchronize()
             rc = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
             sweep.append({"L": Lc, "recall@10": round(rc, 4)})
             if rc >= TARGET_RECALL:
-                L = Lc
-                break
-    search(L, with_stats=True)
-    stream.synchronize()
-    rec = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
-    it = iters.cpu().numpy().astype(np.int64)
-    nd = ndist.cpu().numpy().astype(np.int64)
+                return Lc, sweep
+        return L_SWEEP[-1], sweep
+
+    def timed(L, mode, steps, clk=None):
+        for _ in range(args.warmup):
+            search(L, mode)
+        stream.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter()
+        for s in range(steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(s & 0xFF)
+                starts[s].record(stream)
+            search(L, mode)
+            ends[s].record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        torch.cuda.synchronize(dev)
+        barrier()
+        step_ms = [starts[s].elapsed_time(ends[s]) for s in range(steps)]
+        total_ms = sum(step_ms)
+        if world > 1:
+            t = torch.tensor([total_ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        return total_ms, step_ms, t_wall
+
+    def measure(name, steps):
+        mode, flags, what = FORMS[name]
+        place(flags)
+        L, sweep = operating_point(mode)
+        search(L, mode, with_stats=True)
+        stream.synchronize()
+        rec = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
+        it = iters.cpu().numpy().astype(np.int64)
+        nd = ndist.cpu().numpy().astype(np.int64)
+        total_ms, step_ms, t_wall = timed(L, mode, steps)
+        return dict(form=name, what=what, mode=mode, placement=flags, L=L,
+                    recall=round(rec, 4), sweep=sweep, iters=it, ndist=nd,
+                    value=nq * world * steps / (total_ms / 1e3), ms_per_step=total_ms / steps,
+                    launch_s=statistics.mean(step_ms) / 1e3, t_wall=t_wall)
+
+    # ---- the two forms of the paper's base method (host graph): time both,
+    # report the faster at recall@10 >= 0.9 with the plain form beside it
+    with ClockSampler(local) as clk:
+        res = {f: measure(f, args.steps) for f in ("fp32", "bf16")}
+    ok = [f for f in ("bf16", "fp32") if res[f]["recall"] >= TARGET_RECALL]
+    head = res[max(ok, key=lambda f: res[f]["value"])] if ok else res["fp32"]
+    variants = {f: measure(f, max(5, args.steps // 5)) for f in ("in_memory", "exact")}
+    place(0)
+    L, mode = head["L"], head["mode"]
+    it, nd = head["iters"], head["ndist"]
 
     # ---- per-phase SM cycles of the fused kernel (one untimed launch): the
     # counterpart of the paper's per-kernel share of GPU time
     phase = torch.zeros((nq, len(bang.PHASES)), dtype=torch.int64, device=dev)
-    ix.search(q_dev, K, L, ids, dist_out, bang.make_params(bloom_log2=args.bloom_log2,
-                                                           out_phase_cycles=phase), stream=sptr)
+    search(L, mode, phase=phase)
     stream.synchronize()
     ph = phase.cpu().numpy().astype(np.float64).sum(0)
     phases = {name: round(float(ph[i] / ph[-1]), 4) for i, name in enumerate(bang.PHASES[:-1])}
     phases["cycles_per_expansion"] = round(float(ph[-1] / max(1, it.sum())), 1)
 
     # ---- algorithmic bytes per launch (one launch = the whole batch)
-    R = w["adj"].shape[1]
     host_bytes = int(it.sum()) * (R * 4 + d * 1)           # neighbour row + full vector per expansion
     hbm_bytes = int(nd.sum()) * M + nq * d + nq * K * 8 + 256 * d * 4
-
-    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
-    for _ in range(args.warmup):
-        search(L)
-    stream.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    barrier()
-    torch.cuda.synchronize(dev)
-    with ClockSampler(local) as clk:
-        t_wall = time.perf_counter()
-        for s in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.fill_(s & 0xFF)
-                starts[s].record(stream)
-            search(L)
-            ends[s].record(stream)
-        stream.synchronize()
-        t_wall = time.perf_counter() - t_wall
-    torch.cuda.synchronize(dev)
-    barrier()
-    step_ms = [starts[s].elapsed_time(ends[s]) for s in range(args.steps)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = nq * world * args.steps / (total_ms / 1e3)
-    launch_s = statistics.mean(step_ms) / 1e3
+    launch_s = head["launch_s"]
 
     # ---- end to end through the C ABI: pinned host queries and results
     q_host = torch.from_numpy(w["queries"]).pin_memory()
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+    hp = bang.make_params(bloom_log2=args.bloom_log2, mode=mode)
     for _ in range(2):
-        ix.search(q_host, K, L, ids_h, dist_h, bang.make_params(bloom_log2=args.bloom_log2),
-                  stream=sptr)
+        ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))
     t0 = time.perf_counter()
     for _ in range(e2e_steps):
-        ix.search(q_host, K, L, ids_h, dist_h, bang.make_params(bloom_log2=args.bloom_log2),
-                  stream=sptr)
+        ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    search(L, mode)
+    stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
 
     link = bang.bang_probe_host_link(local, 1 << 30, R * 4)
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_gbs = hbm_bytes / launch_s / 1e9
+
+    def brief(r):
+        return {"what": r["what"], "value": r["value"], "ms_per_step": r["ms_per_step"],
+                "L": r["L"], "recall@10": r["recall"], "sweep": r["sweep"],
+                "mean_iterations": float(r["iters"].mean())}
+
     line = {
-        "metric": "queries/s at recall@10=0.9", "value": value, "unit": "queries/s",
+        "metric": "queries/s at recall@10=0.9", "value": head["value"], "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "L": L, "recall@10": round(rec, 4), "k": K,
-                   "bloom_log2": args.bloom_log2, "sweep": sweep,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16-table/f32" if mode == 1 else "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "form": head["form"], "form_what": head["what"],
+                   "L": L, "recall@10": head["recall"], "k": K,
+                   "bloom_log2": args.bloom_log2, "sweep": head["sweep"],
                    "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
                    "phase_share": phases,
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "l2": "512 MB flush written between timed steps",
                    "n": int(w["base"].shape[0]), "nq": nq},
+        "plain_form": brief(res["fp32"]),
+        "forms": {f: brief(r) for f, r in list(res.items()) + list(variants.items())},
         "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": hbm_gbs / hbm_peak, "traffic": None,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
@@ -337,16 +381,17 @@ def main():
                       "copy_engine_gbs": link["h2d_copy_gbs"],
                       "load_latency_ns": link["latency_ns"],
                       "algorithmic_bytes_per_launch": host_bytes,
-                      "note": "neighbour rows and full vectors read in place from page-locked "
-                              "host memory"},
+                      "note": "binding link: neighbour rows and full vectors read in place from "
+                              "page-locked host memory"},
         "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d,
                 "d2h_bytes_per_step": nq * K * 8},
         "gpu_launches": args.steps,
         "clocks": clk.summary(),
-        "wall_s_timed_region": t_wall,
+        "wall_s_timed_region": res["fp32"]["t_wall"] + res["bf16"]["t_wall"],
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, L, min(args.cpu_sample, nq), args.bloom_log2)
+        line["cpu_baseline"] = cpu_baseline(w, res["fp32"]["L"], min(args.cpu_sample, nq),
+                                            args.bloom_log2)
     ix.close()
     if rank == 0:
         print(json.dumps(line), flush=True)

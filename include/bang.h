@@ -71,7 +71,19 @@ typedef struct bang_search_params {
      * merge shifting of the worklist (§4.6-§4.7), and the query's total: the
      * paper's per-kernel GPU-time breakdown (§7.3) for the fused kernel. */
     unsigned long long *out_phase_cycles;
+    /* Distance mode (bang_mode): PQ distances from an FP32 table (0, the
+     * default, bit-exact with the reference order), from a BF16 table summed
+     * in FP32 (1, the reduced-precision form: half the table's shared memory),
+     * or exact distances in the loop without table or re-rank (2, the
+     * paper's Exact-distance variant, §5.2; results are the first k entries
+     * of the final worklist). */
+    uint32_t mode;
 } bang_search_params;
+
+typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2 } bang_mode;
+
+/* Placement flags for bang_set_placement. */
+enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2 };
 
 /* Create an empty index bound to CUDA device `device`.  *out receives an
  * opaque handle owned by the library; free it with bang_destroy. */
@@ -129,6 +141,15 @@ int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype);
 int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
                 const bang_search_params *params, uint32_t *out_ids, float *out_dist,
                 void *stream);
+
+/* Choose where the search reads the graph and the full vectors: 0 keeps
+ * both in host memory, read in place (Alg. 2); BANG_GRAPH_IN_HBM and/or
+ * BANG_VECTORS_IN_HBM copy the registered arrays into device memory once
+ * (the paper's In-memory variant, §5.1; BANG_MODE_EXACT usually wants the
+ * vectors there too).  The copies are owned by the library and dropped when
+ * the corresponding array is registered again or the flag is cleared.
+ * Blocks until the copies are done.  BANG_ENOMEM if the device is full. */
+int bang_set_placement(bang_index *ix, uint32_t flags);
 
 /* Release device memory, unregister host memory registered by the library
  * and free the handle.  NULL is accepted. */

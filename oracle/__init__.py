@@ -86,8 +86,8 @@ def lib():
         L.orc_bloom_test.argtypes = [vp, u32, u32]
         L.orc_bloom_test.restype = i32
         L.orc_bloom_insert.argtypes = [vp, u32, u32]
-        L.orc_search.argtypes = [ctypes.POINTER(OrcIndex), vp, u32, u32, u32, u32, u32, vp, vp,
-                                 vp, vp, vp, vp, u32, i32]
+        L.orc_search.argtypes = [ctypes.POINTER(OrcIndex), vp, i32, u32, u32, u32, u32, u32, vp,
+                                 vp, vp, vp, vp, vp, u32, i32]
         L.orc_search.restype = i32
         L.orc_max_threads.restype = i32
         L.orc_bruteforce_knn.argtypes = [vp, vp, i32, u64, u32, u32, u32, vp, vp, i32]
@@ -229,7 +229,8 @@ class Index:
                            self.codes.ctypes.data, self.adj.ctypes.data,
                            self.base.ctypes.data)
 
-    def search(self, queries, k, L, log2z=16, iter_cap=None, trace_cap=0, nthreads=0):
+    def search(self, queries, k, L, log2z=16, iter_cap=None, trace_cap=0, nthreads=0, exact=False):
+        """Alg. 2 search; exact=True runs the Exact-distance variant (§5.2)."""
         q = np.ascontiguousarray(queries, dtype=self.base.dtype)
         nq = q.shape[0]
         if iter_cap is None:
@@ -240,7 +241,8 @@ class Index:
         status = np.zeros(nq, np.int32)
         ndist = np.zeros(nq, np.uint64)
         trace = np.zeros((nq, trace_cap), np.uint32) if trace_cap else None
-        rc = lib().orc_search(ctypes.byref(self._s), _p(q), nq, k, L, log2z, iter_cap, _p(ids),
+        rc = lib().orc_search(ctypes.byref(self._s), _p(q), 1 if exact else 0, nq, k, L, log2z,
+                              iter_cap, _p(ids),
                               _p(dist), _p(iters), _p(status), _p(ndist), _p(trace), trace_cap,
                               nthreads)
         if rc != 0:

@@ -31,7 +31,8 @@
  *   orc_fnv1a32/_fnv1a64     §4.3, §6.3 (two FNV-1a hash functions)
  *   orc_bloom_*              §4.3 (per-query Bloom filter of visited nodes)
  *   orc_exact_dist           §4.8 (exact distance used by the re-rank)
- *   orc_search               Alg. 1, Alg. 2, §4.3-§4.8
+ *   orc_search               Alg. 1, Alg. 2, §4.3-§4.8; mode 1: the Exact-distance
+ *                            variant of §5.2 (exact distances, no table, no re-rank)
  *   orc_bruteforce_knn       §6.3 (ground truth S for k-recall@k)
  */
 #include <math.h>
@@ -520,7 +521,7 @@ static int dpair_cmp_stable(const void *pa, const void *pb) { return dpair_cmp(p
  *    the first k; pad with id 0xFFFFFFFF and distance +inf.
  * The eager choice of the next candidate (§4.5) is the first unvisited
  * entry after the merge, so it does not appear as a separate step. */
-static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t Lsz,
+static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k, uint32_t Lsz,
                        uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
                        uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
                        uint32_t *trace, uint32_t trace_cap)
@@ -533,16 +534,18 @@ static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t 
     orc_entry *Lst = (orc_entry *)malloc(sizeof(orc_entry) * (Lsz + R + 1));
     uint32_t *Np = (uint32_t *)malloc(sizeof(uint32_t) * (R + 1));
     uint32_t ccap = iter_cap + 1, nc = 0, nl, iters = 0;
-    orc_dpair *C = (orc_dpair *)malloc(sizeof(orc_dpair) * ccap);
+    orc_dpair *C = (orc_dpair *)malloc(sizeof(orc_dpair) * (ccap > Lsz + R + 1 ? ccap : Lsz + R + 1));
     uint64_t ndist = 0;
     int32_t status = 0;
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
 
     for (i = 0; i < d; i++) qf[i] = elem_f(q, ix->dtype, i);
-    orc_adc_table_f32(qf, M, ix->off, ix->codebook, T);
+    if (mode == 0) orc_adc_table_f32(qf, M, ix->off, ix->codebook, T);
 
     Lst[0].id = ix->medoid;
-    Lst[0].dist = orc_adc_dist_f32(T, M, ix->codes + (uint64_t)ix->medoid * M);
+    Lst[0].dist = mode == 0 ? orc_adc_dist_f32(T, M, ix->codes + (uint64_t)ix->medoid * M)
+                            : (float)orc_exact_dist(q, (const unsigned char *)ix->base +
+                                                    (uint64_t)ix->medoid * d * esz, ix->dtype, d);
     Lst[0].visited = 0;
     ndist++;
     nl = 1;
@@ -558,10 +561,12 @@ static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t 
             uint32_t us = Lst[u].id;
             if (trace && iters < trace_cap) trace[iters] = us;
             iters++;
-            C[nc].id = us;
-            C[nc].dist = orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)us * d * esz,
-                                        ix->dtype, d);
-            nc++;
+            if (mode == 0) {
+                C[nc].id = us;
+                C[nc].dist = orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)us * d * esz,
+                                            ix->dtype, d);
+                nc++;
+            }
             for (r = 0; r < R; r++) {
                 uint32_t nb = ix->adj[(uint64_t)us * R + r];
                 if (nb == ORC_NONE) continue;
@@ -572,7 +577,10 @@ static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t 
         nadd = 0;
         for (i = 0; i < nn; i++) {
             Lst[nl + nadd].id = Np[i];
-            Lst[nl + nadd].dist = orc_adc_dist_f32(T, M, ix->codes + (uint64_t)Np[i] * M);
+            Lst[nl + nadd].dist =
+                mode == 0 ? orc_adc_dist_f32(T, M, ix->codes + (uint64_t)Np[i] * M)
+                          : (float)orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)Np[i] * d * esz,
+                                                  ix->dtype, d);
             Lst[nl + nadd].visited = 0;
             nadd++;
         }
@@ -581,6 +589,10 @@ static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t 
         nl = (nl + nadd < Lsz) ? nl + nadd : Lsz;
     }
 
+    if (mode != 0) {                    /* Alg. 1: the k nearest entries of the worklist */
+        nc = 0;
+        for (i = 0; i < nl; i++) { C[nc].id = Lst[i].id; C[nc].dist = (double)Lst[i].dist; nc++; }
+    }
     qsort(C, nc, sizeof(orc_dpair), dpair_cmp_stable);
     for (i = 0; i < k; i++) {
         if (i < nc) { out_ids[i] = C[i].id; out_dist[i] = (float)C[i].dist; }
@@ -592,14 +604,14 @@ static void search_one(const orc_index *ix, const void *q, uint32_t k, uint32_t 
     free(qf); free(T); free(bits); free(Lst); free(Np); free(C);
 }
 
-int orc_search(const orc_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
-               uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
+int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, uint32_t k,
+               uint32_t L, uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
                uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
                uint32_t *trace, uint32_t trace_cap, int nthreads)
 {
     int64_t qi;
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
-    if (k == 0 || L < k || ix->M == 0 || ix->d == 0) return -1;
+    if (k == 0 || L < k || ix->M == 0 || ix->d == 0 || mode < 0 || mode > 1) return -1;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
@@ -607,7 +619,7 @@ int orc_search(const orc_index *ix, const void *queries, uint32_t nq, uint32_t k
     (void)nthreads;
 #endif
     for (qi = 0; qi < (int64_t)nq; qi++) {
-        search_one(ix, (const unsigned char *)queries + (uint64_t)qi * ix->d * esz, k, L, log2z,
+        search_one(ix, (const unsigned char *)queries + (uint64_t)qi * ix->d * esz, mode, k, L, log2z,
                    iter_cap, out_ids + (uint64_t)qi * k, out_dist + (uint64_t)qi * k,
                    out_iters ? out_iters + qi : NULL, out_status ? out_status + qi : NULL,
                    out_ndist ? out_ndist + qi : NULL,

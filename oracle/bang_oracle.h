@@ -50,8 +50,10 @@ uint64_t orc_fnv1a64_bytes(const unsigned char *b, uint32_t len);
 void orc_bloom_positions(uint32_t id, uint32_t log2z, uint32_t *pos2);
 int orc_bloom_test(const uint32_t *bits, uint32_t log2z, uint32_t id);
 void orc_bloom_insert(uint32_t *bits, uint32_t log2z, uint32_t id);
-int orc_search(const orc_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
-               uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
+/* mode 0: PQ distances + re-rank of the expanded nodes (§4); mode 1: exact
+ * distances in the loop, no re-rank, result = the worklist's first k (§5.2). */
+int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, uint32_t k,
+               uint32_t L, uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
                uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
                uint32_t *trace, uint32_t trace_cap, int nthreads);
 int orc_max_threads(void);

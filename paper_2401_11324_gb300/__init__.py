@@ -33,7 +33,8 @@ class bang_search_params(ctypes.Structure):
     _fields_ = [("bloom_log2", ctypes.c_uint32), ("iter_cap", ctypes.c_uint32),
                 ("out_iters", ctypes.c_void_p), ("out_status", ctypes.c_void_p),
                 ("out_ndist", ctypes.c_void_p), ("trace", ctypes.c_void_p),
-                ("trace_cap", ctypes.c_uint32), ("out_phase_cycles", ctypes.c_void_p)]
+                ("trace_cap", ctypes.c_uint32), ("out_phase_cycles", ctypes.c_void_p),
+                ("mode", ctypes.c_uint32)]
 
 
 class bang_link_probe(ctypes.Structure):
@@ -68,11 +69,12 @@ def _load():
     L.bang_search.argtypes = [vp, vp, u32, u32, u32, ctypes.POINTER(bang_search_params), vp, vp,
                               vp]
     L.bang_destroy.argtypes = [vp]
+    L.bang_set_placement.argtypes = [vp, u32]
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
     L.bang_probe_host_link.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
-              "bang_search", "bang_destroy"):
+              "bang_search", "bang_destroy", "bang_set_placement"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -128,10 +130,14 @@ PHASES = ("table", "select", "filter", "distance", "next", "rerank", "merge", "m
           "merge_shift", "total")
 
 
+BANG_MODE_PQ_F32, BANG_MODE_PQ_BF16, BANG_MODE_EXACT = 0, 1, 2
+BANG_GRAPH_IN_HBM, BANG_VECTORS_IN_HBM = 1, 2
+
+
 def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
-                trace=None, trace_cap=0, out_phase_cycles=None):
+                trace=None, trace_cap=0, out_phase_cycles=None, mode=0):
     return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
-                              _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles))
+                              _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles), mode)
 
 
 def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
@@ -139,6 +145,10 @@ def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
     s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
     return _check(lib().bang_search(ix, _ptr(queries), nq, k, L, p, _ptr(out_ids),
                                     _ptr(out_dist), s))
+
+
+def bang_set_placement(ix, flags):
+    return _check(lib().bang_set_placement(ix, flags))
 
 
 def bang_destroy(ix):
@@ -166,6 +176,9 @@ class Index:
         bang_load_pq(self.h, self.d, M, self._codebook, self._codes, self.n)
         bang_register_graph(self.h, self.adj, self.R, self.medoid)
         bang_register_vectors(self.h, self.base, self.dtype)
+
+    def set_placement(self, flags):
+        return bang_set_placement(self.h, flags)
 
     def search(self, queries, k, L, out_ids, out_dist, params=None, stream=None):
         nq = queries.shape[0]

@@ -12,7 +12,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libbang.so")
-SOURCES = ["bang_api.cu", "link_probe.cu"]
+SOURCES = ["bang_api.cu", "link_probe.cu", "search_f32.cu", "search_bf16.cu", "search_exact.cu"]
 HEADERS = ["search_kernel.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -34,16 +34,28 @@ def _stale():
 
 
 def build(force=False, verbose=False):
+    """Compile every translation unit in parallel, then link libbang.so."""
     if not force and not _stale():
         return LIB
-    cmd = [nvcc(), *ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false",
-           "-Xcompiler", "-fPIC", "-shared", "-I", os.path.join(ROOT, "include"),
-           "-o", LIB + ".tmp"] + [os.path.join(CSRC, f) for f in SOURCES]
+    flags = [*ARCH, "-O3", "-lineinfo", "-std=c++17", "--fmad=false", "-Xcompiler", "-fPIC",
+             "-I", os.path.join(ROOT, "include")]
     if verbose:
-        cmd.insert(1, "-Xptxas=-v")
-        print(" ".join(cmd), flush=True)
-    subprocess.check_call(cmd, cwd=CSRC)
+        flags.append("-Xptxas=-v")
+    objs, procs = [], []
+    for f in SOURCES:
+        obj = os.path.join(CSRC, os.path.splitext(f)[0] + ".o")
+        objs.append(obj)
+        cmd = [nvcc(), *flags, "-c", os.path.join(CSRC, f), "-o", obj]
+        if verbose:
+            print(" ".join(cmd), flush=True)
+        procs.append((f, subprocess.Popen(cmd, cwd=CSRC)))
+    failed = [f for f, p in procs if p.wait() != 0]
+    if failed:
+        raise RuntimeError("nvcc failed on %s" % ", ".join(failed))
+    subprocess.check_call([nvcc(), *ARCH, "-shared", "-o", LIB + ".tmp", *objs], cwd=CSRC)
     os.replace(LIB + ".tmp", LIB)
+    for o in objs:
+        os.remove(o)
     return LIB
 
 

@@ -146,6 +146,9 @@ struct bang_index {
     HostView adj, base;
     bool have_pq = false, have_graph = false, have_vectors = false;
     DevBuf staging;
+    // In-memory placement (§5.1): device copies of the graph and/or vectors.
+    DevBuf adj_hbm, base_hbm;
+    uint32_t placement = 0;
 };
 
 namespace {
@@ -203,33 +206,6 @@ bool validate_graph(const uint32_t *adj, uint64_t n, uint32_t R, uint64_t *bad_r
     for (unsigned t = 0; t < nt; ++t)
         if (bad[t] != UINT64_MAX) { *bad_row = bad[t]; return false; }
     return true;
-}
-
-template <int DT, int RPL, int DCH> int launch_one(const bang::SearchArgs &a, size_t smem,
-                                                  cudaStream_t st)
-{
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, []() {
-        err = cudaFuncSetAttribute(bang::search_kernel<DT, RPL, DCH>,
-                                   cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-    });
-    if (err != cudaSuccess)
-        return fail(BANG_ECUDA, "cudaFuncSetAttribute failed: %s", cudaGetErrorString(err));
-    bang::search_kernel<DT, RPL, DCH><<<a.nq, 32, smem, st>>>(a);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(e));
-    return BANG_OK;
-}
-
-// Neighbours per lane (R <= 32, 64, 128) and 128-dimension chunks per lane
-// (d <= 128, 512) are compile-time, so no lane works on padding.
-template <int DT> int launch_dt(const bang::SearchArgs &a, size_t smem, cudaStream_t st)
-{
-    const bool narrow = a.d <= 128;
-    if (a.R <= 32) return narrow ? launch_one<DT, 1, 1>(a, smem, st) : launch_one<DT, 1, 4>(a, smem, st);
-    if (a.R <= 64) return narrow ? launch_one<DT, 2, 1>(a, smem, st) : launch_one<DT, 2, 4>(a, smem, st);
-    return narrow ? launch_one<DT, 4, 1>(a, smem, st) : launch_one<DT, 4, 4>(a, smem, st);
 }
 
 }  // namespace
@@ -301,6 +277,8 @@ int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_
     DeviceGuard g(ix->device);
     if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
     ix->adj.release();
+    ix->adj_hbm.release();
+    ix->placement &= ~(uint32_t)BANG_GRAPH_IN_HBM;
     ix->have_graph = false;
     int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->adj);
     if (rc) return rc;
@@ -319,6 +297,8 @@ int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype)
     DeviceGuard g(ix->device);
     if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
     ix->base.release();
+    ix->base_hbm.release();
+    ix->placement &= ~(uint32_t)BANG_VECTORS_IN_HBM;
     ix->have_vectors = false;
     int rc = map_host(base, (size_t)ix->n * ix->d * elem_size(dtype), ix->base);
     if (rc) return rc;
@@ -349,7 +329,8 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     uint32_t cap = p.iter_cap ? p.iter_cap : 8u * L + 64u;
     if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search: trace_cap is 0");
 
-    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d);
+    if (p.mode > 2) return fail(BANG_EINVAL, "bang_search: unknown mode %u", p.mode);
+    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search: %u bytes of shared memory per query exceed 227 KB "
                     "(reduce L, k, M or bloom_log2)", lay.total);
@@ -395,8 +376,8 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.codebook = ix->codebook;
     a.off = ix->off;
     a.codes = ix->codes;
-    a.adj = static_cast<const uint32_t *>(ix->adj.dev);
-    a.base = ix->base.dev;
+    a.adj = static_cast<const uint32_t *>((ix->placement & BANG_GRAPH_IN_HBM) ? ix->adj_hbm.p : ix->adj.dev);
+    a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
     a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
     a.medoid = ix->medoid;
     a.nq = nq; a.k = k; a.L = L; a.log2z = log2z; a.iter_cap = cap;
@@ -413,15 +394,14 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
         // 4-element vector loads need rows that start on 16-byte boundaries
         const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
         const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
-        a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) && (ba % 16 == 0) ? 1u : 0u;
+        a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;
+        a.vecb_ok = (ix->d % 4 == 0) && (ba % 16 == 0) ? 1u : 0u;
     }
-    int rc;
-    switch (ix->dtype) {
-    case BANG_U8: rc = launch_dt<0>(a, lay.total, st); break;
-    case BANG_I8: rc = launch_dt<1>(a, lay.total, st); break;
-    default: rc = launch_dt<2>(a, lay.total, st); break;
-    }
-    if (rc) return rc;
+    cudaError_t le;
+    if (p.mode == 0) le = bang::launch_search_f32(a, ix->dtype, lay.total, st);
+    else if (p.mode == 1) le = bang::launch_search_bf16(a, ix->dtype, lay.total, st);
+    else le = bang::launch_search_exact(a, ix->dtype, lay.total, st);
+    if (le != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(le));
     for (int i = 1; i < 8; ++i) {
         Slot &s = slots[i];
         if (s.user && !s.dev)
@@ -429,6 +409,36 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
                                      cudaMemcpyDeviceToHost, st));
     }
     if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
+    return BANG_OK;
+}
+
+int bang_set_placement(bang_index *ix, uint32_t flags)
+{
+    if (!ix) return fail(BANG_EINVAL, "bang_set_placement: index is NULL");
+    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM))
+        return fail(BANG_EINVAL, "bang_set_placement: unknown flags 0x%x", flags);
+    if ((flags & BANG_GRAPH_IN_HBM) && !ix->have_graph)
+        return fail(BANG_ESTATE, "bang_set_placement: register the graph first");
+    if ((flags & BANG_VECTORS_IN_HBM) && !ix->have_vectors)
+        return fail(BANG_ESTATE, "bang_set_placement: register the vectors first");
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    CUDA_TRY(cudaDeviceSynchronize());
+    if (flags & BANG_GRAPH_IN_HBM) {
+        const size_t bytes = (size_t)ix->n * ix->R * sizeof(uint32_t);
+        CUDA_TRY(ix->adj_hbm.ensure(bytes));
+        CUDA_TRY(cudaMemcpy(ix->adj_hbm.p, ix->adj.host, bytes, cudaMemcpyHostToDevice));
+    } else {
+        ix->adj_hbm.release();
+    }
+    if (flags & BANG_VECTORS_IN_HBM) {
+        const size_t bytes = (size_t)ix->n * ix->d * elem_size(ix->dtype);
+        CUDA_TRY(ix->base_hbm.ensure(bytes));
+        CUDA_TRY(cudaMemcpy(ix->base_hbm.p, ix->base.host, bytes, cudaMemcpyHostToDevice));
+    } else {
+        ix->base_hbm.release();
+    }
+    ix->placement = flags;
     return BANG_OK;
 }
 
@@ -443,6 +453,8 @@ int bang_destroy(bang_index *ix)
         ix->adj.release();
         ix->base.release();
         ix->staging.release();
+        ix->adj_hbm.release();
+        ix->base_hbm.release();
     }
     delete ix;
     return BANG_OK;

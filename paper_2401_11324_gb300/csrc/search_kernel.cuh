@@ -27,6 +27,7 @@
 #pragma once
 
 #include <cstdint>
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 namespace bang {
@@ -40,6 +41,14 @@ constexpr int kMaxK = 256;
 constexpr int kMaxL = 1024;
 constexpr int kRegK = 32;         // k up to this keeps the re-rank top-k in registers
 
+// Distance modes of the search loop.
+//  kModeF32:   PQ distances from an FP32 table (the bit-exact form, §4.1, §4.4)
+//  kModeBF16:  PQ distances from a BF16 table, summed in FP32 (reduced form:
+//              half the table's shared memory, so more queries per SM)
+//  kModeExact: exact distances to the full vectors in the loop, no table and
+//              no re-rank (the paper's Exact-distance variant, §5.2)
+enum { kModeF32 = 0, kModeBF16 = 1, kModeExact = 2 };
+
 struct SearchArgs {
     const void *queries;      // device, nq*d elements
     const float *codebook;    // device, 256*d
@@ -49,7 +58,8 @@ struct SearchArgs {
     const void *base;         // device-accessible (mapped host), n*d
     uint32_t n, d, M, Mpad, R, medoid;
     uint32_t nq, k, L, log2z, iter_cap;
-    uint32_t vec_ok;          // rows of `base` and `queries` allow 4-element vector loads
+    uint32_t vec_ok;          // rows of `queries` allow 4-element vector loads
+    uint32_t vecb_ok;         // rows of `base` allow 4-element vector loads
     uint32_t *out_ids;        // device, nq*k
     float *out_dist;          // device, nq*k
     uint32_t *out_iters;      // device or null
@@ -68,15 +78,17 @@ enum Phase { kPhTable = 0, kPhSelect, kPhFilter, kPhDistance, kPhNext, kPhRerank
 struct SmemLayout {
     uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_Ck, off_q, off_offs, total;
     __host__ __device__ static uint32_t up16(uint32_t x) { return (x + 15u) & ~15u; }
-    __host__ __device__ SmemLayout(uint32_t M, uint32_t log2z, uint32_t L, uint32_t k, uint32_t d)
+    __host__ __device__ SmemLayout(uint32_t M, uint32_t log2z, uint32_t L, uint32_t k, uint32_t d,
+                                   int mode)
     {
         uint32_t o = 0;
-        off_T = o;      o += up16(M * 256u * 4u);
+        const uint32_t tsz = mode == kModeF32 ? 4u : (mode == kModeBF16 ? 2u : 0u);
+        off_T = o;      o += up16(M * 256u * tsz);
         off_bloom = o;  o += up16(((1u << log2z) / 8u) < 4u ? 4u : (1u << log2z) / 8u);
         off_L = o;      o += up16(L * 8u);
         off_Nk = o;     o += up16(kMaxR * 8u);
         off_Nid = o;    o += up16(kMaxR * 4u);
-        off_Ck = o;     o += up16(k > (uint32_t)kRegK ? k * 8u : 0u);
+        off_Ck = o;     o += up16(k > (uint32_t)kRegK && mode != kModeExact ? k * 8u : 0u);
         off_q = o;      o += up16(d * 4u);
         off_offs = o;   o += up16((M + 1u) * 4u);
         total = o;
@@ -140,8 +152,17 @@ __device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int delta)
     return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
+// Table entry as FP32: FP32 tables are read directly, BF16 entries widened.
+template <int MODE> __device__ __forceinline__ float table_entry(const void *T, uint32_t i)
+{
+    if (MODE == kModeBF16)
+        return __uint_as_float(static_cast<uint32_t>(static_cast<const uint16_t *>(T)[i]) << 16);
+    return static_cast<const float *>(T)[i];
+}
+
 // PQ distance of one code row (§4.4), in the fixed order described above.
-__device__ __forceinline__ float adc_distance(const float *__restrict__ T,
+template <int MODE>
+__device__ __forceinline__ float adc_distance(const void *__restrict__ T,
                                               const uint8_t *__restrict__ row, uint32_t M,
                                               uint32_t Mpad)
 {
@@ -152,16 +173,16 @@ __device__ __forceinline__ float adc_distance(const float *__restrict__ T,
     for (uint32_t c16 = 0; c16 < Mpad / 16u; ++c16) {
         uint4 v = __ldg(row16 + c16);
         uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        const float *Tc = T + c16 * 16u * 256u;
+        const uint32_t tc = c16 * 16u * 256u;
         if (c16 * 16u + 16u <= M) {
 #pragma unroll
             for (int b = 0; b < 16; ++b)
-                p[b & 7] = __fadd_rn(p[b & 7], Tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)]);
+                p[b & 7] = __fadd_rn(p[b & 7], table_entry<MODE>(T, tc + b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)));
         } else {
 #pragma unroll
             for (int b = 0; b < 16; ++b)
                 if (c16 * 16u + b < M)
-                    p[b & 7] = __fadd_rn(p[b & 7], Tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)]);
+                    p[b & 7] = __fadd_rn(p[b & 7], table_entry<MODE>(T, tc + b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)));
         }
     }
 #pragma unroll
@@ -253,7 +274,7 @@ template <int DT, int RPL, int DCH> struct NodeData {
     VecShare<DT, DCH> x;
 };
 
-template <int DT, int RPL, int DCH>
+template <int DT, int RPL, int DCH, bool WITH_VECTOR>
 __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int lane,
                                           NodeData<DT, RPL, DCH> &nd)
 {
@@ -264,18 +285,28 @@ __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int l
         uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
         nd.nb[r] = i < a.R ? row[i] : kNone;
     }
-    const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
-    load_share<DT, DCH>(x, a.d, a.vec_ok != 0, lane, nd.x);
+    if (WITH_VECTOR) {
+        const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
+        load_share<DT, DCH>(x, a.d, a.vecb_ok != 0, lane, nd.x);
+    }
 }
 
-// PQ distance table of one query into shared memory (§4.1).
+template <int MODE> __device__ __forceinline__ void store_entry(void *Ts, uint32_t c, float v)
+{
+    if (MODE == kModeBF16) static_cast<uint16_t *>(Ts)[c] = __bfloat16_as_ushort(__float2bfloat16_rn(v));
+    else static_cast<float *>(Ts)[c] = v;
+}
+
+// PQ distance table of one query into shared memory (§4.1); entries are
+// computed in FP32 and stored in the mode's precision.
+template <int MODE>
 __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv,
-                                            const uint32_t *offs, float *T, int lane)
+                                            const uint32_t *offs, void *T, int lane)
 {
     for (uint32_t s = 0; s < a.M; ++s) {
         const uint32_t o = offs[s], ds = offs[s + 1] - o;
         const float *cb = a.codebook + 256u * o;
-        float *Ts = T + s * 256u;
+        unsigned char *Ts = static_cast<unsigned char *>(T) + s * 256u * (MODE == kModeBF16 ? 2u : 4u);
         if (ds == 4 && (o & 3u) == 0) {
             const float4 q4 = *reinterpret_cast<const float4 *>(qv + o);
 #pragma unroll
@@ -287,7 +318,7 @@ __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv
                 df = __fsub_rn(q4.y, c4.y); acc = __fmaf_rn(df, df, acc);
                 df = __fsub_rn(q4.z, c4.z); acc = __fmaf_rn(df, df, acc);
                 df = __fsub_rn(q4.w, c4.w); acc = __fmaf_rn(df, df, acc);
-                Ts[c] = acc;
+                store_entry<MODE>(Ts, c, acc);
             }
         } else if (ds == 2 && (o & 1u) == 0) {
             const float2 q2 = *reinterpret_cast<const float2 *>(qv + o);
@@ -298,7 +329,7 @@ __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv
                 float acc = 0.0f, df;
                 df = __fsub_rn(q2.x, c2.x); acc = __fmaf_rn(df, df, acc);
                 df = __fsub_rn(q2.y, c2.y); acc = __fmaf_rn(df, df, acc);
-                Ts[c] = acc;
+                store_entry<MODE>(Ts, c, acc);
             }
         } else {
 #pragma unroll 2
@@ -310,7 +341,7 @@ __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv
                     float df = __fsub_rn(qv[o + j], __ldg(cc + j));
                     acc = __fmaf_rn(df, df, acc);
                 }
-                Ts[c] = acc;
+                store_entry<MODE>(Ts, c, acc);
             }
         }
     }
@@ -335,14 +366,15 @@ struct PhaseClock {
     }
 };
 
-template <int DT, int RPL, int DCH>
+template <int DT, int RPL, int DCH, int MODE>
 __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 {
     using E = typename Elem<DT>::T;
+    constexpr bool kPQ = MODE != kModeExact;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x;
-    const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d);
-    float *T = reinterpret_cast<float *>(smem + lay.off_T);
+    const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d, MODE);
+    void *T = smem + lay.off_T;
     uint32_t *bloom = reinterpret_cast<uint32_t *>(smem + lay.off_bloom);
     uint64_t *Lk = reinterpret_cast<uint64_t *>(smem + lay.off_L);
     uint64_t *Nk = reinterpret_cast<uint64_t *>(smem + lay.off_Nk);
@@ -368,15 +400,24 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         load_share<DT, DCH>(qp, d, a.vec_ok != 0, lane, qs);
         for (uint32_t w = lane; w < nwords; w += kWarp) bloom[w] = 0u;
         __syncwarp();
-        build_table(a, qv, offs, T, lane);
+        if (kPQ) build_table<MODE>(a, qv, offs, T, lane);
         __syncwarp();
         clk.mark(kPhTable);
 
         // ---- start: worklist = {medoid}, medoid marked seen
+        uint32_t dm_bits = 0;
+        if (!kPQ) {
+            VecShare<DT, DCH> xs;
+            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(a.medoid) * d, d,
+                                a.vecb_ok != 0, lane, xs);
+            dm_bits = exact_distance_bits<DT, DCH>(qs, xs);
+        }
         if (lane == 0) {
             const uint32_t s = a.medoid;
-            float dm = adc_distance(T, a.codes + static_cast<uint64_t>(s) * a.Mpad, a.M, a.Mpad);
-            Lk[0] = make_key(__float_as_uint(dm), s);
+            if (kPQ)
+                dm_bits = __float_as_uint(adc_distance<MODE>(T, a.codes + static_cast<uint64_t>(s) * a.Mpad,
+                                                             a.M, a.Mpad));
+            Lk[0] = make_key(dm_bits, s);
             uint32_t p1 = fnv1a32_id(s) & zmask, p2 = fnv1a64_id_folded(s) & zmask;
             bloom[p1 >> 5] |= 1u << (p1 & 31u);
             bloom[p2 >> 5] |= 1u << (p2 & 31u);
@@ -387,7 +428,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         uint64_t ck = ~0ull;               // register top-k (k <= kRegK): lane i holds rank i
         uint32_t cur = a.medoid;
         NodeData<DT, RPL, DCH> nd;
-        load_node<DT, RPL, DCH>(a, cur, lane, nd);
+        load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
         __syncwarp();
 
         while (have_next) {
@@ -408,9 +449,9 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             ++iters;
             if (u != cur) {  // the prefetched node is always u*; reload if not
                 cur = u;
-                load_node<DT, RPL, DCH>(a, cur, lane, nd);
+                load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
             }
-            const VecShare<DT, DCH> xu = nd.x;   // u*'s vector, for the re-rank below
+            const VecShare<DT, DCH> xu = nd.x;   // u*'s vector, for the re-rank below (PQ modes)
             clk.mark(kPhSelect);
 
             // ---- filter seen neighbours, §4.3: test all, then insert all
@@ -444,12 +485,35 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             __syncwarp();
             clk.mark(kPhFilter);
 
-            // ---- PQ distances of the new neighbours, §4.4
-            for (uint32_t j = lane; j < nn; j += kWarp) {
-                const uint32_t id = Nid[j];
-                const float dj = adc_distance(T, a.codes + static_cast<uint64_t>(id) * a.Mpad, a.M,
-                                              a.Mpad);
-                Nk[j] = make_key(__float_as_uint(dj), id);
+            // ---- distances of the new neighbours: PQ (§4.4), one lane per
+            // neighbour; or exact (§5.2), the warp per neighbour, four
+            // neighbours' vectors requested at a time
+            if (kPQ) {
+                for (uint32_t j = lane; j < nn; j += kWarp) {
+                    const uint32_t id = Nid[j];
+                    const float dj = adc_distance<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
+                                                        a.M, a.Mpad);
+                    Nk[j] = make_key(__float_as_uint(dj), id);
+                }
+            } else {
+                for (uint32_t j0 = 0; j0 < nn; j0 += 4) {
+                    VecShare<DT, DCH> xs[4];
+                    uint32_t ids[4];
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        ids[t] = j0 + t < nn ? Nid[j0 + t] : 0u;
+                        if (j0 + t < nn)
+                            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(ids[t]) * d,
+                                                d, a.vecb_ok != 0, lane, xs[t]);
+                    }
+#pragma unroll
+                    for (int t = 0; t < 4; ++t) {
+                        if (j0 + t < nn) {
+                            const uint32_t e = exact_distance_bits<DT, DCH>(qs, xs[t]);
+                            if (lane == 0) Nk[j0 + t] = make_key(e, ids[t]);
+                        }
+                    }
+                }
             }
             ndist += nn;
             __syncwarp();
@@ -478,13 +542,13 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 // settled by the merge below
                 if (best != ~0ull) {
                     cur = key_id(best);
-                    load_node<DT, RPL, DCH>(a, cur, lane, nd);
+                    load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
                 }
             }
             clk.mark(kPhNext);
             // ---- re-rank candidate: exact distance of u* (§4.8), off the
             // critical path: the next node's lists are already requested
-            {
+            if (kPQ) {
                 const uint64_t e = make_key(exact_distance_bits<DT, DCH>(qs, xu), u);
                 if (regk) {
                     const uint32_t pos = __popc(__ballot_sync(0xFFFFFFFFu, ck < e));
@@ -607,8 +671,22 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             clk.mark(kPhMerge);
         }
 
-        // ---- output: re-ranked top-k (§4.8), padded
-        if (regk) {
+        // ---- output: re-ranked top-k (§4.8), or in the exact mode the first
+        // k worklist entries (Alg. 1's result); padded
+        if (!kPQ) {
+            for (uint32_t i = lane; i < k; i += kWarp) {
+                const uint64_t o = static_cast<uint64_t>(q) * k + i;
+                if (i < nl) {
+                    const uint64_t key = Lk[i];
+                    const uint32_t bits = static_cast<uint32_t>(key >> 32);
+                    a.out_ids[o] = key_id(key);
+                    a.out_dist[o] = DT == 2 ? __uint_as_float(bits) : static_cast<float>(bits);
+                } else {
+                    a.out_ids[o] = kNone;
+                    a.out_dist[o] = __uint_as_float(0x7F800000u);
+                }
+            }
+        } else if (regk) {
             if (static_cast<uint32_t>(lane) < k) {
                 const uint64_t o = static_cast<uint64_t>(q) * k + lane;
                 if (static_cast<uint32_t>(lane) < nc) {
@@ -648,5 +726,34 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         __syncwarp();
     }
 }
+
+// Launch for one mode: dispatch on element type, neighbours per lane
+// (R <= 64 or <= 128) and 128-dimension chunks per lane (d <= 128 or <= 512).
+template <int DT, int RPL, int DCH, int MODE>
+cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
+    if (e != cudaSuccess) return e;
+    search_kernel<DT, RPL, DCH, MODE><<<a.nq, 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st)
+{
+    const bool narrow = a.d <= 128, wide_r = a.R > 64;
+#define BANG_DISPATCH(DT)                                                                    \
+    return wide_r ? (narrow ? launch_one<DT, 4, 1, MODE>(a, smem, st) : launch_one<DT, 4, 4, MODE>(a, smem, st)) \
+                  : (narrow ? launch_one<DT, 2, 1, MODE>(a, smem, st) : launch_one<DT, 2, 4, MODE>(a, smem, st))
+    if (dtype == 0) { BANG_DISPATCH(0); }
+    if (dtype == 1) { BANG_DISPATCH(1); }
+    BANG_DISPATCH(2);
+#undef BANG_DISPATCH
+}
+
+// One translation unit per mode instantiates these.
+cudaError_t launch_search_f32(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
+cudaError_t launch_search_bf16(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
+cudaError_t launch_search_exact(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 
 }  // namespace bang

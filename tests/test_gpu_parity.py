@@ -17,9 +17,12 @@ import paper_2401_11324_gb300 as bang  # noqa: E402
 RTOL = 1e-5
 
 
-def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None):
+def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
+               placement=0):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
+    if placement:
+        ix.set_placement(placement)
     nq = Q.shape[0]
     dev = "cpu" if host else "cuda"
     if host:
@@ -33,7 +36,8 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     ndist = torch.empty(nq, dtype=torch.int32, device=dev)
     trace = torch.zeros((nq, max(trace_cap, 1)), dtype=torch.int32, device=dev)
     p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
-                         out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap)
+                         out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
+                         mode=mode)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
@@ -43,10 +47,10 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     return out
 
 
-def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None):
+def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None, exact=False):
     M = M or w["M"]
     ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
-    return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap)
+    return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap, exact=exact)
 
 
 def assert_parity(g, o, trace_cap=0, exact_dist=True):
@@ -196,3 +200,48 @@ def test_empty_batch(u8small):
     dist = torch.empty((0, 10), dtype=torch.float32, device="cuda")
     ix.search(q, 10, 32, ids, dist)
     ix.close()
+
+
+# ---------------------------------------------------------------- other forms
+
+def test_in_memory_placement_matches_host_placement(u8small):
+    # §5.1: graph (and vectors) read from HBM instead of host memory
+    Q = u8small["queries"][:100]
+    ref = gpu_search(u8small, Q, 10, 64, trace_cap=300)
+    for flags in (bang.BANG_GRAPH_IN_HBM, bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
+        g = gpu_search(u8small, Q, 10, 64, trace_cap=300, placement=flags)
+        for f in ("ids", "dist", "iters", "ndist", "trace"):
+            assert (g[f] == ref[f]).all()
+
+
+@pytest.mark.parametrize("placement", [0, 3])
+def test_exact_mode_bit_exact(u8small, cfg1, placement):
+    # §5.2: exact distances in the loop, no table, no re-rank
+    for w, Q, L in ((u8small, u8small["queries"][:120], 48), (cfg1, cfg1["queries"], 64)):
+        g = gpu_search(w, Q, 10, L, trace_cap=400, mode=bang.BANG_MODE_EXACT, placement=placement)
+        o = oracle_search(w, Q, 10, L, trace_cap=400, exact=True)
+        assert_parity(g, o, trace_cap=400)
+
+
+def test_exact_mode_int8():
+    w = cases.clustered(n=8_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40,
+                        centre="uniform100")
+    Q = w["queries"]
+    g = gpu_search(w, Q, 10, 40, trace_cap=200, mode=bang.BANG_MODE_EXACT)
+    assert_parity(g, oracle_search(w, Q, 10, 40, trace_cap=200, exact=True), trace_cap=200)
+
+
+def test_bf16_table_recall_within_tolerance(u8small):
+    # reduced-precision form: judged by recall@10 against the FP32 form
+    Q = u8small["queries"]
+    gt = u8small["gt_ids"]
+    for L in (32, 96):
+        o = oracle_search(u8small, Q, 10, L)
+        g = gpu_search(u8small, Q, 10, L, mode=bang.BANG_MODE_PQ_BF16)
+        r_o = oracle.recall_at_k(o["ids"], gt, 10)
+        r_g = oracle.recall_at_k(g["ids"], gt, 10)
+        assert abs(r_g - r_o) <= 0.005 + 1.0 / (10 * len(Q)), (L, r_g, r_o)
+        # the re-rank makes the returned distances exact for the ids returned
+        ex = ((u8small["base"][g["ids"]].astype(np.int64) -
+               Q[:, None, :].astype(np.int64)) ** 2).sum(-1)
+        assert (g["dist"] == ex.astype(np.float32)).all()

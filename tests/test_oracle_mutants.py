@@ -30,6 +30,8 @@ MUTANTS = [
     ("encode_ties_high", "if (acc < best) { best = acc; bc = c; }", "if (acc <= best) { best = acc; bc = c; }", 1),
     ("prune_alpha_unsquared", "double a2 = (double)alpha * (double)alpha;", "double a2 = (double)alpha;", 0),
     ("bruteforce_l1", "ia += t2 * t2;", "ia += t2 < 0 ? -t2 : t2;", 0),
+    ("exact_mode_keeps_rerank", "if (mode != 0) {                    /* Alg. 1",
+     "if (mode == 7) {                    /* Alg. 1", 0),
 ]
 
 

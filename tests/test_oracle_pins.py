@@ -341,6 +341,27 @@ def test_complete_graph_equals_bruteforce():
                 assert r["iters"][qi] == (L if med in topL.tolist() else L + 1)
 
 
+def test_exact_mode_complete_graph_equals_bruteforce():
+    # Exact-distance variant (§5.2): exact distances in the loop, no re-rank;
+    # on a complete graph the worklist after the first expansion holds the L
+    # nearest points, so its first k are the exact k-NN.
+    rng = np.random.default_rng(16)
+    n = 40
+    X = rng.normal(size=(n, 12)).astype(np.float32)
+    cb = rng.normal(size=256 * 12).astype(np.float32)          # unused by the exact mode
+    codes = rng.integers(0, 256, size=(n, 3)).astype(np.uint8)
+    ix = oracle.Index(X, cb, codes, complete_graph(n), 7, 3)
+    Q = rng.normal(size=(5, 12)).astype(np.float32)
+    r = ix.search(Q, k=4, L=6, log2z=18, exact=True)
+    ref = ((X[None].astype(np.float64) - Q[:, None].astype(np.float64)) ** 2).sum(-1)
+    for qi in range(5):
+        assert r["ids"][qi].tolist() == np.argsort(ref[qi])[:4].tolist()
+        for j, i in enumerate(r["ids"][qi]):
+            assert abs(r["dist"][qi][j] - ref[qi][i]) <= 1e-5 * ref[qi][i]
+        top6 = np.argsort(ref[qi])[:6].tolist()
+        assert r["iters"][qi] == (6 if 7 in top6 else 7)
+
+
 def test_full_worklist_visits_every_reachable_node():
     # With L >= n on a connected graph and a filter without false positives
     # in practice (z = 2^22 bits for <= 64 ids), every node is expanded and
