@@ -78,6 +78,9 @@ typedef struct bang_search_params {
      * paper's Exact-distance variant, §5.2; results are the first k entries
      * of the final worklist). */
     uint32_t mode;
+    /* bang_search_batched only: the persistent grid is grid_mult times the
+     * CTAs that fit on the device at once (0 or 1: exactly that many). */
+    uint32_t grid_mult;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2 } bang_mode;
@@ -141,6 +144,25 @@ int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype);
 int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
                 const bang_search_params *params, uint32_t *out_ids, float *out_dist,
                 void *stream);
+
+/* Batched form: queries with their own k and L in one persistent launch.
+ *   k_per_q, L_per_q  host or device, nq entries each; query i needs
+ *                     1 <= k_i <= k_max and k_i <= L_i <= L_max (otherwise its
+ *                     row is padded and out_status[i] = -1).
+ *   k_max, L_max      bounds (as bang_search's k, L); they size the shared
+ *                     memory and the output rows: out_ids and out_dist are
+ *                     nq*k_max, row i holding k_i results then padding.
+ * A grid of resident CTAs pulls queries from a device work counter; when
+ * L_per_q is host memory the queries are handed out by decreasing L.  With
+ * every pointer argument in device memory the call only enqueues work
+ * (cudaMemsetAsync + one kernel) and can be captured in a CUDA graph; make one
+ * call with the same stream outside the capture first, since the first call
+ * on a stream allocates its 256-byte work counter.  Calls in flight on
+ * different streams use separate counters. */
+int bang_search_batched(bang_index *ix, const void *queries, uint32_t nq, const uint32_t *k_per_q,
+                        const uint32_t *L_per_q, uint32_t k_max, uint32_t L_max,
+                        const bang_search_params *params, uint32_t *out_ids, float *out_dist,
+                        void *stream);
 
 /* Choose where the search reads the graph and the full vectors: 0 keeps
  * both in host memory, read in place (Alg. 2); BANG_GRAPH_IN_HBM and/or

@@ -34,7 +34,7 @@ class bang_search_params(ctypes.Structure):
                 ("out_iters", ctypes.c_void_p), ("out_status", ctypes.c_void_p),
                 ("out_ndist", ctypes.c_void_p), ("trace", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_uint32), ("out_phase_cycles", ctypes.c_void_p),
-                ("mode", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32)]
 
 
 class bang_link_probe(ctypes.Structure):
@@ -70,11 +70,13 @@ def _load():
                               vp]
     L.bang_destroy.argtypes = [vp]
     L.bang_set_placement.argtypes = [vp, u32]
+    L.bang_search_batched.argtypes = [vp, vp, u32, vp, vp, u32, u32,
+                                      ctypes.POINTER(bang_search_params), vp, vp, vp]
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
     L.bang_probe_host_link.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
-              "bang_search", "bang_destroy", "bang_set_placement"):
+              "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -135,9 +137,10 @@ BANG_GRAPH_IN_HBM, BANG_VECTORS_IN_HBM = 1, 2
 
 
 def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
-                trace=None, trace_cap=0, out_phase_cycles=None, mode=0):
+                trace=None, trace_cap=0, out_phase_cycles=None, mode=0, grid_mult=0):
     return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
-                              _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles), mode)
+                              _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles), mode,
+                              grid_mult)
 
 
 def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
@@ -145,6 +148,14 @@ def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
     s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
     return _check(lib().bang_search(ix, _ptr(queries), nq, k, L, p, _ptr(out_ids),
                                     _ptr(out_dist), s))
+
+
+def bang_search_batched(ix, queries, nq, k_per_q, L_per_q, k_max, L_max, params, out_ids,
+                        out_dist, stream=None):
+    p = ctypes.byref(params) if params is not None else None
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    return _check(lib().bang_search_batched(ix, _ptr(queries), nq, _ptr(k_per_q), _ptr(L_per_q),
+                                            k_max, L_max, p, _ptr(out_ids), _ptr(out_dist), s))
 
 
 def bang_set_placement(ix, flags):
@@ -176,6 +187,12 @@ class Index:
         bang_load_pq(self.h, self.d, M, self._codebook, self._codes, self.n)
         bang_register_graph(self.h, self.adj, self.R, self.medoid)
         bang_register_vectors(self.h, self.base, self.dtype)
+
+    def search_batched(self, queries, k_per_q, L_per_q, k_max, L_max, out_ids, out_dist,
+                       params=None, stream=None):
+        nq = queries.shape[0]
+        return bang_search_batched(self.h, queries, nq, k_per_q, L_per_q, k_max, L_max, params,
+                                   out_ids, out_dist, stream)
 
     def set_placement(self, flags):
         return bang_set_placement(self.h, flags)

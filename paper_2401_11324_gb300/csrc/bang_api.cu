@@ -7,6 +7,8 @@
 
 #include <algorithm>
 #include <cstdarg>
+#include <map>
+#include <numeric>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -149,6 +151,8 @@ struct bang_index {
     // In-memory placement (§5.1): device copies of the graph and/or vectors.
     DevBuf adj_hbm, base_hbm;
     uint32_t placement = 0;
+    // Batched form: per-stream work counter, query order and staged k / L.
+    std::map<cudaStream_t, DevBuf> work;
 };
 
 namespace {
@@ -307,9 +311,15 @@ int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype)
     return BANG_OK;
 }
 
-int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
-                const bang_search_params *params, uint32_t *out_ids, float *out_dist,
-                void *stream)
+}  // extern "C"
+
+namespace {
+
+// Shared by bang_search (k_arr, L_arr null: every query uses k, L) and
+// bang_search_batched (k, L are the bounds; persistent launch).
+int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
+                const uint32_t *k_arr, const uint32_t *L_arr, bool persistent,
+                const bang_search_params *params, uint32_t *out_ids, float *out_dist, void *stream)
 {
     if (!ix) return fail(BANG_EINVAL, "bang_search: index is NULL");
     if (!ix->have_pq || !ix->have_graph || !ix->have_vectors)
@@ -326,7 +336,7 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     uint32_t log2z = p.bloom_log2 ? p.bloom_log2 : 16u;
     if (log2z < 10 || log2z > 20)
         return fail(BANG_EINVAL, "bang_search: bloom_log2=%u outside 10..20", log2z);
-    uint32_t cap = p.iter_cap ? p.iter_cap : 8u * L + 64u;
+    if (persistent && (!k_arr || !L_arr)) return fail(BANG_EINVAL, "bang_search_batched: NULL k or L array");
     if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search: trace_cap is 0");
 
     if (p.mode > 2) return fail(BANG_EINVAL, "bang_search: unknown mode %u", p.mode);
@@ -342,7 +352,7 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     // Host buffers are staged through one device allocation.
     const size_t qbytes = (size_t)nq * ix->d * elem_size(ix->dtype);
     struct Slot { const void *user; size_t bytes; bool in; size_t off; bool dev; };
-    Slot slots[8] = {
+    Slot slots[10] = {
         {queries, qbytes, true, 0, false},
         {out_ids, (size_t)nq * k * 4, false, 0, false},
         {out_dist, (size_t)nq * k * 4, false, 0, false},
@@ -350,10 +360,12 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
         {p.out_status, (size_t)nq * 4, false, 0, false},
         {p.out_ndist, (size_t)nq * 4, false, 0, false},
         {p.trace, (size_t)nq * p.trace_cap * 4, false, 0, false},
-        {p.out_phase_cycles, (size_t)nq * bang::kPhases * 8, false, 0, false}};
+        {p.out_phase_cycles, (size_t)nq * bang::kPhases * 8, false, 0, false},
+        {k_arr, (size_t)nq * 4, true, 0, false},
+        {L_arr, (size_t)nq * 4, true, 0, false}};
     size_t need = 0;
     bool any_host = false;
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 10; ++i) {
         Slot &s = slots[i];
         if (!s.user) continue;
         s.dev = is_device_accessible(s.user);
@@ -369,7 +381,32 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
         if (!s.user) return nullptr;
         return s.dev ? const_cast<void *>(s.user) : static_cast<char *>(ix->staging.p) + s.off;
     };
-    if (!slots[0].dev) CUDA_TRY(cudaMemcpyAsync(dptr(0), queries, qbytes, cudaMemcpyHostToDevice, st));
+    for (int i = 0; i < 10; ++i)
+        if (slots[i].user && slots[i].in && !slots[i].dev)
+            CUDA_TRY(cudaMemcpyAsync(dptr(i), slots[i].user, slots[i].bytes, cudaMemcpyHostToDevice, st));
+
+    // Persistent launch: a zeroed work counter, and, when the worklist sizes
+    // are on the host, the queries ordered by decreasing L so the longest
+    // searches start first.
+    unsigned int *queue = nullptr;
+    const uint32_t *order = nullptr;
+    if (persistent) {
+        const bool host_order = !slots[9].dev;
+        DevBuf &wb = ix->work[st];
+        CUDA_TRY(wb.ensure(256 + (host_order ? (size_t)nq * 4 : 0)));
+        queue = static_cast<unsigned int *>(wb.p);
+        CUDA_TRY(cudaMemsetAsync(queue, 0, sizeof(unsigned int), st));
+        if (host_order) {
+            std::vector<uint32_t> ord(nq);
+            std::iota(ord.begin(), ord.end(), 0u);
+            std::stable_sort(ord.begin(), ord.end(),
+                             [&](uint32_t x, uint32_t y) { return L_arr[x] > L_arr[y]; });
+            uint32_t *dord = reinterpret_cast<uint32_t *>(static_cast<char *>(wb.p) + 256);
+            CUDA_TRY(cudaMemcpyAsync(dord, ord.data(), (size_t)nq * 4, cudaMemcpyHostToDevice, st));
+            CUDA_TRY(cudaStreamSynchronize(st));      // `ord` is freed on return
+            order = dord;
+        }
+    }
 
     bang::SearchArgs a;
     a.queries = dptr(0);
@@ -380,7 +417,12 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
     a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
     a.medoid = ix->medoid;
-    a.nq = nq; a.k = k; a.L = L; a.log2z = log2z; a.iter_cap = cap;
+    a.nq = nq; a.k = k; a.L = L; a.log2z = log2z; a.iter_cap = p.iter_cap;
+    a.k_per_q = static_cast<const uint32_t *>(dptr(8));
+    a.L_per_q = static_cast<const uint32_t *>(dptr(9));
+    a.order = order;
+    a.queue = queue;
+    a.grid_mult = p.grid_mult;
     a.out_ids = static_cast<uint32_t *>(dptr(1));
     a.out_dist = static_cast<float *>(dptr(2));
     a.out_iters = static_cast<uint32_t *>(dptr(3));
@@ -404,12 +446,33 @@ int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     if (le != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(le));
     for (int i = 1; i < 8; ++i) {
         Slot &s = slots[i];
-        if (s.user && !s.dev)
+        if (s.user && !s.dev && !s.in)
             CUDA_TRY(cudaMemcpyAsync(const_cast<void *>(s.user), dptr(i), s.bytes,
                                      cudaMemcpyDeviceToHost, st));
     }
     if (any_host) CUDA_TRY(cudaStreamSynchronize(st));
     return BANG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int bang_search(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
+                const bang_search_params *params, uint32_t *out_ids, float *out_dist,
+                void *stream)
+{
+    return search_impl(ix, queries, nq, k, L, nullptr, nullptr, false, params, out_ids, out_dist,
+                       stream);
+}
+
+int bang_search_batched(bang_index *ix, const void *queries, uint32_t nq, const uint32_t *k_per_q,
+                        const uint32_t *L_per_q, uint32_t k_max, uint32_t L_max,
+                        const bang_search_params *params, uint32_t *out_ids, float *out_dist,
+                        void *stream)
+{
+    return search_impl(ix, queries, nq, k_max, L_max, k_per_q, L_per_q, true, params, out_ids,
+                       out_dist, stream);
 }
 
 int bang_set_placement(bang_index *ix, uint32_t flags)
@@ -455,6 +518,7 @@ int bang_destroy(bang_index *ix)
         ix->staging.release();
         ix->adj_hbm.release();
         ix->base_hbm.release();
+        for (auto &kv : ix->work) kv.second.release();
     }
     delete ix;
     return BANG_OK;

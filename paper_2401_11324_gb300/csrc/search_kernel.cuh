@@ -67,6 +67,14 @@ struct SearchArgs {
     uint32_t *out_ndist;      // device or null
     uint32_t *trace;          // device or null
     uint32_t trace_cap;
+    // Batched form: per-query k and L (device or null: every query uses k, L,
+    // which are otherwise the bounds and the output row stride), an optional
+    // processing order and a work counter for the persistent launch.
+    const uint32_t *k_per_q;
+    const uint32_t *L_per_q;
+    const uint32_t *order;
+    unsigned int *queue;      // device counter, zero at launch; null: grid covers the queries
+    uint32_t grid_mult;       // persistent grid = grid_mult x resident CTAs (>= 1)
     unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
 };
 
@@ -383,14 +391,43 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     float *qv = reinterpret_cast<float *>(smem + lay.off_q);
     uint32_t *offs = reinterpret_cast<uint32_t *>(smem + lay.off_offs);
 
-    const uint32_t d = a.d, L = a.L, k = a.k;
+    const uint32_t d = a.d, kstride = a.k;
     const uint32_t zmask = (1u << a.log2z) - 1u;
     const uint32_t nwords = (1u << a.log2z) >= 32u ? (1u << a.log2z) / 32u : 1u;
-    const bool regk = k <= static_cast<uint32_t>(kRegK);
 
     for (uint32_t i = lane; i <= a.M; i += kWarp) offs[i] = a.off[i];
 
-    for (uint32_t q = blockIdx.x; q < a.nq; q += gridDim.x) {
+    uint32_t next_static = blockIdx.x;
+    for (;;) {
+        // ---- next query: from the work counter (persistent launch) or by grid stride
+        uint32_t qi;
+        if (a.queue) {
+            uint32_t t = 0;
+            if (lane == 0) t = atomicAdd(a.queue, 1u);
+            qi = __shfl_sync(0xFFFFFFFFu, t, 0);
+        } else {
+            qi = next_static;
+            next_static += gridDim.x;
+        }
+        if (qi >= a.nq) break;
+        const uint32_t q = a.order ? a.order[qi] : qi;
+        const uint32_t k = a.k_per_q ? a.k_per_q[q] : a.k;
+        const uint32_t L = a.L_per_q ? a.L_per_q[q] : a.L;
+        const bool regk = k <= static_cast<uint32_t>(kRegK);
+        if (k == 0 || k > a.k || L < k || L > a.L) {     // per-query arguments out of range
+            for (uint32_t i = lane; i < kstride; i += kWarp) {
+                a.out_ids[static_cast<uint64_t>(q) * kstride + i] = kNone;
+                a.out_dist[static_cast<uint64_t>(q) * kstride + i] = __uint_as_float(0x7F800000u);
+            }
+            if (lane == 0) {
+                if (a.out_iters) a.out_iters[q] = 0;
+                if (a.out_status) a.out_status[q] = -1;
+                if (a.out_ndist) a.out_ndist[q] = 0;
+            }
+            __syncwarp();
+            continue;
+        }
+        const uint32_t iter_cap = a.iter_cap ? a.iter_cap : 8u * L + 64u;
         PhaseClock clk(a.phase_cycles != nullptr);
         const unsigned long long t_start = clk.t;
         // ---- query: FP32 copy in shared memory, this lane's share in registers
@@ -432,7 +469,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         __syncwarp();
 
         while (have_next) {
-            if (iters >= a.iter_cap) {
+            if (iters >= iter_cap) {
                 status = 1;
                 break;
             }
@@ -674,9 +711,9 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         // ---- output: re-ranked top-k (§4.8), or in the exact mode the first
         // k worklist entries (Alg. 1's result); padded
         if (!kPQ) {
-            for (uint32_t i = lane; i < k; i += kWarp) {
-                const uint64_t o = static_cast<uint64_t>(q) * k + i;
-                if (i < nl) {
+            for (uint32_t i = lane; i < kstride; i += kWarp) {
+                const uint64_t o = static_cast<uint64_t>(q) * kstride + i;
+                if (i < nl && i < k) {
                     const uint64_t key = Lk[i];
                     const uint32_t bits = static_cast<uint32_t>(key >> 32);
                     a.out_ids[o] = key_id(key);
@@ -687,9 +724,9 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 }
             }
         } else if (regk) {
-            if (static_cast<uint32_t>(lane) < k) {
-                const uint64_t o = static_cast<uint64_t>(q) * k + lane;
-                if (static_cast<uint32_t>(lane) < nc) {
+            for (uint32_t i = lane; i < kstride; i += kWarp) {
+                const uint64_t o = static_cast<uint64_t>(q) * kstride + i;
+                if (i < nc) {                  // nc <= k <= 32: rank i is lane i's register
                     const uint32_t bits = static_cast<uint32_t>(ck >> 32);
                     a.out_ids[o] = key_id(ck);
                     a.out_dist[o] = DT == 2 ? __uint_as_float(bits) : static_cast<float>(bits);
@@ -699,8 +736,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 }
             }
         } else {
-            for (uint32_t i = lane; i < k; i += kWarp) {
-                const uint64_t o = static_cast<uint64_t>(q) * k + i;
+            for (uint32_t i = lane; i < kstride; i += kWarp) {
+                const uint64_t o = static_cast<uint64_t>(q) * kstride + i;
                 if (i < nc) {
                     const uint64_t key = Ck[i];
                     const uint32_t bits = static_cast<uint32_t>(key >> 32);
@@ -735,7 +772,19 @@ cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
-    search_kernel<DT, RPL, DCH, MODE><<<a.nq, 32, smem, st>>>(a);
+    uint32_t grid = a.nq;
+    if (a.queue) {                     // persistent: a multiple of the resident CTAs
+        int dev = 0, sms = 0, per_sm = 0;
+        if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+        if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE>,
+                                                               32, smem)) != cudaSuccess)
+            return e;
+        const uint64_t want = static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1) *
+                              (a.grid_mult ? a.grid_mult : 1u);
+        grid = static_cast<uint32_t>(want < a.nq ? want : a.nq);
+    }
+    search_kernel<DT, RPL, DCH, MODE><<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

@@ -245,3 +245,94 @@ def test_bf16_table_recall_within_tolerance(u8small):
         ex = ((u8small["base"][g["ids"]].astype(np.int64) -
                Q[:, None, :].astype(np.int64)) ** 2).sum(-1)
         assert (g["dist"] == ex.astype(np.float32)).all()
+
+
+# ---------------------------------------------------------------- batched form
+
+def _mixed_kl(nq, seed):
+    rng = np.random.default_rng(seed)
+    k = rng.choice([1, 10, 100], size=nq).astype(np.uint32)
+    L = np.maximum(rng.choice([32, 64, 128, 256], size=nq), k).astype(np.uint32)
+    return k, L
+
+
+def _oracle_mixed(w, Q, k, L, mode_exact=False):
+    kmax = int(k.max())
+    ids = np.full((len(Q), kmax), bang.BANG_NONE, np.uint32)
+    dist = np.full((len(Q), kmax), np.inf, np.float32)
+    iters = np.zeros(len(Q), np.uint32)
+    for kk in np.unique(k):
+        for LL in np.unique(L[k == kk]):
+            sel = np.where((k == kk) & (L == LL))[0]
+            o = oracle_search(w, Q[sel], int(kk), int(LL), exact=mode_exact)
+            ids[sel, :kk] = o["ids"]
+            dist[sel, :kk] = o["dist"]
+            iters[sel] = o["iters"]
+    return ids, dist, iters
+
+
+def test_batched_uneven_k_and_L_host_arrays(u8small):
+    Q = u8small["queries"][:160]
+    k, L = _mixed_kl(len(Q), 5)
+    ids_o, dist_o, iters_o = _oracle_mixed(u8small, Q, k, L)
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    kmax, Lmax = int(k.max()), int(L.max())
+    for mult in (0, 3):
+        ids = np.zeros((len(Q), kmax), np.uint32)
+        dist = np.zeros((len(Q), kmax), np.float32)
+        iters = np.zeros(len(Q), np.uint32)
+        ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist,
+                          bang.make_params(out_iters=iters, grid_mult=mult))
+        assert (ids == ids_o).all() and (iters == iters_o).all()
+        fin = np.isfinite(dist_o)
+        assert (np.isfinite(dist) == fin).all() and (dist[fin] == dist_o[fin]).all()
+    ix.close()
+
+
+def test_batched_cuda_graph_replay(u8small):
+    Q = u8small["queries"][:128]
+    k, L = _mixed_kl(len(Q), 6)
+    ids_o, _, _ = _oracle_mixed(u8small, Q, k, L)
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    kmax, Lmax = int(k.max()), int(L.max())
+    q = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    kd = torch.from_numpy(k.view(np.int32)).cuda()
+    Ld = torch.from_numpy(L.view(np.int32)).cuda()
+    ids = torch.zeros((len(Q), kmax), dtype=torch.int32, device="cuda")
+    dist = torch.zeros((len(Q), kmax), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    p = bang.make_params()
+    with torch.cuda.stream(s):
+        ix.search_batched(q, kd, Ld, kmax, Lmax, ids, dist, p, stream=s.cuda_stream)  # allocates
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ix.search_batched(q, kd, Ld, kmax, Lmax, ids, dist, p, stream=s.cuda_stream)
+    for _ in range(2):
+        ids.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert (ids.cpu().numpy().view(np.uint32) == ids_o).all()
+    ix.close()
+
+
+def test_batched_invalid_rows_are_flagged(u8small):
+    Q = u8small["queries"][:4]
+    k = np.array([10, 0, 10, 5], np.uint32)
+    L = np.array([64, 64, 5, 64], np.uint32)           # row 1: k=0, row 2: L<k
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    ids = np.zeros((4, 10), np.uint32)
+    dist = np.zeros((4, 10), np.float32)
+    status = np.zeros(4, np.int32)
+    ix.search_batched(np.ascontiguousarray(Q), k, L, 10, 64, ids, dist,
+                      bang.make_params(out_status=status))
+    assert status.tolist() == [0, -1, -1, 0]
+    assert (ids[1] == bang.BANG_NONE).all() and (ids[2] == bang.BANG_NONE).all()
+    o = oracle_search(u8small, Q[[0]], 10, 64)
+    assert (ids[0] == o["ids"][0]).all()
+    o5 = oracle_search(u8small, Q[[3]], 5, 64)
+    assert (ids[3, :5] == o5["ids"][0]).all() and (ids[3, 5:] == bang.BANG_NONE).all()
+    ix.close()
