@@ -164,6 +164,30 @@ int bang_search_batched(bang_index *ix, const void *queries, uint32_t nq, const 
                         const bang_search_params *params, uint32_t *out_ids, float *out_dist,
                         void *stream);
 
+/* Allocation-free batched search (the paper has no counterpart).  Same
+ * arguments, results and per-query rules as bang_search_batched, for callers
+ * that cannot let a library allocate device memory: a serving loop that must
+ * not stall on the device-wide synchronisation cudaMalloc/cudaFree can cause,
+ * work recorded into a CUDA graph under global stream capture (allocations
+ * are refused there), or a framework that owns the whole memory budget.
+ *   - Allocates nothing (no cudaMalloc/cudaFree, no pinned or staging
+ *     buffers): every pointer argument must already be device memory,
+ *     otherwise BANG_EINVAL.
+ *   - Its scratch (the persistent launch's work counter and the
+ *     longest-L-first query order, computed on the device) is a file-scope
+ *     device array of about 270 KB that every GPU loading the library keeps
+ *     until exit; nq above 65536 (its capacity) returns BANG_EINVAL.
+ *   - The first call on a device looks up that array's device address; make
+ *     it before any stream capture.
+ *   - All calls share the array: calls that overlap on the GPU (on different
+ *     streams, or different indexes at once) race and must not be issued.
+ *     Each call clears the counter it needs and rewrites the order.
+ * Enqueues two kernels on `stream` and returns. */
+int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq,
+                                const uint32_t *k_per_q, const uint32_t *L_per_q, uint32_t k_max,
+                                uint32_t L_max, const bang_search_params *params,
+                                uint32_t *out_ids, float *out_dist, void *stream);
+
 /* Choose where the search reads the graph and the full vectors: 0 keeps
  * both in host memory, read in place (Alg. 2); BANG_GRAPH_IN_HBM and/or
  * BANG_VECTORS_IN_HBM copy the registered arrays into device memory once

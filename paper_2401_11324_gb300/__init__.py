@@ -72,11 +72,13 @@ def _load():
     L.bang_set_placement.argtypes = [vp, u32]
     L.bang_search_batched.argtypes = [vp, vp, u32, vp, vp, u32, u32,
                                       ctypes.POINTER(bang_search_params), vp, vp, vp]
+    L.bang_search_batched_noalloc.argtypes = L.bang_search_batched.argtypes
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
     L.bang_probe_host_link.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
-              "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched"):
+              "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
+              "bang_search_batched_noalloc"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -156,6 +158,17 @@ def bang_search_batched(ix, queries, nq, k_per_q, L_per_q, k_max, L_max, params,
     s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
     return _check(lib().bang_search_batched(ix, _ptr(queries), nq, _ptr(k_per_q), _ptr(L_per_q),
                                             k_max, L_max, p, _ptr(out_ids), _ptr(out_dist), s))
+
+
+def bang_search_batched_noalloc(ix, queries, nq, k_per_q, L_per_q, k_max, L_max, params, out_ids,
+                                out_dist, stream=None):
+    """bang_search_batched without any allocation (device buffers only); see
+    include/bang.h for who needs it and its limits."""
+    p = ctypes.byref(params) if params is not None else None
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    return _check(lib().bang_search_batched_noalloc(ix, _ptr(queries), nq, _ptr(k_per_q),
+                                                    _ptr(L_per_q), k_max, L_max, p, _ptr(out_ids),
+                                                    _ptr(out_dist), s))
 
 
 def bang_set_placement(ix, flags):

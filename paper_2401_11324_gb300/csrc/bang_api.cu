@@ -525,3 +525,177 @@ int bang_destroy(bang_index *ix)
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched search.
+//
+// Some callers cannot let a library call cudaMalloc: a serving loop that must
+// not stall on the implicit device-wide synchronisation cudaMalloc/cudaFree
+// can cause, code recorded into a CUDA graph under global stream capture
+// (where allocation calls are refused), or a host framework that owns the
+// whole device-memory budget through its own pool.  For them the batched
+// search has a variant whose scratch -- the work counter of the persistent
+// launch, the per-L bucket cursors and the longest-L-first query order --
+// lives in the file-scope array below instead of memory allocated per index
+// and stream.  Every GPU that loads this library keeps the array
+// (kNoAllocScratchWords * 4 bytes, about 270 KB) until the process exits.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr uint32_t kNoAllocMaxQueries = 65536;           // queries per call, at most
+constexpr uint32_t kNoAllocBuckets = bang::kMaxL + 1;     // L = 1..kMaxL; 0 = out of range
+constexpr uint32_t kNoAllocCursor = 64;                   // word offsets in the array
+constexpr uint32_t kNoAllocOrder = kNoAllocCursor + 2048;
+constexpr uint32_t kNoAllocScratchWords = kNoAllocOrder + kNoAllocMaxQueries;
+
+static __device__ __align__(256) unsigned int g_noalloc_scratch[kNoAllocScratchWords];
+
+// One CTA of 1024 threads: zero the work counter and write the queries'
+// order by decreasing L (counting sort; order within one L is arbitrary, and
+// out-of-range L values go last, where the search flags them).
+__global__ void __launch_bounds__(1024) noalloc_order_by_L(const uint32_t *L_per_q, uint32_t nq)
+{
+    __shared__ unsigned int hist[kNoAllocBuckets];
+    __shared__ unsigned int scan[1024];
+    unsigned int *cursor = g_noalloc_scratch + kNoAllocCursor;
+    unsigned int *order = g_noalloc_scratch + kNoAllocOrder;
+    const uint32_t t = threadIdx.x;
+    for (uint32_t b = t; b < kNoAllocBuckets; b += blockDim.x) hist[b] = 0;
+    __syncthreads();
+    for (uint32_t q = t; q < nq; q += blockDim.x) {
+        const uint32_t L = L_per_q[q];
+        atomicAdd(&hist[(L >= 1 && L <= (uint32_t)bang::kMaxL) ? L : 0u], 1u);
+    }
+    __syncthreads();
+    // rank buckets by decreasing L: thread t owns bucket kMaxL - t (t < kMaxL)
+    const uint32_t mine = hist[bang::kMaxL - t];
+    scan[t] = mine;
+    __syncthreads();
+    for (uint32_t off = 1; off < 1024; off <<= 1) {
+        const uint32_t v = t >= off ? scan[t - off] : 0u;
+        __syncthreads();
+        scan[t] += v;
+        __syncthreads();
+    }
+    cursor[bang::kMaxL - t] = scan[t] - mine;                 // exclusive start
+    if (t == 0) {
+        cursor[0] = scan[1023];                               // out-of-range L last
+        g_noalloc_scratch[0] = 0u;                            // work counter
+    }
+    __syncthreads();
+    for (uint32_t q = t; q < nq; q += blockDim.x) {
+        const uint32_t L = L_per_q[q];
+        const uint32_t b = (L >= 1 && L <= (uint32_t)bang::kMaxL) ? L : 0u;
+        order[atomicAdd(&cursor[b], 1u)] = q;
+    }
+}
+
+std::mutex g_noalloc_mu;
+unsigned int *g_noalloc_addr[128] = {};                       // per device ordinal
+
+}  // namespace
+
+extern "C" {
+
+int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq,
+                                const uint32_t *k_per_q, const uint32_t *L_per_q, uint32_t k_max,
+                                uint32_t L_max, const bang_search_params *params,
+                                uint32_t *out_ids, float *out_dist, void *stream)
+{
+    if (!ix) return fail(BANG_EINVAL, "bang_search_batched_noalloc: index is NULL");
+    if (!ix->have_pq || !ix->have_graph || !ix->have_vectors)
+        return fail(BANG_ESTATE, "bang_search_batched_noalloc: PQ data, graph and vectors must all be set");
+    if (k_max == 0 || k_max > (uint32_t)bang::kMaxK)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: k_max=%u outside 1..%d", k_max, bang::kMaxK);
+    if (L_max < k_max || L_max > (uint32_t)bang::kMaxL)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: L_max=%u must satisfy k_max <= L_max <= %d",
+                    L_max, bang::kMaxL);
+    if (nq > kNoAllocMaxQueries)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: nq=%u exceeds the %u queries its static "
+                    "scratch holds; split the batch or use bang_search_batched", nq, kNoAllocMaxQueries);
+    if (nq == 0) return BANG_OK;
+    bang_search_params p;
+    std::memset(&p, 0, sizeof p);
+    if (params) p = *params;
+    const uint32_t log2z = p.bloom_log2 ? p.bloom_log2 : 16u;
+    if (log2z < 10 || log2z > 20)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: bloom_log2=%u outside 10..20", log2z);
+    if (p.mode > 2) return fail(BANG_EINVAL, "bang_search_batched_noalloc: unknown mode %u", p.mode);
+    if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search_batched_noalloc: trace_cap is 0");
+    const void *ptrs[10] = {queries, k_per_q, L_per_q, out_ids, out_dist, p.out_iters, p.out_status,
+                            p.out_ndist, p.trace, p.out_phase_cycles};
+    for (int i = 0; i < 10; ++i) {
+        if (i < 5 && !ptrs[i]) return fail(BANG_EINVAL, "bang_search_batched_noalloc: NULL buffer");
+        if (ptrs[i] && !is_device_accessible(ptrs[i]))
+            return fail(BANG_EINVAL, "bang_search_batched_noalloc: every buffer must be device memory "
+                        "(host buffers would need staging allocations)");
+    }
+    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, (int)p.mode);
+    if (lay.total > 227u * 1024u)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: %u bytes of shared memory per query "
+                    "exceed 227 KB", lay.total);
+
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    unsigned int *scratch = nullptr;
+    {
+        // set-up, once per device, with that device current: the array's
+        // device address (its name in host code is only a host-side stand-in)
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (ix->device < 0 || ix->device >= 128)
+            return fail(BANG_EINVAL, "bang_search_batched_noalloc: device %d out of range", ix->device);
+        if (!g_noalloc_addr[ix->device]) {
+            void *addr = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
+            if (e != cudaSuccess)
+                return fail(BANG_ECUDA, "bang_search_batched_noalloc: cudaGetSymbolAddress failed: %s",
+                            cudaGetErrorString(e));
+            g_noalloc_addr[ix->device] = static_cast<unsigned int *>(addr);
+        }
+        scratch = g_noalloc_addr[ix->device];
+    }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    noalloc_order_by_L<<<1, 1024, 0, st>>>(L_per_q, nq);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess)
+        return fail(BANG_ECUDA, "bang_search_batched_noalloc: order kernel launch failed: %s",
+                    cudaGetErrorString(e));
+
+    bang::SearchArgs a;
+    std::memset(&a, 0, sizeof a);
+    a.queries = queries;
+    a.codebook = ix->codebook;
+    a.off = ix->off;
+    a.codes = ix->codes;
+    a.adj = static_cast<const uint32_t *>((ix->placement & BANG_GRAPH_IN_HBM) ? ix->adj_hbm.p : ix->adj.dev);
+    a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
+    a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
+    a.medoid = ix->medoid;
+    a.nq = nq; a.k = k_max; a.L = L_max; a.log2z = log2z; a.iter_cap = p.iter_cap;
+    a.out_ids = out_ids;
+    a.out_dist = out_dist;
+    a.out_iters = p.out_iters;
+    a.out_status = p.out_status;
+    a.out_ndist = p.out_ndist;
+    a.trace = p.trace;
+    a.trace_cap = p.trace_cap;
+    a.phase_cycles = p.out_phase_cycles;
+    a.k_per_q = k_per_q;
+    a.L_per_q = L_per_q;
+    a.order = scratch + kNoAllocOrder;
+    a.queue = scratch;
+    a.grid_mult = p.grid_mult;
+    const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
+    const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
+    a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;
+    a.vecb_ok = (ix->d % 4 == 0) && (ba % 16 == 0) ? 1u : 0u;
+    if (p.mode == 0) e = bang::launch_search_f32(a, ix->dtype, lay.total, st);
+    else if (p.mode == 1) e = bang::launch_search_bf16(a, ix->dtype, lay.total, st);
+    else e = bang::launch_search_exact(a, ix->dtype, lay.total, st);
+    if (e != cudaSuccess)
+        return fail(BANG_ECUDA, "bang_search_batched_noalloc: search kernel launch failed: %s",
+                    cudaGetErrorString(e));
+    return BANG_OK;
+}
+
+}  // extern "C"
