@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--bloom-log2", type=int, default=16)
     ap.add_argument("--cpu-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serving", action="store_true")
     return ap.parse_args()
 
 
@@ -136,6 +137,53 @@ def measured_peaks():
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         return {}
+
+
+def serving(bang, ix, w, L, mode, capacity_qps, log2z, seconds=2.0):
+    """Continuous batching under Poisson arrivals of requests of 1..1024
+    queries (uniform), k = 10, at fractions of the measured batch throughput:
+    achieved queries/s and p50/p99 latency (submit to results on the host)."""
+    import threading
+    srv = bang.Server(ix, K, L, max_batch=1024, streams=4, mode=mode, bloom_log2=log2z)
+    rng = np.random.default_rng(7)
+    nqall = w["queries"].shape[0]
+    out = []
+    for frac in (0.3, 0.6, 0.9):
+        rate_q = frac * capacity_qps
+        mean_req = 512.5
+        nreq = max(20, int(rate_q / mean_req * seconds))
+        sizes = rng.integers(1, 1025, size=nreq)
+        gaps = rng.exponential(mean_req / rate_q, size=nreq)
+        starts = rng.integers(0, nqall - 1024, size=nreq)
+        tickets, lat = [None] * nreq, [0.0] * nreq
+        done_t = [0.0]
+
+        def waiter():
+            for i in range(nreq):
+                while tickets[i] is None:
+                    time.sleep(5e-5)
+                lat[i] = srv.wait(tickets[i])[2]
+            done_t[0] = time.perf_counter()
+
+        th = threading.Thread(target=waiter)
+        th.start()
+        t0 = time.perf_counter()
+        t_next = t0
+        for i in range(nreq):
+            t_next += gaps[i]
+            while time.perf_counter() < t_next:
+                time.sleep(min(2e-4, max(0.0, t_next - time.perf_counter())))
+            n = int(sizes[i])
+            q = w["queries"][starts[i]:starts[i] + n]
+            tickets[i] = srv.submit(q, np.full(n, K, np.uint32), np.full(n, L, np.uint32))
+        th.join()
+        span = done_t[0] - t0
+        out.append({"offered_qps": rate_q, "achieved_qps": float(sizes.sum()) / span,
+                    "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
+                    "p99_ms": float(np.percentile(lat, 99))})
+    srv.stop()
+    return {"what": "Poisson arrivals of 1..1024-query requests, k=10, L=%d, 4 streams, "
+                    "max 1024 queries per launch" % L, "points": out}
 
 
 def cpu_baseline(w, L, sample, log2z):
@@ -389,6 +437,8 @@ def main():
         "clocks": clk.summary(),
         "wall_s_timed_region": res["fp32"]["t_wall"] + res["bf16"]["t_wall"],
     }
+    if not args.no_serving:
+        line["serving"] = serving(bang, ix, w, L, mode, head["value"], args.bloom_log2)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, res["fp32"]["L"], min(args.cpu_sample, nq),
                                             args.bloom_log2)

@@ -197,6 +197,44 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
  * Blocks until the copies are done.  BANG_ENOMEM if the device is full. */
 int bang_set_placement(bang_index *ix, uint32_t flags);
 
+/* Sizes of a loaded index (any pointer may be NULL); dtype is a bang_dtype,
+ * -1 before bang_register_vectors. */
+int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M, uint32_t *R,
+                    int32_t *dtype);
+
+/* ---- Serving: continuous batching (north of the paper's batch-at-a-time
+ * evaluation, §6.2 runs one batch of 10,000 queries).  A server owns
+ * `streams` slots, each with page-locked and device buffers for max_batch
+ * queries allocated at start (admission is by device memory: a request waits
+ * for a free slot).  A dispatcher thread packs pending requests into one
+ * bang_search_batched launch per free slot; launches on different slots
+ * overlap on the GPU.  Results are identical to searching each request alone
+ * with the same k, L and settings. */
+typedef struct bang_server bang_server;
+typedef struct bang_server_config {
+    uint32_t k_max, L_max;   /* bounds of every request's k and L */
+    uint32_t max_batch;      /* queries per launch, and per request, at most */
+    uint32_t streams;        /* slots (launches in flight at once), 1..16 */
+    uint32_t mode;           /* bang_mode of the searches */
+    uint32_t bloom_log2;     /* as bang_search_params (0 = 16) */
+} bang_server_config;
+
+/* Start a server on the calling thread's current device for a fully loaded
+ * index (which must outlive the server).  BANG_ENOMEM if the slots do not fit. */
+int bang_server_start(bang_index *ix, const bang_server_config *cfg, bang_server **out);
+/* Queue nq (1..max_batch) host queries with their k and L (host arrays,
+ * copied before return); *ticket identifies the request. */
+int bang_server_submit(bang_server *s, const void *queries, uint32_t nq, const uint32_t *k_per_q,
+                       const uint32_t *L_per_q, uint64_t *ticket);
+/* Wait up to timeout_ms (negative: no limit) for a request, copy its results
+ * (nq*k_max ids and distances, rows padded as bang_search_batched) to host
+ * memory and release the ticket; *latency_ms = submit to results in host
+ * memory.  BANG_ETIMEOUT leaves the ticket valid. */
+int bang_server_wait(bang_server *s, uint64_t ticket, int32_t timeout_ms, uint32_t *out_ids,
+                     float *out_dist, double *latency_ms);
+/* Finish queued and running requests, then free the server. */
+int bang_server_stop(bang_server *s);
+
 /* Release device memory, unregister host memory registered by the library
  * and free the handle.  NULL is accepted. */
 int bang_destroy(bang_index *ix);

@@ -49,6 +49,12 @@ def bang_probe_host_link(device=0, nbytes=1 << 30, row_bytes=256):
                 latency_ns=out.latency_ns, gather_row_bytes=out.gather_row_bytes)
 
 
+class bang_server_config(ctypes.Structure):
+    _fields_ = [("k_max", ctypes.c_uint32), ("L_max", ctypes.c_uint32),
+                ("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32),
+                ("mode", ctypes.c_uint32), ("bloom_log2", ctypes.c_uint32)]
+
+
 def library_path():
     return _build.LIB
 
@@ -73,12 +79,19 @@ def _load():
     L.bang_search_batched.argtypes = [vp, vp, u32, vp, vp, u32, u32,
                                       ctypes.POINTER(bang_search_params), vp, vp, vp]
     L.bang_search_batched_noalloc.argtypes = L.bang_search_batched.argtypes
+    L.bang_index_info.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.bang_server_start.argtypes = [vp, ctypes.POINTER(bang_server_config), ctypes.POINTER(vp)]
+    L.bang_server_submit.argtypes = [vp, vp, u32, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
+    L.bang_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, vp, vp,
+                                   ctypes.POINTER(ctypes.c_double)]
+    L.bang_server_stop.argtypes = [vp]
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
     L.bang_probe_host_link.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
-              "bang_search_batched_noalloc"):
+              "bang_search_batched_noalloc", "bang_index_info", "bang_server_start",
+              "bang_server_submit", "bang_server_wait", "bang_server_stop"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -224,3 +237,40 @@ class Index:
             self.close()
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching server over an Index (see bang_server_* in bang.h).
+    submit() copies host queries and returns a ticket; wait() returns the
+    request's ids, distances (nq x k_max) and latency in milliseconds."""
+
+    def __init__(self, index, k_max, L_max, max_batch=1024, streams=4, mode=0, bloom_log2=0):
+        self.index = index
+        self.k_max = k_max
+        cfg = bang_server_config(k_max, L_max, max_batch, streams, mode, bloom_log2)
+        h = ctypes.c_void_p()
+        _check(lib().bang_server_start(index.h, ctypes.byref(cfg), ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, queries, k_per_q, L_per_q):
+        q = np.ascontiguousarray(queries)
+        k = np.ascontiguousarray(k_per_q, np.uint32)
+        L = np.ascontiguousarray(L_per_q, np.uint32)
+        t = ctypes.c_uint64()
+        _check(lib().bang_server_submit(self.h, _ptr(q), q.shape[0], _ptr(k), _ptr(L),
+                                        ctypes.byref(t)))
+        return t.value, q.shape[0]
+
+    def wait(self, ticket, timeout_ms=-1):
+        t, nq = ticket
+        ids = np.zeros((nq, self.k_max), np.uint32)
+        dist = np.zeros((nq, self.k_max), np.float32)
+        lat = ctypes.c_double()
+        _check(lib().bang_server_wait(self.h, t, timeout_ms, _ptr(ids), _ptr(dist),
+                                      ctypes.byref(lat)))
+        return ids, dist, lat.value
+
+    def stop(self):
+        if self.h is not None:
+            _check(lib().bang_server_stop(self.h))
+            self.h = None

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "bang.h"
+#include "bang_internal.h"
 #include "search_kernel.cuh"
 
 namespace {
@@ -136,6 +137,10 @@ struct DevBuf {
 };
 
 }  // namespace
+
+namespace bang {
+void set_error(const std::string &msg) { g_err = msg; }
+}  // namespace bang
 
 struct bang_index {
     int device = 0;
@@ -473,6 +478,18 @@ int bang_search_batched(bang_index *ix, const void *queries, uint32_t nq, const 
 {
     return search_impl(ix, queries, nq, k_max, L_max, k_per_q, L_per_q, true, params, out_ids,
                        out_dist, stream);
+}
+
+int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M, uint32_t *R,
+                    int32_t *dtype)
+{
+    if (!ix) return fail(BANG_EINVAL, "bang_index_info: index is NULL");
+    if (n) *n = ix->n;
+    if (d) *d = ix->d;
+    if (M) *M = ix->M;
+    if (R) *R = ix->R;
+    if (dtype) *dtype = ix->dtype;
+    return BANG_OK;
 }
 
 int bang_set_placement(bang_index *ix, uint32_t flags)

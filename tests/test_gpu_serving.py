@@ -1,0 +1,76 @@
+"""Serving with continuous batching: requests submitted from several threads
+while others run are packed into overlapping launches, and every request's
+result equals the same request searched alone (FP32 form: bit for bit)."""
+import threading
+
+import numpy as np
+import pytest
+
+from tests import cases
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2401_11324_gb300 as bang  # noqa: E402
+
+
+@pytest.fixture(scope="module")
+def index():
+    w = cases.clustered(n=20_000, nq=300, ncomp=8)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    yield w, ix
+    ix.close()
+
+
+def _alone(ix, Q, k, L, kmax, Lmax):
+    ids = np.zeros((len(Q), kmax), np.uint32)
+    dist = np.zeros((len(Q), kmax), np.float32)
+    ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist)
+    return ids, dist
+
+
+def test_each_result_same_alone_and_in_the_mix(index):
+    w, ix = index
+    kmax, Lmax = 10, 128
+    srv = bang.Server(ix, kmax, Lmax, max_batch=96, streams=3)
+    rng = np.random.default_rng(11)
+    reqs = []
+    for _ in range(60):
+        n = int(rng.integers(1, 40))
+        sel = rng.choice(w["queries"].shape[0], n, replace=False)
+        k = rng.choice([1, 5, 10], size=n).astype(np.uint32)
+        L = np.maximum(rng.choice([16, 64, 128], size=n), k).astype(np.uint32)
+        reqs.append((w["queries"][sel], k, L))
+    tickets = [None] * len(reqs)
+
+    def submitter(part):
+        for i in part:
+            tickets[i] = srv.submit(*reqs[i])
+
+    th = [threading.Thread(target=submitter, args=(range(j, len(reqs), 2),)) for j in range(2)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    lat = []
+    for i, (Q, k, L) in enumerate(reqs):
+        ids, dist, ms = srv.wait(tickets[i], timeout_ms=60_000)
+        ids_a, dist_a = _alone(ix, Q, k, L, kmax, Lmax)
+        assert (ids == ids_a).all(), i
+        fin = np.isfinite(dist_a)
+        assert (dist[fin] == dist_a[fin]).all() and np.isinf(dist[~fin]).all()
+        lat.append(ms)
+    assert min(lat) > 0
+    srv.stop()
+
+
+def test_server_rejects_oversized_requests(index):
+    w, ix = index
+    srv = bang.Server(ix, 10, 64, max_batch=8, streams=1)
+    with pytest.raises(bang.BangError) as e:
+        srv.submit(w["queries"][:9], np.full(9, 10, np.uint32), np.full(9, 64, np.uint32))
+    assert e.value.code == bang.BANG_EINVAL
+    t = srv.submit(w["queries"][:8], np.full(8, 10, np.uint32), np.full(8, 64, np.uint32))
+    ids, _, _ = srv.wait(t)
+    assert (ids != bang.BANG_NONE).any()
+    srv.stop()
