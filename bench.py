@@ -242,10 +242,17 @@ def run_reference(args):
     return 0
 
 
+# DRAM traffic per launch of the head form's kernel from one ncu capture of
+# the current kernel version (profiles/search_kernel_bf16_u8_n1M.md); set to
+# None whenever that kernel changes.
+NCU_TRAFFIC = {"bf16": 33514752 + 256}
+
 FORMS = {
     # name: (distance mode, placement flags, what it is)
     "fp32": (0, 0, "plain method: FP32 PQ table, graph and vectors in host memory (Alg. 2)"),
     "bf16": (1, 0, "reduced precision: BF16 PQ table summed in FP32, host graph and vectors"),
+    "bf16_tc": (1, 0, "reduced precision with the BF16 tables of the whole batch built on the "
+                      "tensor cores (tcgen05) first"),
     "in_memory": (0, 3, "In-memory variant (§5.1): FP32 PQ table, graph and vectors in HBM"),
     "exact": (2, 3, "Exact-distance variant (§5.2): exact distances, graph and vectors in HBM"),
 }
@@ -289,19 +296,19 @@ def main():
             ix.set_placement(flags)
             placement[0] = flags
 
-    def search(L, mode, with_stats=False, phase=None):
-        p = bang.make_params(bloom_log2=args.bloom_log2, mode=mode,
+    def search(L, mode, with_stats=False, phase=None, tsrc=0):
+        p = bang.make_params(bloom_log2=args.bloom_log2, mode=mode, table_source=tsrc,
                              out_iters=iters if with_stats else None,
                              out_ndist=ndist if with_stats else None, out_phase_cycles=phase)
         ix.search(q_dev, K, L, ids, dist_out, p, stream=sptr)
 
-    def operating_point(mode):
+    def operating_point(mode, tsrc=0):
         """Smallest L of the sweep with recall@10 >= 0.9 (or --L)."""
         sweep = []
         if args.L is not None:
             return args.L, sweep
         for Lc in L_SWEEP:
-            search(Lc, mode)
+            search(Lc, mode, tsrc=tsrc)
             stream.synchronize()
             rc = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
             sweep.append({"L": Lc, "recall@10": round(rc, 4)})
@@ -309,9 +316,9 @@ def main():
                 return Lc, sweep
         return L_SWEEP[-1], sweep
 
-    def timed(L, mode, steps, clk=None):
+    def timed(L, mode, steps, tsrc=0):
         for _ in range(args.warmup):
-            search(L, mode)
+            search(L, mode, tsrc=tsrc)
         stream.synchronize()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -322,7 +329,7 @@ def main():
             with torch.cuda.stream(stream):
                 flush.fill_(s & 0xFF)
                 starts[s].record(stream)
-            search(L, mode)
+            search(L, mode, tsrc=tsrc)
             ends[s].record(stream)
         stream.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -338,15 +345,16 @@ def main():
 
     def measure(name, steps):
         mode, flags, what = FORMS[name]
+        tsrc = 1 if name.endswith("_tc") else 0
         place(flags)
-        L, sweep = operating_point(mode)
-        search(L, mode, with_stats=True)
+        L, sweep = operating_point(mode, tsrc)
+        search(L, mode, with_stats=True, tsrc=tsrc)
         stream.synchronize()
         rec = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
         it = iters.cpu().numpy().astype(np.int64)
         nd = ndist.cpu().numpy().astype(np.int64)
-        total_ms, step_ms, t_wall = timed(L, mode, steps)
-        return dict(form=name, what=what, mode=mode, placement=flags, L=L,
+        total_ms, step_ms, t_wall = timed(L, mode, steps, tsrc)
+        return dict(form=name, what=what, mode=mode, placement=flags, L=L, tsrc=tsrc,
                     recall=round(rec, 4), sweep=sweep, iters=it, ndist=nd,
                     value=nq * world * steps / (total_ms / 1e3), ms_per_step=total_ms / steps,
                     launch_s=statistics.mean(step_ms) / 1e3, t_wall=t_wall)
@@ -354,18 +362,18 @@ def main():
     # ---- the two forms of the paper's base method (host graph): time both,
     # report the faster at recall@10 >= 0.9 with the plain form beside it
     with ClockSampler(local) as clk:
-        res = {f: measure(f, args.steps) for f in ("fp32", "bf16")}
-    ok = [f for f in ("bf16", "fp32") if res[f]["recall"] >= TARGET_RECALL]
+        res = {f: measure(f, args.steps) for f in ("fp32", "bf16", "bf16_tc")}
+    ok = [f for f in ("bf16_tc", "bf16", "fp32") if res[f]["recall"] >= TARGET_RECALL]
     head = res[max(ok, key=lambda f: res[f]["value"])] if ok else res["fp32"]
     variants = {f: measure(f, max(5, args.steps // 5)) for f in ("in_memory", "exact")}
     place(0)
-    L, mode = head["L"], head["mode"]
+    L, mode, tsrc = head["L"], head["mode"], head["tsrc"]
     it, nd = head["iters"], head["ndist"]
 
     # ---- per-phase SM cycles of the fused kernel (one untimed launch): the
     # counterpart of the paper's per-kernel share of GPU time
     phase = torch.zeros((nq, len(bang.PHASES)), dtype=torch.int64, device=dev)
-    search(L, mode, phase=phase)
+    search(L, mode, phase=phase, tsrc=tsrc)
     stream.synchronize()
     ph = phase.cpu().numpy().astype(np.float64).sum(0)
     phases = {name: round(float(ph[i] / ph[-1]), 4) for i, name in enumerate(bang.PHASES[:-1])}
@@ -380,7 +388,7 @@ def main():
     q_host = torch.from_numpy(w["queries"]).pin_memory()
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-    hp = bang.make_params(bloom_log2=args.bloom_log2, mode=mode)
+    hp = bang.make_params(bloom_log2=args.bloom_log2, mode=mode, table_source=tsrc)
     for _ in range(2):
         ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))
@@ -388,7 +396,7 @@ def main():
     for _ in range(e2e_steps):
         ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    search(L, mode)
+    search(L, mode, tsrc=tsrc)
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
 
@@ -418,7 +426,8 @@ def main():
         "plain_form": brief(res["fp32"]),
         "forms": {f: brief(r) for f, r in list(res.items()) + list(variants.items())},
         "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": hbm_gbs / hbm_peak, "traffic": None,
+                     "frac": hbm_gbs / hbm_peak,
+                     "traffic": NCU_TRAFFIC.get(head["form"]) if args.n is None else None,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "algorithmic_bytes_per_launch": hbm_bytes},
         "host_link": {"achieved_gbs": host_bytes / launch_s / 1e9,
@@ -433,9 +442,9 @@ def main():
                               "page-locked host memory"},
         "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d,
                 "d2h_bytes_per_step": nq * K * 8},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if tsrc else 1),
         "clocks": clk.summary(),
-        "wall_s_timed_region": res["fp32"]["t_wall"] + res["bf16"]["t_wall"],
+        "wall_s_timed_region": sum(r["t_wall"] for r in res.values()),
     }
     if not args.no_serving:
         line["serving"] = serving(bang, ix, w, L, mode, head["value"], args.bloom_log2)

@@ -56,7 +56,9 @@ typedef struct bang_search_params {
     uint32_t iter_cap;
     /* Optional per-query outputs (nq entries each), host or device:
      * expansions (the paper's iteration count I, §7.7), status (0 = converged,
-     * 1 = stopped by iter_cap), and PQ distances computed (§4.4). */
+     * 1 = stopped by iter_cap, 2 = its tensor-core table could not be built,
+     * -1 = its k or L out of range in the batched form), and PQ distances
+     * computed (§4.4). */
     uint32_t *out_iters;
     int32_t *out_status;
     uint32_t *out_ndist;
@@ -81,6 +83,11 @@ typedef struct bang_search_params {
     /* bang_search_batched only: the persistent grid is grid_mult times the
      * CTAs that fit on the device at once (0 or 1: exactly that many). */
     uint32_t grid_mult;
+    /* Where the PQ tables of mode 1 come from: 0 = built by each query's warp
+     * on CUDA cores; 1 = built for the whole batch by the tensor-core kernel
+     * of bang_pq_tables into per-stream device scratch owned by the index
+     * (nq*M*512 bytes), then read by the search. */
+    uint32_t table_source;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2 } bang_mode;
@@ -196,6 +203,17 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
  * the corresponding array is registered again or the flag is cleared.
  * Blocks until the copies are done.  BANG_ENOMEM if the device is full. */
 int bang_set_placement(bang_index *ix, uint32_t flags);
+
+/* PQ distance tables of nq queries on the tensor cores (§4.1 as a dense
+ * queries x centroids contraction: tcgen05 MMAs with BF16 high/low operand
+ * splits and FP32 accumulation, about FP32-accurate):
+ * out[q][s][c] = ||q_s - C_s[c]||^2, M x 256 per query, FP32 or (out_bf16)
+ * BF16.  queries and out are device memory; waits for the stream.  Needs the
+ * vectors registered (for the element type); BANG_EINVAL if a subspace
+ * spans more than 4 blocks of 16 dimensions; BANG_ETIMEOUT if a bounded
+ * tensor-core wait gave up. */
+int bang_pq_tables(bang_index *ix, const void *queries, uint32_t nq, void *out, uint32_t out_bf16,
+                   void *stream);
 
 /* Sizes of a loaded index (any pointer may be NULL); dtype is a bang_dtype,
  * -1 before bang_register_vectors. */

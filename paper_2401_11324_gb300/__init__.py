@@ -34,7 +34,8 @@ class bang_search_params(ctypes.Structure):
                 ("out_iters", ctypes.c_void_p), ("out_status", ctypes.c_void_p),
                 ("out_ndist", ctypes.c_void_p), ("trace", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_uint32), ("out_phase_cycles", ctypes.c_void_p),
-                ("mode", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32)]
+                ("mode", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32),
+                ("table_source", ctypes.c_uint32)]
 
 
 class bang_link_probe(ctypes.Structure):
@@ -80,6 +81,7 @@ def _load():
                                       ctypes.POINTER(bang_search_params), vp, vp, vp]
     L.bang_search_batched_noalloc.argtypes = L.bang_search_batched.argtypes
     L.bang_index_info.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.bang_pq_tables.argtypes = [vp, vp, u32, vp, u32, vp]
     L.bang_server_start.argtypes = [vp, ctypes.POINTER(bang_server_config), ctypes.POINTER(vp)]
     L.bang_server_submit.argtypes = [vp, vp, u32, vp, vp, ctypes.POINTER(ctypes.c_uint64)]
     L.bang_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, vp, vp,
@@ -90,7 +92,7 @@ def _load():
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
-              "bang_search_batched_noalloc", "bang_index_info", "bang_server_start",
+              "bang_search_batched_noalloc", "bang_index_info", "bang_server_start", "bang_pq_tables",
               "bang_server_submit", "bang_server_wait", "bang_server_stop"):
         getattr(L, f).restype = i32
     _lib = L
@@ -152,10 +154,11 @@ BANG_GRAPH_IN_HBM, BANG_VECTORS_IN_HBM = 1, 2
 
 
 def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
-                trace=None, trace_cap=0, out_phase_cycles=None, mode=0, grid_mult=0):
+                trace=None, trace_cap=0, out_phase_cycles=None, mode=0, grid_mult=0,
+                table_source=0):
     return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
                               _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles), mode,
-                              grid_mult)
+                              grid_mult, table_source)
 
 
 def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
@@ -182,6 +185,11 @@ def bang_search_batched_noalloc(ix, queries, nq, k_per_q, L_per_q, k_max, L_max,
     return _check(lib().bang_search_batched_noalloc(ix, _ptr(queries), nq, _ptr(k_per_q),
                                                     _ptr(L_per_q), k_max, L_max, p, _ptr(out_ids),
                                                     _ptr(out_dist), s))
+
+
+def bang_pq_tables(ix, queries, nq, out, out_bf16=0, stream=None):
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    return _check(lib().bang_pq_tables(ix, _ptr(queries), nq, _ptr(out), out_bf16, s))
 
 
 def bang_set_placement(ix, flags):

@@ -12,9 +12,9 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libbang.so")
-SOURCES = ["bang_api.cu", "link_probe.cu", "server.cu", "search_f32.cu", "search_bf16.cu",
-           "search_exact.cu"]
-HEADERS = ["search_kernel.cuh", "bang_internal.h"]
+SOURCES = ["bang_api.cu", "link_probe.cu", "server.cu", "adc_table_tc.cu", "search_f32.cu",
+           "search_bf16.cu", "search_exact.cu"]
+HEADERS = ["search_kernel.cuh", "bang_internal.h", "adc_table_tc.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "bang.h"
+#include "adc_table_tc.h"
 #include "bang_internal.h"
 #include "search_kernel.cuh"
 
@@ -158,6 +159,12 @@ struct bang_index {
     uint32_t placement = 0;
     // Batched form: per-stream work counter, query order and staged k / L.
     std::map<cudaStream_t, DevBuf> work;
+    // Tensor-core tables: centroid tiles (BF16 hi/lo, core-matrix layout),
+    // first tile per subspace, squared centroid norms; per-stream table
+    // scratch for searches that read precomputed tables; error flag.
+    DevBuf tc_btiles, tc_bfirst, tc_cnorm, tc_err;
+    bool tc_ok = false;
+    std::map<cudaStream_t, DevBuf> tables;
 };
 
 namespace {
@@ -175,6 +182,65 @@ struct DeviceGuard {
         if (prev >= 0) cudaSetDevice(prev);
     }
 };
+
+// Round-to-nearest-even FP32 -> BF16 (finite inputs).
+uint16_t bf16_rne(float x)
+{
+    uint32_t b;
+    std::memcpy(&b, &x, 4);
+    b += 0x7FFFu + ((b >> 16) & 1u);
+    return static_cast<uint16_t>(b >> 16);
+}
+float bf16_to_f32(uint16_t h)
+{
+    const uint32_t b = static_cast<uint32_t>(h) << 16;
+    float x;
+    std::memcpy(&x, &b, 4);
+    return x;
+}
+
+// Centroid operands of the tensor-core table kernel: for every subspace and
+// every 16-wide K block it touches, a 256 x 16 BF16 tile of the centroids
+// (zero outside the subspace's dimensions) in the no-swizzle K-major
+// core-matrix layout, split into high, middle and low BF16 parts.
+bool build_tc_tiles(const float *codebook, uint32_t d, uint32_t M, const std::vector<uint32_t> &off,
+                    std::vector<uint16_t> &tiles, std::vector<uint32_t> &first, std::vector<float> &cnorm)
+{
+    const uint32_t elems = 256u * 16u;                  // one tile
+    first.assign(M, 0);
+    cnorm.assign((size_t)M * 256, 0.0f);
+    tiles.clear();
+    for (uint32_t s = 0; s < M; ++s) {
+        const uint32_t o = off[s], ds = off[s + 1] - o;
+        const uint32_t kb0 = o / 16, kb1 = (o + ds - 1) / 16;
+        if (kb1 - kb0 + 1 > bang::kMaxKbPerSub) return false;
+        first[s] = static_cast<uint32_t>(tiles.size() / elems);
+        const float *cb = codebook + (size_t)256 * o;
+        for (uint32_t c = 0; c < 256; ++c) {
+            double acc = 0.0;
+            for (uint32_t j = 0; j < ds; ++j) acc += (double)cb[c * ds + j] * (double)cb[c * ds + j];
+            cnorm[(size_t)s * 256 + c] = static_cast<float>(acc);
+        }
+        for (uint32_t kb = kb0; kb <= kb1; ++kb) {
+            const size_t base = tiles.size();
+            tiles.resize(base + 3 * (size_t)elems, 0);
+            for (uint32_t c = 0; c < 256; ++c)
+                for (uint32_t kk = 0; kk < 16; ++kk) {
+                    const uint32_t j = kb * 16 + kk;
+                    const float x = (j >= o && j < o + ds) ? cb[c * ds + (j - o)] : 0.0f;
+                    const uint16_t hi = bf16_rne(x);
+                    const float r1 = x - bf16_to_f32(hi);
+                    const uint16_t mid = bf16_rne(r1);
+                    const uint16_t lo = bf16_rne(r1 - bf16_to_f32(mid));
+                    const size_t e = (((c >> 3) * 2 + (kk >> 3)) * 128 + (c & 7) * 16 + (kk & 7) * 2) / 2;
+                    tiles[base + e] = hi;
+                    tiles[base + elems + e] = mid;
+                    tiles[base + 2 * (size_t)elems + e] = lo;
+                }
+        }
+    }
+    return true;
+}
 
 std::vector<uint32_t> chunk_offsets(uint32_t d, uint32_t M)
 {
@@ -268,6 +334,23 @@ int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
     if (Mpad != M) CUDA_TRY(cudaMemset(ix->codes, 0, (size_t)n * Mpad));
     CUDA_TRY(cudaMemcpy2D(ix->codes, Mpad, codes, M, M, n, cudaMemcpyHostToDevice));
     ix->d = d; ix->M = M; ix->Mpad = Mpad; ix->n = n;
+    {   // operands of the tensor-core table kernel
+        std::vector<uint16_t> tiles;
+        std::vector<uint32_t> first;
+        std::vector<float> cn;
+        ix->tc_ok = build_tc_tiles(codebook, d, M, off, tiles, first, cn) &&
+                    bang::tc_table_smem_bytes(d, 2) <= 227u * 1024u;
+        if (ix->tc_ok) {
+            CUDA_TRY(ix->tc_btiles.ensure(tiles.size() * 2));
+            CUDA_TRY(ix->tc_bfirst.ensure(first.size() * 4));
+            CUDA_TRY(ix->tc_cnorm.ensure(cn.size() * 4));
+            CUDA_TRY(ix->tc_err.ensure(256));
+            CUDA_TRY(cudaMemcpy(ix->tc_btiles.p, tiles.data(), tiles.size() * 2, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(ix->tc_bfirst.p, first.data(), first.size() * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemcpy(ix->tc_cnorm.p, cn.data(), cn.size() * 4, cudaMemcpyHostToDevice));
+            CUDA_TRY(cudaMemset(ix->tc_err.p, 0, 256));
+        }
+    }
     ix->have_pq = true;
     return BANG_OK;
 }
@@ -393,6 +476,33 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     // Persistent launch: a zeroed work counter, and, when the worklist sizes
     // are on the host, the queries ordered by decreasing L so the longest
     // searches start first.
+    // Tensor-core tables (reduced-precision form): all tables of the batch
+    // into per-stream scratch, then the search reads them.
+    const uint16_t *tables = nullptr;
+    if (p.table_source == 1) {
+        if (p.mode != 1) return fail(BANG_EINVAL, "bang_search: table_source 1 needs mode 1 (BF16 tables)");
+        if (!ix->tc_ok) return fail(BANG_EINVAL, "bang_search: tensor-core tables unavailable for this "
+                                    "PQ layout (a subspace spans more than %u 16-dim blocks)", bang::kMaxKbPerSub);
+        DevBuf &tb = ix->tables[st];
+        CUDA_TRY(tb.ensure((size_t)nq * ix->M * 256 * 2));
+        CUDA_TRY(cudaMemsetAsync(ix->tc_err.p, 0, 4, st));
+        bang::TcTableArgs ta;
+        ta.queries = dptr(0);
+        ta.nq = nq; ta.d = ix->d; ta.M = ix->M;
+        ta.off = ix->off;
+        ta.btiles = static_cast<const unsigned char *>(ix->tc_btiles.p);
+        ta.bfirst = static_cast<const uint32_t *>(ix->tc_bfirst.p);
+        ta.cnorm = static_cast<const float *>(ix->tc_cnorm.p);
+        ta.out = tb.p;
+        ta.out_bf16 = 1;
+        ta.err = static_cast<unsigned int *>(ix->tc_err.p);
+        cudaError_t te = bang::launch_tc_tables(ta, ix->dtype, st);
+        if (te != cudaSuccess) return fail(BANG_ECUDA, "table kernel launch failed: %s", cudaGetErrorString(te));
+        tables = static_cast<const uint16_t *>(tb.p);
+    } else if (p.table_source != 0) {
+        return fail(BANG_EINVAL, "bang_search: unknown table_source %u", p.table_source);
+    }
+
     unsigned int *queue = nullptr;
     const uint32_t *order = nullptr;
     if (persistent) {
@@ -428,6 +538,8 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.order = order;
     a.queue = queue;
     a.grid_mult = p.grid_mult;
+    a.tables = tables;
+    a.tables_err = static_cast<const unsigned int *>(ix->tc_err.p);
     a.out_ids = static_cast<uint32_t *>(dptr(1));
     a.out_dist = static_cast<float *>(dptr(2));
     a.out_iters = static_cast<uint32_t *>(dptr(3));
@@ -478,6 +590,39 @@ int bang_search_batched(bang_index *ix, const void *queries, uint32_t nq, const 
 {
     return search_impl(ix, queries, nq, k_max, L_max, k_per_q, L_per_q, true, params, out_ids,
                        out_dist, stream);
+}
+
+int bang_pq_tables(bang_index *ix, const void *queries, uint32_t nq, void *out, uint32_t out_bf16,
+                   void *stream)
+{
+    if (!ix || !queries || !out) return fail(BANG_EINVAL, "bang_pq_tables: NULL argument");
+    if (!ix->have_pq) return fail(BANG_ESTATE, "bang_pq_tables: load the PQ data first");
+    if (ix->dtype < 0) return fail(BANG_ESTATE, "bang_pq_tables: register the vectors first (element type)");
+    if (!ix->tc_ok) return fail(BANG_EINVAL, "bang_pq_tables: unavailable for this PQ layout");
+    if (!is_device_accessible(queries) || !is_device_accessible(out))
+        return fail(BANG_EINVAL, "bang_pq_tables: queries and out must be device memory");
+    if (nq == 0) return BANG_OK;
+    DeviceGuard g(ix->device);
+    if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    bang::TcTableArgs ta;
+    ta.queries = queries;
+    ta.nq = nq; ta.d = ix->d; ta.M = ix->M;
+    ta.off = ix->off;
+    ta.btiles = static_cast<const unsigned char *>(ix->tc_btiles.p);
+    ta.bfirst = static_cast<const uint32_t *>(ix->tc_bfirst.p);
+    ta.cnorm = static_cast<const float *>(ix->tc_cnorm.p);
+    ta.out = out;
+    ta.out_bf16 = out_bf16 ? 1u : 0u;
+    ta.err = static_cast<unsigned int *>(ix->tc_err.p);
+    CUDA_TRY(cudaMemsetAsync(ix->tc_err.p, 0, 4, st));
+    cudaError_t te = bang::launch_tc_tables(ta, ix->dtype, st);
+    if (te != cudaSuccess) return fail(BANG_ECUDA, "table kernel launch failed: %s", cudaGetErrorString(te));
+    unsigned int flag = 0;
+    CUDA_TRY(cudaMemcpyAsync(&flag, ix->tc_err.p, 4, cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(cudaStreamSynchronize(st));
+    if (flag) return fail(BANG_ETIMEOUT, "bang_pq_tables: a tensor-core wait gave up");
+    return BANG_OK;
 }
 
 int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M, uint32_t *R,
@@ -536,6 +681,11 @@ int bang_destroy(bang_index *ix)
         ix->adj_hbm.release();
         ix->base_hbm.release();
         for (auto &kv : ix->work) kv.second.release();
+        for (auto &kv : ix->tables) kv.second.release();
+        ix->tc_btiles.release();
+        ix->tc_bfirst.release();
+        ix->tc_cnorm.release();
+        ix->tc_err.release();
     }
     delete ix;
     return BANG_OK;
@@ -702,6 +852,8 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.order = scratch + kNoAllocOrder;
     a.queue = scratch;
     a.grid_mult = p.grid_mult;
+    if (p.table_source != 0)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0 (tables need scratch)");
     const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
     const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
     a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;

@@ -75,6 +75,8 @@ struct SearchArgs {
     const uint32_t *order;
     unsigned int *queue;      // device counter, zero at launch; null: grid covers the queries
     uint32_t grid_mult;       // persistent grid = grid_mult x resident CTAs (>= 1)
+    const uint16_t *tables;   // BF16 mode: nq*M*256 precomputed tables (tensor cores), or null
+    const unsigned int *tables_err;  // set when the table kernel gave up
     unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
 };
 
@@ -437,7 +439,15 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         load_share<DT, DCH>(qp, d, a.vec_ok != 0, lane, qs);
         for (uint32_t w = lane; w < nwords; w += kWarp) bloom[w] = 0u;
         __syncwarp();
-        if (kPQ) build_table<MODE>(a, qv, offs, T, lane);
+        bool table_failed = false;
+        if (MODE == kModeBF16 && a.tables) {             // precomputed on the tensor cores
+            table_failed = *a.tables_err != 0u;
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.tables + static_cast<uint64_t>(q) * a.M * 256u);
+            uint4 *dst = reinterpret_cast<uint4 *>(T);
+            for (uint32_t i = lane; i < a.M * 256u * 2u / 16u; i += kWarp) dst[i] = src[i];
+        } else if (kPQ) {
+            build_table<MODE>(a, qv, offs, T, lane);
+        }
         __syncwarp();
         clk.mark(kPhTable);
 
@@ -460,8 +470,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             bloom[p2 >> 5] |= 1u << (p2 & 31u);
         }
         uint32_t nl = 1, nc = 0, iters = 0, ndist = 1, first = 0;
-        bool have_next = true;
-        int32_t status = 0;
+        bool have_next = !table_failed;
+        int32_t status = table_failed ? 2 : 0;
         uint64_t ck = ~0ull;               // register top-k (k <= kRegK): lane i holds rank i
         uint32_t cur = a.medoid;
         NodeData<DT, RPL, DCH> nd;
