@@ -60,6 +60,18 @@ def dist_env():
     return rank, world, local
 
 
+def job_throughput(units_per_rank, steps, total_ms_local, world, dist=None, device="cpu"):
+    """Whole-job units/s for replicas: every rank processed units_per_rank per
+    step; the job took as long as the slowest rank.  Returns (units/s, ms)."""
+    t = float(total_ms_local)
+    if world > 1:
+        import torch
+        x = torch.tensor([t], dtype=torch.float64, device=device)
+        dist.all_reduce(x, op=dist.ReduceOp.MAX)
+        t = float(x.item())
+    return units_per_rank * world * steps / (t / 1e3), t
+
+
 def load_workload(args, rank, world, barrier):
     import workload
     kw = dict(n=args.n, nq=args.nq, ncomp=args.ncomp, k=100)
@@ -336,11 +348,7 @@ def main():
         torch.cuda.synchronize(dev)
         barrier()
         step_ms = [starts[s].elapsed_time(ends[s]) for s in range(steps)]
-        total_ms = sum(step_ms)
-        if world > 1:
-            t = torch.tensor([total_ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        _, total_ms = job_throughput(nq, steps, sum(step_ms), world, dist, dev)
         return total_ms, step_ms, t_wall
 
     def measure(name, steps):
