@@ -8,7 +8,7 @@ test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 no code with the CUDA implementation.
 
 Parity status of each function (see the C file for the passage it follows):
-  pq_train, pq_encode, medoid, adc_table, adc_dist, exact_dist, bloom,
+  pq_train, pq_encode, medoid, adc_table, adc_dist, adc_table_q8, adc_dist_q8, exact_dist, bloom,
   search, bruteforce_knn : pinned by tests/test_oracle_*.py
   vamana_build           : invariants only ("parity unpinned" beyond degree,
                            self-loop, duplicate, pruning-rule and reachability
@@ -76,6 +76,9 @@ def lib():
         L.orc_adc_table_f32.argtypes = [vp, u32, vp, vp, vp]
         L.orc_adc_dist_f32.argtypes = [vp, u32, vp]
         L.orc_adc_dist_f32.restype = f32
+        L.orc_adc_table_q8.argtypes = [vp, u32, vp]
+        L.orc_adc_dist_q8.argtypes = [vp, u32, vp]
+        L.orc_adc_dist_q8.restype = u32
         L.orc_exact_dist.argtypes = [vp, vp, i32, u32]
         L.orc_exact_dist.restype = ctypes.c_double
         L.orc_fnv1a32_bytes.argtypes = [ctypes.c_char_p, u32]
@@ -179,6 +182,20 @@ def adc_dist(T, code):
     return float(lib().orc_adc_dist_f32(_p(T), T.shape[0], _p(code)))
 
 
+def adc_table_q8(T):
+    """8-bit form of an FP32 table (per-subspace offset, one scale)."""
+    T = _c(T, np.float32)
+    Q = np.zeros(T.shape, np.uint8)
+    lib().orc_adc_table_q8(_p(T), T.shape[0], _p(Q))
+    return Q
+
+
+def adc_dist_q8(Q, code):
+    Q = _c(Q, np.uint8)
+    code = _c(code, np.uint8)
+    return int(lib().orc_adc_dist_q8(_p(Q), Q.shape[0], _p(code)))
+
+
 def exact_dist(q, x):
     q = np.ascontiguousarray(q)
     x = np.ascontiguousarray(x, dtype=q.dtype)
@@ -229,8 +246,12 @@ class Index:
                            self.codes.ctypes.data, self.adj.ctypes.data,
                            self.base.ctypes.data)
 
-    def search(self, queries, k, L, log2z=16, iter_cap=None, trace_cap=0, nthreads=0, exact=False):
-        """Alg. 2 search; exact=True runs the Exact-distance variant (§5.2)."""
+    def search(self, queries, k, L, log2z=16, iter_cap=None, trace_cap=0, nthreads=0, exact=False,
+               q8=False):
+        """Alg. 2 search; exact=True runs the Exact-distance variant (§5.2),
+        q8=True the search on the 8-bit table."""
+        assert not (exact and q8)
+        mode = 1 if exact else (2 if q8 else 0)
         q = np.ascontiguousarray(queries, dtype=self.base.dtype)
         nq = q.shape[0]
         if iter_cap is None:
@@ -241,7 +262,7 @@ class Index:
         status = np.zeros(nq, np.int32)
         ndist = np.zeros(nq, np.uint64)
         trace = np.zeros((nq, trace_cap), np.uint32) if trace_cap else None
-        rc = lib().orc_search(ctypes.byref(self._s), _p(q), 1 if exact else 0, nq, k, L, log2z,
+        rc = lib().orc_search(ctypes.byref(self._s), _p(q), mode, nq, k, L, log2z,
                               iter_cap, _p(ids),
                               _p(dist), _p(iters), _p(status), _p(ndist), _p(trace), trace_cap,
                               nthreads)

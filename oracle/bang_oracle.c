@@ -28,11 +28,15 @@
  *   orc_adc_table_f32        §4.1 (PQDistTable: squared distance of each query
  *                            sub-vector to each centroid)
  *   orc_adc_dist_f32         §4.4 (asymmetric distance = sum of table entries)
+ *   orc_adc_table_q8/_dist_q8 an 8-bit form of the §4.1 table that the paper
+ *                            does not have (its table is FP32): per-subspace
+ *                            offset, one scale per query, integer sums
  *   orc_fnv1a32/_fnv1a64     §4.3, §6.3 (two FNV-1a hash functions)
  *   orc_bloom_*              §4.3 (per-query Bloom filter of visited nodes)
  *   orc_exact_dist           §4.8 (exact distance used by the re-rank)
  *   orc_search               Alg. 1, Alg. 2, §4.3-§4.8; mode 1: the Exact-distance
- *                            variant of §5.2 (exact distances, no table, no re-rank)
+ *                            variant of §5.2 (exact distances, no table, no re-rank);
+ *                            mode 2: mode 0 with the 8-bit table
  *   orc_bruteforce_knn       §6.3 (ground truth S for k-recall@k)
  */
 #include <math.h>
@@ -396,6 +400,60 @@ float orc_adc_dist_f32(const float *T, uint32_t M, const uint8_t *code)
 }
 
 /* ---------------------------------------------------------------------- */
+/* 8-bit table.  Not in the paper, whose table is FP32 (§4.1); added as a   */
+/* reduced form whose table is a quarter of the FP32 one.  From the FP32    */
+/* table T of one query:                                                    */
+/*   lo_s = min_c T[s][c],  w_s = max_c T[s][c] - lo_s  (FP32 subtraction), */
+/*   g = max_s w_s;  if g == 0 every entry is 0; otherwise                  */
+/*   inv = 255 / g (FP32 division) and                                      */
+/*   Q[s][c] = min(255, rint((T[s][c] - lo_s) * inv)),                      */
+/* the subtraction and the product each rounded to FP32, rint rounding      */
+/* halves to even.  Q[s][c] * g / 255 + lo_s approximates T[s][c] within    */
+/* g / 510 plus rounding.  The per-subspace offsets add the same constant   */
+/* to every candidate of the query, so the integer sum of Q ranks the       */
+/* candidates as the dequantised sum does.                                  */
+/* ---------------------------------------------------------------------- */
+
+void orc_adc_table_q8(const float *T, uint32_t M, uint8_t *Q)
+{
+    uint32_t s, c;
+    float g = 0.0f;
+    float *lo = (float *)malloc(sizeof(float) * (M ? M : 1));
+    for (s = 0; s < M; s++) {
+        float mn = T[s * 256], mx = T[s * 256], w;
+        for (c = 1; c < 256; c++) {
+            if (T[s * 256 + c] < mn) mn = T[s * 256 + c];
+            if (T[s * 256 + c] > mx) mx = T[s * 256 + c];
+        }
+        lo[s] = mn;
+        w = mx - mn;
+        if (w > g) g = w;
+    }
+    for (s = 0; s < M; s++) {
+        for (c = 0; c < 256; c++) {
+            uint32_t v = 0;
+            if (g > 0.0f) {
+                float inv = 255.0f / g;
+                float x = (T[s * 256 + c] - lo[s]) * inv;
+                v = (uint32_t)rintf(x);
+                if (v > 255u) v = 255u;
+            }
+            Q[s * 256 + c] = (uint8_t)v;
+        }
+    }
+    free(lo);
+}
+
+/* Asymmetric distance on the 8-bit table: the exact integer sum over the
+ * subspaces of Q[s][code[s]]. */
+uint32_t orc_adc_dist_q8(const uint8_t *Q, uint32_t M, const uint8_t *code)
+{
+    uint32_t s, acc = 0;
+    for (s = 0; s < M; s++) acc += Q[s * 256 + code[s]];
+    return acc;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Exact distance for the re-rank (§4.8).                                   */
 /* Integer data: exact integer sum of squared differences.                  */
 /* FP32 data: 32 partial sums p_r over the dimensions j with                */
@@ -505,6 +563,19 @@ static int entry_cmp(const void *pa, const void *pb)
 
 static int dpair_cmp_stable(const void *pa, const void *pb) { return dpair_cmp(pa, pb); }
 
+/* Distance of node v in the search loop: mode 0 the FP32 PQ distance
+ * (§4.4), mode 1 the exact distance (§5.2), mode 2 the 8-bit table's integer
+ * sum (exact in FP32: at most 255 * M). */
+static float search_dist(const orc_index *ix, int mode, const float *T, const uint8_t *Q,
+                         const void *q, uint32_t v)
+{
+    size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
+    if (mode == 0) return orc_adc_dist_f32(T, ix->M, ix->codes + (uint64_t)v * ix->M);
+    if (mode == 2) return (float)orc_adc_dist_q8(Q, ix->M, ix->codes + (uint64_t)v * ix->M);
+    return (float)orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)v * ix->d * esz,
+                                 ix->dtype, ix->d);
+}
+
 /* One query.  Steps, in the order of Alg. 2 and §4:
  *  - T <- PQDistTable row of the query (§4.1); the query is converted to FP32.
  *  - worklist L <- [(ADC(s), s, unvisited)], s inserted into the Bloom filter.
@@ -529,6 +600,7 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
     uint32_t d = ix->d, M = ix->M, R = ix->R, i, r;
     float *qf = (float *)malloc(sizeof(float) * d);
     float *T = (float *)malloc(sizeof(float) * (size_t)M * 256);
+    uint8_t *Q = (uint8_t *)malloc((size_t)M * 256);
     uint32_t nwords = (log2z >= 5) ? (1u << (log2z - 5)) : 1u;
     uint32_t *bits = (uint32_t *)calloc(nwords, sizeof(uint32_t));
     orc_entry *Lst = (orc_entry *)malloc(sizeof(orc_entry) * (Lsz + R + 1));
@@ -540,12 +612,11 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
 
     for (i = 0; i < d; i++) qf[i] = elem_f(q, ix->dtype, i);
-    if (mode == 0) orc_adc_table_f32(qf, M, ix->off, ix->codebook, T);
+    if (mode != 1) orc_adc_table_f32(qf, M, ix->off, ix->codebook, T);
+    if (mode == 2) orc_adc_table_q8(T, M, Q);
 
     Lst[0].id = ix->medoid;
-    Lst[0].dist = mode == 0 ? orc_adc_dist_f32(T, M, ix->codes + (uint64_t)ix->medoid * M)
-                            : (float)orc_exact_dist(q, (const unsigned char *)ix->base +
-                                                    (uint64_t)ix->medoid * d * esz, ix->dtype, d);
+    Lst[0].dist = search_dist(ix, mode, T, Q, q, ix->medoid);
     Lst[0].visited = 0;
     ndist++;
     nl = 1;
@@ -561,7 +632,7 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
             uint32_t us = Lst[u].id;
             if (trace && iters < trace_cap) trace[iters] = us;
             iters++;
-            if (mode == 0) {
+            if (mode != 1) {
                 C[nc].id = us;
                 C[nc].dist = orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)us * d * esz,
                                             ix->dtype, d);
@@ -577,10 +648,7 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
         nadd = 0;
         for (i = 0; i < nn; i++) {
             Lst[nl + nadd].id = Np[i];
-            Lst[nl + nadd].dist =
-                mode == 0 ? orc_adc_dist_f32(T, M, ix->codes + (uint64_t)Np[i] * M)
-                          : (float)orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)Np[i] * d * esz,
-                                                  ix->dtype, d);
+            Lst[nl + nadd].dist = search_dist(ix, mode, T, Q, q, Np[i]);
             Lst[nl + nadd].visited = 0;
             nadd++;
         }
@@ -589,7 +657,7 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
         nl = (nl + nadd < Lsz) ? nl + nadd : Lsz;
     }
 
-    if (mode != 0) {                    /* Alg. 1: the k nearest entries of the worklist */
+    if (mode == 1) {                    /* Alg. 1: the k nearest entries of the worklist */
         nc = 0;
         for (i = 0; i < nl; i++) { C[nc].id = Lst[i].id; C[nc].dist = (double)Lst[i].dist; nc++; }
     }
@@ -601,7 +669,7 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
     if (out_iters) *out_iters = iters;
     if (out_status) *out_status = status;
     if (out_ndist) *out_ndist = ndist;
-    free(qf); free(T); free(bits); free(Lst); free(Np); free(C);
+    free(qf); free(T); free(Q); free(bits); free(Lst); free(Np); free(C);
 }
 
 int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, uint32_t k,
@@ -611,7 +679,7 @@ int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, 
 {
     int64_t qi;
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
-    if (k == 0 || L < k || ix->M == 0 || ix->d == 0 || mode < 0 || mode > 1) return -1;
+    if (k == 0 || L < k || ix->M == 0 || ix->d == 0 || mode < 0 || mode > 2) return -1;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)

@@ -30,7 +30,13 @@ MUTANTS = [
     ("encode_ties_high", "if (acc < best) { best = acc; bc = c; }", "if (acc <= best) { best = acc; bc = c; }", 1),
     ("prune_alpha_unsquared", "double a2 = (double)alpha * (double)alpha;", "double a2 = (double)alpha;", 0),
     ("bruteforce_l1", "ia += t2 * t2;", "ia += t2 < 0 ? -t2 : t2;", 0),
-    ("exact_mode_keeps_rerank", "if (mode != 0) {                    /* Alg. 1",
+    ("q8_no_offset", "float x = (T[s * 256 + c] - lo[s]) * inv;",
+     "float x = (T[s * 256 + c] - 0.0f * lo[s]) * inv;", 0),
+    ("q8_truncates", "v = (uint32_t)rintf(x);", "v = (uint32_t)x;", 0),
+    ("q8_last_subspace_scale", "if (w > g) g = w;", "g = w;", 0),
+    ("q8_search_uses_exact", "if (mode == 2) return (float)orc_adc_dist_q8(",
+     "if (mode == 9) return (float)orc_adc_dist_q8(", 0),
+    ("exact_mode_keeps_rerank", "if (mode == 1) {                    /* Alg. 1",
      "if (mode == 7) {                    /* Alg. 1", 0),
 ]
 

@@ -107,6 +107,42 @@ def test_adc_dist_is_sum_of_selected_entries():
         assert oracle.adc_dist(T, code) == float(sum(int(T[s, code[s]]) for s in range(M)))
 
 
+def test_q8_table_closed_form():
+    # Subspace 0: entries 2*pi(c), pi a permutation of 0..255 (width 510);
+    # subspace 1: 100 + c (width 255); subspace 2: constant (width 0).  The
+    # widest subspace fixes the scale 255/510 = 1/2 exactly, so subspace 0
+    # maps to pi(c), subspace 1 to c/2 rounded half to even, subspace 2 to 0.
+    perm = (np.arange(256) * 37) % 256
+    T = np.stack([2.0 * perm, 100.0 + np.arange(256), np.full(256, 7.0)]).astype(np.float32)
+    Q = oracle.adc_table_q8(T)
+    assert Q[0].tolist() == perm.tolist()
+    assert Q[1].tolist() == [round(c / 2) for c in range(256)]     # Python rounds halves to even
+    assert Q[1][1] == 0 and Q[1][3] == 2 and Q[1][5] == 2 and Q[1][255] == 128
+    assert not Q[2].any()
+    # the distance is the integer sum of the selected entries
+    assert oracle.adc_dist_q8(Q, np.array([5, 7, 9], np.uint8)) == 185 + 4 + 0
+
+
+def test_q8_table_invariants():
+    rng = np.random.default_rng(21)
+    for trial in range(20):
+        M = int(rng.integers(1, 40))
+        T = (rng.gamma(2.0, 1.0, size=(M, 256)) * rng.uniform(0.1, 1e4, size=(M, 1))).astype(np.float32)
+        Q = oracle.adc_table_q8(T).astype(np.int64)
+        lo = T.astype(np.float64).min(1)
+        width = T.astype(np.float64).max(1) - lo
+        g = width.max()
+        assert (Q.min(1) == 0).all()                       # every subspace's minimum maps to 0
+        assert Q[int(np.argmax(width))].max() == 255       # the widest subspace spans the range
+        assert Q.max() <= 255
+        err = np.abs(Q * g / 255.0 - (T - lo[:, None]))
+        assert (err <= g / 510.0 * (1 + 1e-5) + 1e-6 * T.max()).all()
+        for s in range(M):                                 # order within a subspace is kept
+            o = np.argsort(T[s], kind="stable")
+            assert (np.diff(Q[s][o]) >= 0).all()
+    assert not oracle.adc_table_q8(np.full((4, 256), 3.5, np.float32)).any()
+
+
 def test_adc_dist_summation_tree():
     # Reading of §4.4 (order of the segment sums): 8 strided partials, then
     # butterfly p_r += p_(r^4), p_r += p_(r^2), p_r += p_(r^1).  Values
@@ -319,6 +355,51 @@ def test_chain_graph_visit_order():
         assert r["ids"][0, 0] == 13 and r["dist"][0, 0] == 0.0
     r = ix.search(q, k=3, L=3, log2z=16)
     assert r["ids"][0].tolist() == [13, 12, 14]      # (distance, id) ties: 12 before 14
+
+
+def test_q8_chain_graph_visit_order():
+    # The chain graph of test_chain_graph_visit_order on the 8-bit table.
+    # With the lossless codebook and query 13 the FP32 entries are (13-c)^2,
+    # widest 242^2 = 58564, so the scale is 255/58564 and points 0, 1, 2
+    # (169, 144, 121) quantise to 1 while 3..20 (at most 100) quantise to 0.
+    # Worked by hand: L=1 stops after 0 (1 ties with 0 and loses on id);
+    # L=2 stops after 0, 1; L=3 expands 0..5: 3 enters at distance 0 and
+    # every later point ties at 0 and falls off behind smaller ids once 6
+    # arrives.  The re-rank then returns the nearest expanded node.
+    n = 21
+    X = np.arange(n, dtype=np.uint8)[:, None]
+    adj = np.full((n, 2), NONE, np.uint32)
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        adj[i, :len(nb)] = nb
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, 0, 1)
+    q = np.array([[13]], np.uint8)
+    Q = oracle.adc_table_q8(oracle.adc_table(q[0].astype(np.float32), 1, cb))
+    assert Q[0][:21].tolist() == [1, 1, 1] + [0] * 18
+    for L, trace, best in ((1, [0], 0), (2, [0, 1], 1), (3, [0, 1, 2, 3, 4, 5], 5)):
+        r = ix.search(q, k=1, L=L, log2z=16, trace_cap=64, q8=True)
+        it = int(r["iters"][0])
+        assert r["trace"][0][:it].tolist() == trace
+        assert r["ids"][0, 0] == best and r["dist"][0, 0] == float((13 - best) ** 2)
+
+
+def test_q8_mode_worklist_of_all_points_equals_bruteforce():
+    # With L >= n on a complete graph every point is expanded, so the re-rank
+    # returns the exact k-NN whatever the table's precision.
+    rng = np.random.default_rng(22)
+    n = 30
+    X = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+    cb = rng.normal(128, 40, size=256 * 16).astype(np.float32)
+    codes = rng.integers(0, 256, size=(n, 4)).astype(np.uint8)
+    ix = oracle.Index(X, cb, codes, complete_graph(n), 3, 4)
+    Q = rng.integers(0, 256, size=(6, 16)).astype(np.uint8)
+    r = ix.search(Q, k=5, L=n, log2z=18, q8=True)
+    for qi in range(len(Q)):
+        ids, dd = brute_ids(X, Q[qi], 5)
+        assert r["ids"][qi].tolist() == ids.tolist()
+        assert r["dist"][qi].tolist() == dd.astype(np.float32).tolist()
+        assert r["iters"][qi] == n
 
 
 def test_complete_graph_equals_bruteforce():
