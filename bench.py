@@ -257,7 +257,7 @@ def run_reference(args):
 # DRAM traffic per launch of the head form's kernel from one ncu capture of
 # the current kernel version (profiles/search_kernel_bf16_u8_n1M.md); set to
 # None whenever that kernel changes.
-NCU_TRAFFIC = {"bf16": 33514752 + 256}
+NCU_TRAFFIC = {}
 
 FORMS = {
     # name: (distance mode, placement flags, what it is)
@@ -265,6 +265,8 @@ FORMS = {
     "bf16": (1, 0, "reduced precision: BF16 PQ table summed in FP32, host graph and vectors"),
     "bf16_tc": (1, 0, "reduced precision with the BF16 tables of the whole batch built on the "
                       "tensor cores (tcgen05) first"),
+    "q8": (3, 0, "reduced precision: 8-bit PQ table (per-subspace offset, one scale per query) "
+                 "summed exactly in integers, host graph and vectors"),
     "in_memory": (0, 3, "In-memory variant (§5.1): FP32 PQ table, graph and vectors in HBM"),
     "exact": (2, 3, "Exact-distance variant (§5.2): exact distances, graph and vectors in HBM"),
 }
@@ -370,8 +372,8 @@ def main():
     # ---- the two forms of the paper's base method (host graph): time both,
     # report the faster at recall@10 >= 0.9 with the plain form beside it
     with ClockSampler(local) as clk:
-        res = {f: measure(f, args.steps) for f in ("fp32", "bf16", "bf16_tc")}
-    ok = [f for f in ("bf16_tc", "bf16", "fp32") if res[f]["recall"] >= TARGET_RECALL]
+        res = {f: measure(f, args.steps) for f in ("fp32", "bf16", "bf16_tc", "q8")}
+    ok = [f for f in ("q8", "bf16_tc", "bf16", "fp32") if res[f]["recall"] >= TARGET_RECALL]
     head = res[max(ok, key=lambda f: res[f]["value"])] if ok else res["fp32"]
     variants = {f: measure(f, max(5, args.steps // 5)) for f in ("in_memory", "exact")}
     place(0)
@@ -422,7 +424,7 @@ def main():
         "metric": "queries/s at recall@10=0.9", "value": head["value"], "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "bf16-table/f32" if mode == 1 else "f32", "data": "synthetic",
+        "vs_baseline": None, "dtype": {1: "bf16-table/f32", 3: "u8-table/int32"}.get(mode, "f32"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": head["form"], "form_what": head["what"],
                    "L": L, "recall@10": head["recall"], "k": K,
                    "bloom_log2": args.bloom_log2, "sweep": head["sweep"],

@@ -78,7 +78,12 @@ typedef struct bang_search_params {
      * in FP32 (1, the reduced-precision form: half the table's shared memory),
      * or exact distances in the loop without table or re-rank (2, the
      * paper's Exact-distance variant, §5.2; results are the first k entries
-     * of the final worklist). */
+     * of the final worklist), or from an 8-bit table summed exactly in
+     * integers (3; not in the paper, whose table is FP32: from the FP32
+     * table T of a query, lo_s = min_c T[s][c], g = the widest subspace's
+     * max - min, entry = min(255, rint((T - lo_s) * (255 / g))), all in FP32;
+     * a quarter of the FP32 table's shared memory; bit-exact with the
+     * reference order like mode 0). */
     uint32_t mode;
     /* bang_search_batched only: the persistent grid is grid_mult times the
      * CTAs that fit on the device at once (0 or 1: exactly that many). */
@@ -90,7 +95,8 @@ typedef struct bang_search_params {
     uint32_t table_source;
 } bang_search_params;
 
-typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2 } bang_mode;
+typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,
+               BANG_MODE_PQ_Q8 = 3 } bang_mode;
 
 /* Placement flags for bang_set_placement. */
 enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2 };

@@ -149,7 +149,7 @@ PHASES = ("table", "select", "filter", "distance", "next", "rerank", "merge", "m
           "merge_shift", "total")
 
 
-BANG_MODE_PQ_F32, BANG_MODE_PQ_BF16, BANG_MODE_EXACT = 0, 1, 2
+BANG_MODE_PQ_F32, BANG_MODE_PQ_BF16, BANG_MODE_EXACT, BANG_MODE_PQ_Q8 = 0, 1, 2, 3
 BANG_GRAPH_IN_HBM, BANG_VECTORS_IN_HBM = 1, 2
 
 

@@ -427,8 +427,8 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     if (persistent && (!k_arr || !L_arr)) return fail(BANG_EINVAL, "bang_search_batched: NULL k or L array");
     if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search: trace_cap is 0");
 
-    if (p.mode > 2) return fail(BANG_EINVAL, "bang_search: unknown mode %u", p.mode);
-    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, (int)p.mode);
+    if (p.mode > 3) return fail(BANG_EINVAL, "bang_search: unknown mode %u", p.mode);
+    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, ix->R, (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search: %u bytes of shared memory per query exceed 227 KB "
                     "(reduce L, k, M or bloom_log2)", lay.total);
@@ -559,6 +559,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     cudaError_t le;
     if (p.mode == 0) le = bang::launch_search_f32(a, ix->dtype, lay.total, st);
     else if (p.mode == 1) le = bang::launch_search_bf16(a, ix->dtype, lay.total, st);
+    else if (p.mode == 3) le = bang::launch_search_q8(a, ix->dtype, lay.total, st);
     else le = bang::launch_search_exact(a, ix->dtype, lay.total, st);
     if (le != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(le));
     for (int i = 1; i < 8; ++i) {
@@ -787,7 +788,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     const uint32_t log2z = p.bloom_log2 ? p.bloom_log2 : 16u;
     if (log2z < 10 || log2z > 20)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: bloom_log2=%u outside 10..20", log2z);
-    if (p.mode > 2) return fail(BANG_EINVAL, "bang_search_batched_noalloc: unknown mode %u", p.mode);
+    if (p.mode > 3) return fail(BANG_EINVAL, "bang_search_batched_noalloc: unknown mode %u", p.mode);
     if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search_batched_noalloc: trace_cap is 0");
     const void *ptrs[10] = {queries, k_per_q, L_per_q, out_ids, out_dist, p.out_iters, p.out_status,
                             p.out_ndist, p.trace, p.out_phase_cycles};
@@ -797,7 +798,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
             return fail(BANG_EINVAL, "bang_search_batched_noalloc: every buffer must be device memory "
                         "(host buffers would need staging allocations)");
     }
-    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, (int)p.mode);
+    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: %u bytes of shared memory per query "
                     "exceed 227 KB", lay.total);
@@ -860,6 +861,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.vecb_ok = (ix->d % 4 == 0) && (ba % 16 == 0) ? 1u : 0u;
     if (p.mode == 0) e = bang::launch_search_f32(a, ix->dtype, lay.total, st);
     else if (p.mode == 1) e = bang::launch_search_bf16(a, ix->dtype, lay.total, st);
+    else if (p.mode == 3) e = bang::launch_search_q8(a, ix->dtype, lay.total, st);
     else e = bang::launch_search_exact(a, ix->dtype, lay.total, st);
     if (e != cudaSuccess)
         return fail(BANG_ECUDA, "bang_search_batched_noalloc: search kernel launch failed: %s",

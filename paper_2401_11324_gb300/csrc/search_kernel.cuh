@@ -18,6 +18,7 @@
 //    dimensions in ascending j, from 0;
 //  - PQ distance: eight partial sums over subspaces s = r (mod 8), in
 //    ascending s, then p_r += p_(r^4), p_r += p_(r^2), p_r += p_(r^1);
+//    on the 8-bit table an exact integer sum;
 //  - exact distance: 32 partial sums, lane r owning the dimensions j with
 //    (j/4) mod 32 = r, each in ascending j (fmaf), then a butterfly over xor
 //    distances 16, 8, 4, 2, 1; integer data is summed exactly;
@@ -47,7 +48,10 @@ constexpr int kRegK = 32;         // k up to this keeps the re-rank top-k in reg
 //              half the table's shared memory, so more queries per SM)
 //  kModeExact: exact distances to the full vectors in the loop, no table and
 //              no re-rank (the paper's Exact-distance variant, §5.2)
-enum { kModeF32 = 0, kModeBF16 = 1, kModeExact = 2 };
+//  kModeQ8:    PQ distances from an 8-bit table (per-subspace offset, one
+//              scale per query) summed exactly in integers: a quarter of the
+//              FP32 table's shared memory; not in the paper
+enum { kModeF32 = 0, kModeBF16 = 1, kModeExact = 2, kModeQ8 = 3 };
 
 struct SearchArgs {
     const void *queries;      // device, nq*d elements
@@ -86,21 +90,23 @@ enum Phase { kPhTable = 0, kPhSelect, kPhFilter, kPhDistance, kPhNext, kPhRerank
 
 // Shared-memory carve-up, in bytes, shared by host (sizing) and device.
 struct SmemLayout {
-    uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_Ck, off_q, off_offs, total;
+    uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_Ck, off_q, off_offs, off_lo, total;
     __host__ __device__ static uint32_t up16(uint32_t x) { return (x + 15u) & ~15u; }
     __host__ __device__ SmemLayout(uint32_t M, uint32_t log2z, uint32_t L, uint32_t k, uint32_t d,
-                                   int mode)
+                                   uint32_t R, int mode)
     {
         uint32_t o = 0;
-        const uint32_t tsz = mode == kModeF32 ? 4u : (mode == kModeBF16 ? 2u : 0u);
+        const uint32_t tsz = mode == kModeF32 ? 4u : mode == kModeBF16 ? 2u : mode == kModeQ8 ? 1u : 0u;
+        const uint32_t rw = (R + 31u) & ~31u;          // neighbour slots: whole lanes' worth
         off_T = o;      o += up16(M * 256u * tsz);
         off_bloom = o;  o += up16(((1u << log2z) / 8u) < 4u ? 4u : (1u << log2z) / 8u);
         off_L = o;      o += up16(L * 8u);
-        off_Nk = o;     o += up16(kMaxR * 8u);
-        off_Nid = o;    o += up16(kMaxR * 4u);
+        off_Nk = o;     o += up16(rw * 8u);
+        off_Nid = o;    o += up16(rw * 4u);
         off_Ck = o;     o += up16(k > (uint32_t)kRegK && mode != kModeExact ? k * 8u : 0u);
-        off_q = o;      o += up16(d * 4u);
+        off_q = o;      o += up16(mode != kModeExact ? d * 4u : 0u);
         off_offs = o;   o += up16((M + 1u) * 4u);
+        off_lo = o;     o += up16(mode == kModeQ8 ? M * 4u : 0u);
         total = o;
     }
 };
@@ -170,6 +176,30 @@ template <int MODE> __device__ __forceinline__ float table_entry(const void *T, 
     return static_cast<const float *>(T)[i];
 }
 
+// PQ distance of one code row on the 8-bit table: the exact integer sum of
+// the selected entries (any order gives the same sum).
+__device__ __forceinline__ uint32_t adc_distance_q8(const uint8_t *__restrict__ T,
+                                                    const uint8_t *__restrict__ row, uint32_t M,
+                                                    uint32_t Mpad)
+{
+    uint32_t p[4] = {0u, 0u, 0u, 0u};
+    const uint4 *row16 = reinterpret_cast<const uint4 *>(row);
+    for (uint32_t c16 = 0; c16 < Mpad / 16u; ++c16) {
+        uint4 v = __ldg(row16 + c16);
+        uint32_t w[4] = {v.x, v.y, v.z, v.w};
+        const uint8_t *tc = T + c16 * 16u * 256u;
+        if (c16 * 16u + 16u <= M) {
+#pragma unroll
+            for (int b = 0; b < 16; ++b) p[b & 3] += tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)];
+        } else {
+#pragma unroll
+            for (int b = 0; b < 16; ++b)
+                if (c16 * 16u + b < M) p[b & 3] += tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)];
+        }
+    }
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
 // PQ distance of one code row (§4.4), in the fixed order described above.
 template <int MODE>
 __device__ __forceinline__ float adc_distance(const void *__restrict__ T,
@@ -209,6 +239,18 @@ __device__ __forceinline__ float adc_distance(const void *__restrict__ T,
 // This lane's share of a vector for the exact distance: dimensions
 // 128*t + 4*lane + i, i < 4, t < DCH.  Integer data is packed four bytes per
 // word (int8 biased by 0x80 so that byte differences are unsigned).
+// Ordering bits of a PQ distance: FP32 distances (all >= +0) through their
+// bit patterns, 8-bit-table sums as integers.
+template <int MODE>
+__device__ __forceinline__ uint32_t pq_dist_bits(const void *T, const uint8_t *row, uint32_t M,
+                                                 uint32_t Mpad)
+{
+    if constexpr (MODE == kModeQ8)
+        return adc_distance_q8(static_cast<const uint8_t *>(T), row, M, Mpad);
+    else
+        return __float_as_uint(adc_distance<MODE>(T, row, M, Mpad));
+}
+
 template <int DT, int DCH> struct VecShare {
     float f[DT == 2 ? 4 * DCH : 1];
     uint32_t w[DT == 2 ? 1 : DCH];
@@ -307,52 +349,104 @@ template <int MODE> __device__ __forceinline__ void store_entry(void *Ts, uint32
     else static_cast<float *>(Ts)[c] = v;
 }
 
+// FP32 table entries T[s][c] of one subspace for the centroids
+// c = lane + 32 t, t < 8 (§4.1), in the fixed order described above.
+__device__ __forceinline__ void subspace_entries(const SearchArgs &a, const float *qv,
+                                                 const uint32_t *offs, uint32_t s, int lane,
+                                                 float (&v)[8])
+{
+    const uint32_t o = offs[s], ds = offs[s + 1] - o;
+    const float *cb = a.codebook + 256u * o;
+    if (ds == 4 && (o & 3u) == 0) {
+        const float4 q4 = *reinterpret_cast<const float4 *>(qv + o);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = lane + kWarp * t;
+            const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cb) + c);
+            float acc = 0.0f, df;
+            df = __fsub_rn(q4.x, c4.x); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q4.y, c4.y); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q4.z, c4.z); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q4.w, c4.w); acc = __fmaf_rn(df, df, acc);
+            v[t] = acc;
+        }
+    } else if (ds == 2 && (o & 1u) == 0) {
+        const float2 q2 = *reinterpret_cast<const float2 *>(qv + o);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = lane + kWarp * t;
+            const float2 c2 = __ldg(reinterpret_cast<const float2 *>(cb) + c);
+            float acc = 0.0f, df;
+            df = __fsub_rn(q2.x, c2.x); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q2.y, c2.y); acc = __fmaf_rn(df, df, acc);
+            v[t] = acc;
+        }
+    } else {
+#pragma unroll 2
+        for (int t = 0; t < 8; ++t) {
+            const uint32_t c = lane + kWarp * t;
+            const float *cc = cb + c * ds;
+            float acc = 0.0f;
+            for (uint32_t j = 0; j < ds; ++j) {
+                float df = __fsub_rn(qv[o + j], __ldg(cc + j));
+                acc = __fmaf_rn(df, df, acc);
+            }
+            v[t] = acc;
+        }
+    }
+}
+
 // PQ distance table of one query into shared memory (§4.1); entries are
-// computed in FP32 and stored in the mode's precision.
+// computed in FP32 and stored in the mode's precision.  The 8-bit table takes
+// two passes: the first finds each subspace's smallest entry lo_s and the
+// widest subspace's range g, the second stores
+// min(255, rint((T[s][c] - lo_s) * (255 / g))), each operation rounded to
+// FP32 (every entry 0 when g is 0).  Entries are >= +0, so their bit
+// patterns order like their values.
 template <int MODE>
 __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv,
-                                            const uint32_t *offs, void *T, int lane)
+                                            const uint32_t *offs, void *T, float *lo, int lane)
 {
-    for (uint32_t s = 0; s < a.M; ++s) {
-        const uint32_t o = offs[s], ds = offs[s + 1] - o;
-        const float *cb = a.codebook + 256u * o;
-        unsigned char *Ts = static_cast<unsigned char *>(T) + s * 256u * (MODE == kModeBF16 ? 2u : 4u);
-        if (ds == 4 && (o & 3u) == 0) {
-            const float4 q4 = *reinterpret_cast<const float4 *>(qv + o);
+    float v[8];
+    if constexpr (MODE == kModeQ8) {
+        float g = 0.0f;
+        for (uint32_t s = 0; s < a.M; ++s) {
+            subspace_entries(a, qv, offs, s, lane, v);
+            uint32_t mn = __float_as_uint(v[0]), mx = mn;
+#pragma unroll
+            for (int t = 1; t < 8; ++t) {
+                const uint32_t b = __float_as_uint(v[t]);
+                mn = b < mn ? b : mn;
+                mx = b > mx ? b : mx;
+            }
+            const float fmn = __uint_as_float(__reduce_min_sync(0xFFFFFFFFu, mn));
+            const float fmx = __uint_as_float(__reduce_max_sync(0xFFFFFFFFu, mx));
+            if (lane == 0) lo[s] = fmn;
+            const float w = __fsub_rn(fmx, fmn);
+            g = w > g ? w : g;
+        }
+        __syncwarp();
+        const float inv = g > 0.0f ? __fdiv_rn(255.0f, g) : 0.0f;
+        for (uint32_t s = 0; s < a.M; ++s) {
+            subspace_entries(a, qv, offs, s, lane, v);
+            const float los = lo[s];
+            uint8_t *Ts = static_cast<uint8_t *>(T) + s * 256u;
 #pragma unroll
             for (int t = 0; t < 8; ++t) {
-                const uint32_t c = lane + kWarp * t;
-                const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cb) + c);
-                float acc = 0.0f, df;
-                df = __fsub_rn(q4.x, c4.x); acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(q4.y, c4.y); acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(q4.z, c4.z); acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(q4.w, c4.w); acc = __fmaf_rn(df, df, acc);
-                store_entry<MODE>(Ts, c, acc);
-            }
-        } else if (ds == 2 && (o & 1u) == 0) {
-            const float2 q2 = *reinterpret_cast<const float2 *>(qv + o);
-#pragma unroll
-            for (int t = 0; t < 8; ++t) {
-                const uint32_t c = lane + kWarp * t;
-                const float2 c2 = __ldg(reinterpret_cast<const float2 *>(cb) + c);
-                float acc = 0.0f, df;
-                df = __fsub_rn(q2.x, c2.x); acc = __fmaf_rn(df, df, acc);
-                df = __fsub_rn(q2.y, c2.y); acc = __fmaf_rn(df, df, acc);
-                store_entry<MODE>(Ts, c, acc);
-            }
-        } else {
-#pragma unroll 2
-            for (int t = 0; t < 8; ++t) {
-                const uint32_t c = lane + kWarp * t;
-                const float *cc = cb + c * ds;
-                float acc = 0.0f;
-                for (uint32_t j = 0; j < ds; ++j) {
-                    float df = __fsub_rn(qv[o + j], __ldg(cc + j));
-                    acc = __fmaf_rn(df, df, acc);
+                uint32_t qv8 = 0;
+                if (g > 0.0f) {
+                    qv8 = __float2uint_rn(__fmul_rn(__fsub_rn(v[t], los), inv));
+                    qv8 = qv8 < 255u ? qv8 : 255u;
                 }
-                store_entry<MODE>(Ts, c, acc);
+                Ts[lane + kWarp * t] = static_cast<uint8_t>(qv8);
             }
+        }
+    } else {
+        for (uint32_t s = 0; s < a.M; ++s) {
+            subspace_entries(a, qv, offs, s, lane, v);
+            unsigned char *Ts = static_cast<unsigned char *>(T) + s * 256u * (MODE == kModeBF16 ? 2u : 4u);
+#pragma unroll
+            for (int t = 0; t < 8; ++t) store_entry<MODE>(Ts, lane + kWarp * t, v[t]);
         }
     }
 }
@@ -383,7 +477,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     constexpr bool kPQ = MODE != kModeExact;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x;
-    const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d, MODE);
+    const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d, a.R, MODE);
     void *T = smem + lay.off_T;
     uint32_t *bloom = reinterpret_cast<uint32_t *>(smem + lay.off_bloom);
     uint64_t *Lk = reinterpret_cast<uint64_t *>(smem + lay.off_L);
@@ -392,6 +486,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     uint64_t *Ck = reinterpret_cast<uint64_t *>(smem + lay.off_Ck);
     float *qv = reinterpret_cast<float *>(smem + lay.off_q);
     uint32_t *offs = reinterpret_cast<uint32_t *>(smem + lay.off_offs);
+    float *lo8 = reinterpret_cast<float *>(smem + lay.off_lo);
 
     const uint32_t d = a.d, kstride = a.k;
     const uint32_t zmask = (1u << a.log2z) - 1u;
@@ -434,7 +529,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         const unsigned long long t_start = clk.t;
         // ---- query: FP32 copy in shared memory, this lane's share in registers
         const E *qp = static_cast<const E *>(a.queries) + static_cast<uint64_t>(q) * d;
-        for (uint32_t j = lane; j < d; j += kWarp) qv[j] = static_cast<float>(qp[j]);
+        if (kPQ)
+            for (uint32_t j = lane; j < d; j += kWarp) qv[j] = static_cast<float>(qp[j]);
         VecShare<DT, DCH> qs;
         load_share<DT, DCH>(qp, d, a.vec_ok != 0, lane, qs);
         for (uint32_t w = lane; w < nwords; w += kWarp) bloom[w] = 0u;
@@ -446,7 +542,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             uint4 *dst = reinterpret_cast<uint4 *>(T);
             for (uint32_t i = lane; i < a.M * 256u * 2u / 16u; i += kWarp) dst[i] = src[i];
         } else if (kPQ) {
-            build_table<MODE>(a, qv, offs, T, lane);
+            build_table<MODE>(a, qv, offs, T, lo8, lane);
         }
         __syncwarp();
         clk.mark(kPhTable);
@@ -462,8 +558,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         if (lane == 0) {
             const uint32_t s = a.medoid;
             if (kPQ)
-                dm_bits = __float_as_uint(adc_distance<MODE>(T, a.codes + static_cast<uint64_t>(s) * a.Mpad,
-                                                             a.M, a.Mpad));
+                dm_bits = pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(s) * a.Mpad, a.M, a.Mpad);
             Lk[0] = make_key(dm_bits, s);
             uint32_t p1 = fnv1a32_id(s) & zmask, p2 = fnv1a64_id_folded(s) & zmask;
             bloom[p1 >> 5] |= 1u << (p1 & 31u);
@@ -538,9 +633,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             if (kPQ) {
                 for (uint32_t j = lane; j < nn; j += kWarp) {
                     const uint32_t id = Nid[j];
-                    const float dj = adc_distance<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
-                                                        a.M, a.Mpad);
-                    Nk[j] = make_key(__float_as_uint(dj), id);
+                    Nk[j] = make_key(pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
+                                                        a.M, a.Mpad), id);
                 }
             } else {
                 for (uint32_t j0 = 0; j0 < nn; j0 += 4) {
@@ -638,7 +732,32 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             // read, then written, from the end of the list down to the first
             // insertion point.
             uint32_t npos = 0;               // new position of `best`, plus one
-            if (nn > 0) {
+            // New keys behind the last entry of a full worklist land at L or
+            // later, and so does every larger key: drop them first, so that
+            // only keys that enter the list are ranked (they are the
+            // smallest, so their ranks among the new keys do not change).
+            uint32_t nm = nn;
+            if (nn > 0 && nl == L) {
+                const uint64_t last = Lk[L - 1] >> 1;
+                uint64_t kk[RPL];
+                bool keep[RPL];
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    const uint32_t j = lane + kWarp * t;
+                    kk[t] = j < nn ? Nk[j] : 0ull;
+                    keep[t] = j < nn && (kk[t] >> 1) < last;
+                }
+                __syncwarp();
+                nm = 0;
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep[t]);
+                    if (keep[t]) Nk[nm + __popc(bal & ((1u << lane) - 1u))] = kk[t];
+                    nm += __popc(bal);
+                }
+                __syncwarp();
+            }
+            if (nm > 0) {
                 uint32_t *ins = Nid;         // ids are in the keys now; reuse
                 uint64_t xk[RPL];
                 uint32_t xpos[RPL];
@@ -648,7 +767,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     const uint32_t j = lane + kWarp * t;
                     xk[t] = 0;
                     xpos[t] = 0xFFFFFFFFu;
-                    if (j < nn) {
+                    if (j < nm) {
                         const uint64_t x = Nk[j];
                         uint32_t lo = 0, hi = nl;
                         while (lo < hi) {
@@ -657,9 +776,9 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                             else hi = mid;
                         }
                         uint32_t rn = 0, tt = 0;
-                        for (; tt + 4 <= nn; tt += 4)
+                        for (; tt + 4 <= nm; tt += 4)
                             rn += (Nk[tt] < x) + (Nk[tt + 1] < x) + (Nk[tt + 2] < x) + (Nk[tt + 3] < x);
-                        for (; tt < nn; ++tt) rn += Nk[tt] < x;
+                        for (; tt < nm; ++tt) rn += Nk[tt] < x;
                         ins[rn] = lo;
                         xk[t] = x;
                         xpos[t] = lo + rn;
@@ -681,7 +800,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                         pos[g] = 0xFFFFFFFFu;
                         if (c >= cmin && i < nl && i >= rmin) {
                             key[g] = Lk[i];
-                            uint32_t lo = 0, hi = nn;    // #{new: insertion point <= i}
+                            uint32_t lo = 0, hi = nm;    // #{new: insertion point <= i}
                             while (lo < hi) {
                                 const uint32_t mid = (lo + hi) >> 1;
                                 if (ins[mid] <= i) lo = mid + 1;
@@ -706,7 +825,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     }
                 }
                 __syncwarp();
-                nl = nl + nn < L ? nl + nn : L;
+                nl = nl + nm < L ? nl + nm : L;
                 npos = __reduce_max_sync(0xFFFFFFFFu, npos);
                 if (npos == 0 && lnext >= 0 && best == lkey)      // in the untouched prefix
                     npos = static_cast<uint32_t>(lnext) + 1;
@@ -814,5 +933,6 @@ template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size
 cudaError_t launch_search_f32(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 cudaError_t launch_search_bf16(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 cudaError_t launch_search_exact(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
+cudaError_t launch_search_q8(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 
 }  // namespace bang

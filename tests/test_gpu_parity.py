@@ -47,10 +47,11 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     return out
 
 
-def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None, exact=False):
+def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None, exact=False, q8=False):
     M = M or w["M"]
     ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
-    return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap, exact=exact)
+    return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap, exact=exact,
+                     q8=q8)
 
 
 def assert_parity(g, o, trace_cap=0, exact_dist=True):
@@ -247,6 +248,30 @@ def test_bf16_table_recall_within_tolerance(u8small):
         assert (g["dist"] == ex.astype(np.float32)).all()
 
 
+# ---------------------------------------------------------------- 8-bit table form
+
+@pytest.mark.parametrize("placement", [0, 3])
+def test_q8_mode_bit_exact(u8small, cfg1, placement):
+    # the 8-bit table is computed from the FP32 table in FP32 and summed in
+    # integers, so the whole search is bit-exact with the oracle's mode
+    for w, Q, L in ((u8small, u8small["queries"], 32), (u8small, u8small["queries"][:150], 128),
+                    (cfg1, cfg1["queries"], 64)):
+        g = gpu_search(w, Q, 10, L, trace_cap=600, mode=bang.BANG_MODE_PQ_Q8, placement=placement)
+        o = oracle_search(w, Q, 10, L, trace_cap=600, q8=True)
+        assert_parity(g, o, trace_cap=600)
+
+
+def test_q8_mode_uneven_subspaces_and_wide_rows():
+    for w, L in ((cases.clustered(n=8_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40,
+                                  centre="uniform100"), 40),
+                 (cases.clustered(n=6_000, nq=50, ncomp=4, dtype="f32", d=96, M=48, R=68,
+                                  centre="uniform255"), 64)):
+        Q = w["queries"]
+        for k, LL, log2z in ((10, L, 16), (1, 1, 12), (40, 2 * L, 18)):
+            g = gpu_search(w, Q, k, LL, log2z, trace_cap=300, mode=bang.BANG_MODE_PQ_Q8)
+            assert_parity(g, oracle_search(w, Q, k, LL, log2z, trace_cap=300, q8=True), trace_cap=300)
+
+
 # ---------------------------------------------------------------- batched form
 
 def _mixed_kl(nq, seed):
@@ -256,7 +281,7 @@ def _mixed_kl(nq, seed):
     return k, L
 
 
-def _oracle_mixed(w, Q, k, L, mode_exact=False):
+def _oracle_mixed(w, Q, k, L, mode_exact=False, q8=False):
     kmax = int(k.max())
     ids = np.full((len(Q), kmax), bang.BANG_NONE, np.uint32)
     dist = np.full((len(Q), kmax), np.inf, np.float32)
@@ -264,7 +289,7 @@ def _oracle_mixed(w, Q, k, L, mode_exact=False):
     for kk in np.unique(k):
         for LL in np.unique(L[k == kk]):
             sel = np.where((k == kk) & (L == LL))[0]
-            o = oracle_search(w, Q[sel], int(kk), int(LL), exact=mode_exact)
+            o = oracle_search(w, Q[sel], int(kk), int(LL), exact=mode_exact, q8=q8)
             ids[sel, :kk] = o["ids"]
             dist[sel, :kk] = o["dist"]
             iters[sel] = o["iters"]
@@ -288,6 +313,24 @@ def test_batched_uneven_k_and_L_host_arrays(u8small):
         fin = np.isfinite(dist_o)
         assert (np.isfinite(dist) == fin).all() and (dist[fin] == dist_o[fin]).all()
     ix.close()
+
+
+def test_batched_q8_uneven_k_and_L(u8small):
+    Q = u8small["queries"][:160]
+    k, L = _mixed_kl(len(Q), 9)
+    ids_o, dist_o, iters_o = _oracle_mixed(u8small, Q, k, L, q8=True)
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    kmax, Lmax = int(k.max()), int(L.max())
+    ids = np.zeros((len(Q), kmax), np.uint32)
+    dist = np.zeros((len(Q), kmax), np.float32)
+    iters = np.zeros(len(Q), np.uint32)
+    ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist,
+                      bang.make_params(out_iters=iters, mode=bang.BANG_MODE_PQ_Q8))
+    ix.close()
+    assert (ids == ids_o).all() and (iters == iters_o).all()
+    fin = np.isfinite(dist_o)
+    assert (np.isfinite(dist) == fin).all() and (dist[fin] == dist_o[fin]).all()
 
 
 def test_batched_cuda_graph_replay(u8small):
