@@ -127,15 +127,22 @@ int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
  *           a row and differ from the row's own id.
  *   R       row width, 1..128.
  *   medoid  entry point s of the search (§6.3), < n.
- * Not copied: the memory must stay valid and unchanged until bang_destroy
- * or the next bang_register_graph.  The library page-locks it with
- * cudaHostRegister unless it is already page-locked, and the GPU reads it
- * in place.  Invalid ids return BANG_EINVAL (checked here, not at search). */
+ * Not copied when `adj` starts on a 128-byte boundary: the memory must then
+ * stay valid and unchanged until bang_destroy or the next
+ * bang_register_graph; the library page-locks it with cudaHostRegister
+ * unless it is already page-locked, and the GPU reads it in place.  A
+ * pointer off that boundary (numpy places large arrays 16 bytes past a page)
+ * is copied once into aligned page-locked memory owned by the index, since a
+ * misaligned 256-byte row costs 9 32-byte sectors on the host link instead
+ * of 8; the caller may then free its copy.  BANG_ENOMEM if that copy cannot
+ * be allocated.  Invalid ids return BANG_EINVAL (checked here, not at
+ * search). */
 int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_t medoid);
 
 /* Register the full-precision vectors used by the re-rank (§4.8), host
- * memory, n*d elements of `dtype`, row-major.  Same ownership rule as the
- * graph.  Queries passed to bang_search have the same element type. */
+ * memory, n*d elements of `dtype`, row-major.  Same ownership and alignment
+ * rule as the graph.  Queries passed to bang_search have the same element
+ * type. */
 int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype);
 
 /* Search a batch of nq queries (Alg. 2; one query per warp): PQ distance
@@ -225,6 +232,53 @@ int bang_pq_tables(bang_index *ix, const void *queries, uint32_t nq, void *out, 
  * -1 before bang_register_vectors. */
 int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M, uint32_t *R,
                     int32_t *dtype);
+
+/* ---- Autotuner (not in the paper).  Picks, for this GPU and index, the
+ * settings that change speed but not the method: the PQ table's precision
+ * (bang_mode; bit m of `modes` admits mode m), whether mode 1's tables come
+ * from the tensor cores (table_source), the Bloom filter size 2^bloom_log2
+ * (the paper's z, §4.3) and, for the batched form, the persistent grid
+ * multiple.  Every candidate searches the given queries on `stream`; its
+ * accuracy is recall@k against `truth` (host, nq*k ids; 0xFFFFFFFF entries
+ * are skipped) or, when truth is NULL, against an FP32 search with worklist
+ * 2L (at most 1024) and a 2^18-bit filter.  Speed is the mean of `reps`
+ * CUDA-event-timed launches after one warm-up.
+ *   target_recall 0: L is fixed (k <= L <= 1024); a candidate qualifies when
+ *                 its recall is at least the FP32 form's (mode 0, 2^16 bits)
+ *                 minus recall_tolerance (default 0.005).
+ *   target_recall in (0, 1]: every candidate takes the smallest worklist of
+ *                 {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512,
+ *                 768, 1024} (at least k, at most L unless L is 0) whose
+ *                 recall reaches the target.
+ * The fastest qualifying candidate is returned in *out with its L, time and
+ * recall, beside the FP32 form's (ref_ms, ref_recall at its own L).  With
+ * cache_path set, a decision is looked up first (JSON lines keyed by GPU
+ * name and SM count, index shape, placement, nq, k, L and the options) and
+ * appended after tuning.  Defaults (0): modes 0, 1 and 3; Bloom 2^13..2^17;
+ * reps 3.  Allocates its own scratch; blocks until done.  BANG_EINVAL when
+ * no candidate qualifies. */
+typedef struct bang_autotune_opts {
+    uint32_t modes;              /* bit mask over bang_mode; 0 = modes 0, 1, 3 */
+    uint32_t bloom_min, bloom_max;   /* log2 filter sizes tried; 0 = 13, 17 */
+    uint32_t try_tensor_tables;  /* also try table_source 1 with mode 1 */
+    uint32_t batched;            /* tune bang_search_batched (grid_mult 1, 2, 4) */
+    uint32_t reps;               /* timed launches per candidate; 0 = 3 */
+    float target_recall;         /* 0: fixed L; else the recall to reach */
+    float recall_tolerance;      /* fixed L: allowed recall loss; 0 = 0.005 */
+    const char *cache_path;      /* JSON-lines decision cache, or NULL */
+} bang_autotune_opts;
+
+typedef struct bang_autotune_result {
+    uint32_t mode, bloom_log2, table_source, grid_mult, L;
+    float ms, recall;            /* chosen settings: ms per batch, recall@k */
+    float ref_ms, ref_recall;    /* FP32 form, 2^16-bit filter */
+    uint32_t candidates;         /* candidates evaluated */
+    uint32_t from_cache;         /* 1 when read from cache_path */
+} bang_autotune_result;
+
+int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,
+                  const uint32_t *truth, const bang_autotune_opts *opts, bang_autotune_result *out,
+                  void *stream);
 
 /* ---- Serving: continuous batching (north of the paper's batch-at-a-time
  * evaluation, §6.2 runs one batch of 10,000 queries).  A server owns

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdarg>
 #include <map>
 #include <numeric>
@@ -48,18 +49,50 @@ int fail(int code, const char *fmt, ...)
 
 // A host range the GPU reads in place.  Registered by the library unless the
 // caller's memory is already page-locked (or device-accessible already).
+// Host ranges that do not start on a 128-byte boundary are replaced by an
+// aligned page-locked copy owned by the index: rows of 32-byte multiples then
+// start on 32-byte sector boundaries, and a 256-byte neighbour row crosses
+// the host link as 8 sectors instead of 9.
+constexpr uintptr_t kHostAlign = 128;
+
 struct HostView {
     const void *host = nullptr;
     const void *dev = nullptr;
     bool registered_here = false;
+    bool copied = false;             // `host` is the library's aligned copy
 
     void release()
     {
-        if (registered_here && host) cudaHostUnregister(const_cast<void *>(host));
+        if (copied && host) cudaFreeHost(const_cast<void *>(host));
+        else if (registered_here && host) cudaHostUnregister(const_cast<void *>(host));
         host = dev = nullptr;
-        registered_here = false;
+        registered_here = copied = false;
     }
 };
+
+// memcpy split over the host's cores (the copies run once, at registration).
+void parallel_copy(void *dst, const void *src, size_t bytes)
+{
+    const size_t chunk = size_t(64) << 20;
+    unsigned nt = std::thread::hardware_concurrency();
+    nt = nt ? nt : 1u;
+    const size_t parts = (bytes + chunk - 1) / chunk;
+    if (parts < 2 || nt < 2) {
+        std::memcpy(dst, src, bytes);
+        return;
+    }
+    nt = static_cast<unsigned>(parts < nt ? parts : nt);
+    std::atomic<size_t> next{0};
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([&] {
+            for (size_t i; (i = next.fetch_add(1)) < parts;) {
+                const size_t o = i * chunk, m = bytes - o < chunk ? bytes - o : chunk;
+                std::memcpy(static_cast<char *>(dst) + o, static_cast<const char *>(src) + o, m);
+            }
+        });
+    for (auto &t : th) t.join();
+}
 
 int map_host(const void *p, size_t bytes, HostView &out)
 {
@@ -70,9 +103,30 @@ int map_host(const void *p, size_t bytes, HostView &out)
         at.type = cudaMemoryTypeUnregistered;
     }
     out.host = p;
-    out.registered_here = false;
+    out.registered_here = out.copied = false;
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
         out.dev = p;
+        return BANG_OK;
+    }
+    if (reinterpret_cast<uintptr_t>(p) % kHostAlign != 0) {
+        void *c = nullptr;
+        e = cudaHostAlloc(&c, bytes, cudaHostAllocMapped);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(e == cudaErrorMemoryAllocation ? BANG_ENOMEM : BANG_ECUDA,
+                        "aligned page-locked copy of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+        }
+        parallel_copy(c, p, bytes);
+        void *dp = nullptr;
+        e = cudaHostGetDevicePointer(&dp, c, 0);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(c);
+            return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+        }
+        out.host = c;
+        out.dev = dp;
+        out.copied = true;
         return BANG_OK;
     }
     if (at.type == cudaMemoryTypeUnregistered) {
@@ -166,6 +220,11 @@ struct bang_index {
     bool tc_ok = false;
     std::map<cudaStream_t, DevBuf> tables;
 };
+
+namespace bang {
+int index_device(const bang_index *ix) { return ix->device; }
+uint32_t index_placement(const bang_index *ix) { return ix->placement; }
+}  // namespace bang
 
 namespace {
 

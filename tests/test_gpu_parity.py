@@ -215,6 +215,27 @@ def test_in_memory_placement_matches_host_placement(u8small):
             assert (g[f] == ref[f]).all()
 
 
+def _placed(a, offset):
+    """Copy of `a` starting `offset` bytes past a 4096-byte boundary."""
+    buf = np.empty(a.nbytes + 8192, np.uint8)
+    start = (-buf.ctypes.data) % 4096 + offset
+    v = buf[start:start + a.nbytes].view(a.dtype).reshape(a.shape)
+    v[...] = a
+    return v
+
+
+def test_host_arrays_aligned_in_place_or_copied(u8small):
+    # 128-byte-aligned graph and vectors are read in place; others are copied
+    # once into aligned page-locked memory; the results are the same
+    Q = u8small["queries"][:80]
+    ref = gpu_search(u8small, Q, 10, 64, trace_cap=300)
+    for off in (0, 16, 64, 128):
+        w = dict(u8small, adj=_placed(u8small["adj"], off), base=_placed(u8small["base"], off))
+        g = gpu_search(w, Q, 10, 64, trace_cap=300)
+        for f in ("ids", "dist", "iters", "ndist", "trace"):
+            assert (g[f] == ref[f]).all()
+
+
 @pytest.mark.parametrize("placement", [0, 3])
 def test_exact_mode_bit_exact(u8small, cfg1, placement):
     # §5.2: exact distances in the loop, no table, no re-rank
