@@ -7,6 +7,13 @@ k = 10).  The worklist size L is the smallest of the sweep
 {16, 24, 32, 48, 64, 96, 128, 160, 192, 256} whose mean recall@10 reaches 0.9
 (ground truth: exact k-NN); a step is one search of the whole batch at that L.
 
+Forms timed: the plain method (FP32 table), the reduced-precision tables
+(BF16 per warp or on the tensor cores, 8-bit), and the settings bang_autotune
+picks for recall@10 >= 0.9 (table precision and source, Bloom filter size,
+L); the fastest form reaching the target is the headline.  The In-memory and
+Exact-distance variants (§5.1, §5.2) are timed beside them.  With `--L` the
+sweep and the autotuner are skipped.
+
 Timed: `--steps` searches of the device-resident batch, each bracketed by CUDA
 events on the launching stream, an L2 flush (a 512 MB write) between them.
 `e2e`: the same search through the C ABI with pinned host queries and
@@ -254,10 +261,12 @@ def run_reference(args):
     return 0
 
 
-# DRAM traffic per launch of the head form's kernel from one ncu capture of
-# the current kernel version (profiles/search_kernel_bf16_u8_n1M.md); set to
-# None whenever that kernel changes.
-NCU_TRAFFIC = {}
+# Traffic per launch of the head kernel from one ncu capture of the current
+# kernel version at the default workload, keyed by (mode, bloom_log2, L):
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and host-memory
+# bytes (32-byte sysmem read sectors).  Cleared whenever the kernel changes.
+NCU_TRAFFIC = {(3, 15, 160): 33478400 + 0}
+NCU_HOST_TRAFFIC = {(3, 15, 160): 24429028 * 32}
 
 FORMS = {
     # name: (distance mode, placement flags, what it is)
@@ -310,19 +319,19 @@ def main():
             ix.set_placement(flags)
             placement[0] = flags
 
-    def search(L, mode, with_stats=False, phase=None, tsrc=0):
-        p = bang.make_params(bloom_log2=args.bloom_log2, mode=mode, table_source=tsrc,
+    def search(L, mode, with_stats=False, phase=None, tsrc=0, lz=None):
+        p = bang.make_params(bloom_log2=lz or args.bloom_log2, mode=mode, table_source=tsrc,
                              out_iters=iters if with_stats else None,
                              out_ndist=ndist if with_stats else None, out_phase_cycles=phase)
         ix.search(q_dev, K, L, ids, dist_out, p, stream=sptr)
 
-    def operating_point(mode, tsrc=0):
+    def operating_point(mode, tsrc=0, lz=None):
         """Smallest L of the sweep with recall@10 >= 0.9 (or --L)."""
         sweep = []
         if args.L is not None:
             return args.L, sweep
         for Lc in L_SWEEP:
-            search(Lc, mode, tsrc=tsrc)
+            search(Lc, mode, tsrc=tsrc, lz=lz)
             stream.synchronize()
             rc = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
             sweep.append({"L": Lc, "recall@10": round(rc, 4)})
@@ -330,9 +339,9 @@ def main():
                 return Lc, sweep
         return L_SWEEP[-1], sweep
 
-    def timed(L, mode, steps, tsrc=0):
+    def timed(L, mode, steps, tsrc=0, lz=None):
         for _ in range(args.warmup):
-            search(L, mode, tsrc=tsrc)
+            search(L, mode, tsrc=tsrc, lz=lz)
         stream.synchronize()
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
@@ -343,7 +352,7 @@ def main():
             with torch.cuda.stream(stream):
                 flush.fill_(s & 0xFF)
                 starts[s].record(stream)
-            search(L, mode, tsrc=tsrc)
+            search(L, mode, tsrc=tsrc, lz=lz)
             ends[s].record(stream)
         stream.synchronize()
         t_wall = time.perf_counter() - t_wall
@@ -353,18 +362,30 @@ def main():
         _, total_ms = job_throughput(nq, steps, sum(step_ms), world, dist, dev)
         return total_ms, step_ms, t_wall
 
-    def measure(name, steps):
-        mode, flags, what = FORMS[name]
-        tsrc = 1 if name.endswith("_tc") else 0
-        place(flags)
-        L, sweep = operating_point(mode, tsrc)
-        search(L, mode, with_stats=True, tsrc=tsrc)
+    def measure(name, steps, tune=None):
+        if tune is None:
+            mode, flags, what = FORMS[name]
+            tsrc = 1 if name.endswith("_tc") else 0
+            lz = args.bloom_log2
+            place(flags)
+            L, sweep = operating_point(mode, tsrc)
+        else:                       # settings chosen by bang_autotune
+            mode, tsrc, lz, L, flags, sweep = (tune["mode"], tune["table_source"],
+                                               tune["bloom_log2"], tune["L"],
+                                               tune.get("placement", 0), [])
+            what = ("autotuned (bang_autotune): %s table%s, Bloom filter 2^%d bits, smallest L "
+                    "reaching recall@10 0.9" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
+                                                " from the tensor cores" if tsrc else "", lz))
+            if flags:
+                what = "In-memory variant (§5.1), graph and vectors in HBM, with the " + what
+            place(flags)
+        search(L, mode, with_stats=True, tsrc=tsrc, lz=lz)
         stream.synchronize()
         rec = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
         it = iters.cpu().numpy().astype(np.int64)
         nd = ndist.cpu().numpy().astype(np.int64)
-        total_ms, step_ms, t_wall = timed(L, mode, steps, tsrc)
-        return dict(form=name, what=what, mode=mode, placement=flags, L=L, tsrc=tsrc,
+        total_ms, step_ms, t_wall = timed(L, mode, steps, tsrc, lz)
+        return dict(form=name, what=what, mode=mode, placement=flags, L=L, tsrc=tsrc, lz=lz,
                     recall=round(rec, 4), sweep=sweep, iters=it, ndist=nd,
                     value=nq * world * steps / (total_ms / 1e3), ms_per_step=total_ms / steps,
                     launch_s=statistics.mean(step_ms) / 1e3, t_wall=t_wall)
@@ -373,17 +394,29 @@ def main():
     # report the faster at recall@10 >= 0.9 with the plain form beside it
     with ClockSampler(local) as clk:
         res = {f: measure(f, args.steps) for f in ("fp32", "bf16", "bf16_tc", "q8")}
-    ok = [f for f in ("q8", "bf16_tc", "bf16", "fp32") if res[f]["recall"] >= TARGET_RECALL]
+        tune = None
+        if args.L is None:
+            place(0)
+            t0 = time.perf_counter()
+            tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
+                               target_recall=TARGET_RECALL, stream=sptr)
+            tune["seconds"] = round(time.perf_counter() - t0, 2)
+            res["autotuned"] = measure("autotuned", args.steps, tune)
+    ok = [f for f in ("autotuned", "q8", "bf16_tc", "bf16", "fp32")
+          if f in res and res[f]["recall"] >= TARGET_RECALL]
     head = res[max(ok, key=lambda f: res[f]["value"])] if ok else res["fp32"]
     variants = {f: measure(f, max(5, args.steps // 5)) for f in ("in_memory", "exact")}
+    if tune is not None:
+        variants["in_memory_autotuned"] = measure("in_memory_autotuned", max(5, args.steps // 5),
+                                                  dict(tune, placement=3))
     place(0)
-    L, mode, tsrc = head["L"], head["mode"], head["tsrc"]
+    L, mode, tsrc, lz = head["L"], head["mode"], head["tsrc"], head["lz"]
     it, nd = head["iters"], head["ndist"]
 
     # ---- per-phase SM cycles of the fused kernel (one untimed launch): the
     # counterpart of the paper's per-kernel share of GPU time
     phase = torch.zeros((nq, len(bang.PHASES)), dtype=torch.int64, device=dev)
-    search(L, mode, phase=phase, tsrc=tsrc)
+    search(L, mode, phase=phase, tsrc=tsrc, lz=lz)
     stream.synchronize()
     ph = phase.cpu().numpy().astype(np.float64).sum(0)
     phases = {name: round(float(ph[i] / ph[-1]), 4) for i, name in enumerate(bang.PHASES[:-1])}
@@ -398,7 +431,7 @@ def main():
     q_host = torch.from_numpy(w["queries"]).pin_memory()
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-    hp = bang.make_params(bloom_log2=args.bloom_log2, mode=mode, table_source=tsrc)
+    hp = bang.make_params(bloom_log2=lz, mode=mode, table_source=tsrc)
     for _ in range(2):
         ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))
@@ -406,7 +439,7 @@ def main():
     for _ in range(e2e_steps):
         ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
-    search(L, mode, tsrc=tsrc)
+    search(L, mode, tsrc=tsrc, lz=lz)
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
 
@@ -427,7 +460,7 @@ def main():
         "vs_baseline": None, "dtype": {1: "bf16-table/f32", 3: "u8-table/int32"}.get(mode, "f32"), "data": "synthetic",
         "config": {"workload": WORKLOAD, "form": head["form"], "form_what": head["what"],
                    "L": L, "recall@10": head["recall"], "k": K,
-                   "bloom_log2": args.bloom_log2, "sweep": head["sweep"],
+                   "bloom_log2": lz, "sweep": head["sweep"], "autotune": tune,
                    "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
                    "phase_share": phases,
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
@@ -437,12 +470,13 @@ def main():
         "forms": {f: brief(r) for f, r in list(res.items()) + list(variants.items())},
         "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": hbm_gbs / hbm_peak,
-                     "traffic": NCU_TRAFFIC.get(head["form"]) if args.n is None else None,
+                     "traffic": NCU_TRAFFIC.get((mode, lz, L)) if args.n is None else None,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "algorithmic_bytes_per_launch": hbm_bytes},
-        "host_link": {"achieved_gbs": host_bytes / launch_s / 1e9,
-                      "peak_gbs": link["gather_gbs"],
+        "host_link": {"bound": "host_link", "achieved": host_bytes / launch_s / 1e9,
+                      "peak": link["gather_gbs"], "unit": "GB/s",
                       "frac": host_bytes / launch_s / 1e9 / link["gather_gbs"],
+                      "traffic": NCU_HOST_TRAFFIC.get((mode, lz, L)) if args.n is None else None,
                       "peak_source": "measured in this run: random %d-byte row gathers in place "
                                      "from mapped host memory" % link["gather_row_bytes"],
                       "copy_engine_gbs": link["h2d_copy_gbs"],
@@ -457,7 +491,7 @@ def main():
         "wall_s_timed_region": sum(r["t_wall"] for r in res.values()),
     }
     if not args.no_serving:
-        line["serving"] = serving(bang, ix, w, L, mode, head["value"], args.bloom_log2)
+        line["serving"] = serving(bang, ix, w, L, mode, head["value"], lz)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, res["fp32"]["L"], min(args.cpu_sample, nq),
                                             args.bloom_log2)
