@@ -56,6 +56,22 @@ class bang_server_config(ctypes.Structure):
                 ("mode", ctypes.c_uint32), ("bloom_log2", ctypes.c_uint32)]
 
 
+class bang_autotune_opts(ctypes.Structure):
+    _fields_ = [("modes", ctypes.c_uint32), ("bloom_min", ctypes.c_uint32),
+                ("bloom_max", ctypes.c_uint32), ("try_tensor_tables", ctypes.c_uint32),
+                ("batched", ctypes.c_uint32), ("reps", ctypes.c_uint32),
+                ("target_recall", ctypes.c_float), ("recall_tolerance", ctypes.c_float),
+                ("cache_path", ctypes.c_char_p)]
+
+
+class bang_autotune_result(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_uint32), ("bloom_log2", ctypes.c_uint32),
+                ("table_source", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32),
+                ("L", ctypes.c_uint32), ("ms", ctypes.c_float), ("recall", ctypes.c_float),
+                ("ref_ms", ctypes.c_float), ("ref_recall", ctypes.c_float),
+                ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_uint32)]
+
+
 def library_path():
     return _build.LIB
 
@@ -87,13 +103,15 @@ def _load():
     L.bang_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, vp, vp,
                                    ctypes.POINTER(ctypes.c_double)]
     L.bang_server_stop.argtypes = [vp]
+    L.bang_autotune.argtypes = [vp, vp, u32, u32, u32, vp, ctypes.POINTER(bang_autotune_opts),
+                                ctypes.POINTER(bang_autotune_result), vp]
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
     L.bang_probe_host_link.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
               "bang_search_batched_noalloc", "bang_index_info", "bang_server_start", "bang_pq_tables",
-              "bang_server_submit", "bang_server_wait", "bang_server_stop"):
+              "bang_server_submit", "bang_server_wait", "bang_server_stop", "bang_autotune"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -192,6 +210,21 @@ def bang_pq_tables(ix, queries, nq, out, out_bf16=0, stream=None):
     return _check(lib().bang_pq_tables(ix, _ptr(queries), nq, _ptr(out), out_bf16, s))
 
 
+def bang_autotune(ix, queries, nq, k, L, truth=None, modes=0, bloom_min=0, bloom_max=0,
+                  try_tensor_tables=1, batched=0, reps=0, target_recall=0.0, recall_tolerance=0.0,
+                  cache_path=None, stream=None):
+    """Returns the chosen settings as a dict (fields of bang_autotune_result)."""
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    o = bang_autotune_opts(modes, bloom_min, bloom_max, try_tensor_tables, batched, reps,
+                           target_recall, recall_tolerance,
+                           cache_path.encode() if cache_path else None)
+    t = None if truth is None else np.ascontiguousarray(truth, np.uint32)
+    r = bang_autotune_result()
+    _check(lib().bang_autotune(ix, _ptr(queries), nq, k, L, _ptr(t), ctypes.byref(o),
+                               ctypes.byref(r), s))
+    return {f: getattr(r, f) for f, _ in bang_autotune_result._fields_}
+
+
 def bang_set_placement(ix, flags):
     return _check(lib().bang_set_placement(ix, flags))
 
@@ -230,6 +263,11 @@ class Index:
 
     def set_placement(self, flags):
         return bang_set_placement(self.h, flags)
+
+    def autotune(self, queries, k, L, truth=None, stream=None, **opts):
+        """bang_autotune over these queries; returns the chosen settings."""
+        return bang_autotune(self.h, queries, queries.shape[0], k, L, truth=truth, stream=stream,
+                             **opts)
 
     def search(self, queries, k, L, out_ids, out_dist, params=None, stream=None):
         nq = queries.shape[0]
