@@ -4,12 +4,14 @@ Workload: the mid-scale plain-method configuration (n = 1,000,000 uint8
 points, d = 128, 256-component mixture, 10,000 queries, PQ M = 32 on the
 device, clustered graph R = 64 and full vectors in page-locked host memory,
 k = 10).  The worklist size L is the smallest of the sweep
-{16, 24, 32, 48, 64, 96, 128, 160, 192, 256} whose mean recall@10 reaches 0.9
-(ground truth: exact k-NN); a step is one search of the whole batch at that L.
+{16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024} (values
+>= k) whose mean recall@k reaches 0.9 (ground truth: exact k-NN); a step is one
+search of the whole batch at that L.  `--k 100` measures 100-recall@100 and
+`--M` another PQ code size (the paper's second workload and compression study).
 
 Forms timed: the plain method (FP32 table), the reduced-precision tables
 (BF16 per warp or on the tensor cores, 8-bit), and the settings bang_autotune
-picks for recall@10 >= 0.9 (table precision and source, Bloom filter size,
+picks for recall@k >= 0.9 (table precision and source, Bloom filter size,
 L); the fastest form reaching the target is the headline.  The In-memory and
 Exact-distance variants (§5.1, §5.2) are timed beside them.  With `--L` the
 sweep and the autotuner are skipped.
@@ -37,10 +39,13 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256)
+L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024)
 TARGET_RECALL = 0.9
-K = 10
-WORKLOAD = "mid-scale plain method: n=1M u8 d=128, 10k queries, PQ M=32, R=64, k=10"
+K = 10                      # k of the search and of recall@k (--k)
+def workload_name(args):
+    n = args.n or 1_000_000
+    return "mid-scale plain method: n=%s u8 d=128, %d queries, PQ M=%d, R=64, k=%d" % (
+        "1M" if n == 1_000_000 else str(n), args.nq or 10_000, args.M, K)
 
 
 def parse():
@@ -57,7 +62,20 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=2000)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
-    return ap.parse_args()
+    ap.add_argument("--k", type=int, default=10, help="k of the search and of k-recall@k")
+    ap.add_argument("--M", type=int, default=32, help="PQ subspaces (bytes per code)")
+    args = ap.parse_args()
+    global K
+    K = args.k
+    return args
+
+
+def metric_name():
+    return "queries/s at recall@%d=0.9" % K
+
+
+def sweep_values():
+    return [L for L in L_SWEEP if L >= K]
 
 
 def dist_env():
@@ -81,7 +99,9 @@ def job_throughput(units_per_rank, steps, total_ms_local, world, dist=None, devi
 
 def load_workload(args, rank, world, barrier):
     import workload
-    kw = dict(n=args.n, nq=args.nq, ncomp=args.ncomp, k=100)
+    kw = dict(n=args.n, nq=args.nq, ncomp=args.ncomp, k=max(100, K))
+    if args.M != 32:
+        kw["M"] = args.M
     if rank == 0:
         w = workload.clustered_workload(2, verbose=True, **kw)
     barrier()
@@ -90,7 +110,8 @@ def load_workload(args, rank, world, barrier):
     return w
 
 
-def recall(found, truth, k=K):
+def recall(found, truth, k=None):
+    k = k or K
     f = np.asarray(found)[:, :k].astype(np.int64)
     t = np.asarray(truth)[:, :k].astype(np.int64)
     hits = (f[:, :, None] == t[:, None, :]).any(-1).sum()
@@ -208,15 +229,15 @@ def serving(bang, ix, w, L, mode, capacity_qps, log2z, seconds=2.0):
 def cpu_baseline(w, L, sample, log2z):
     """The oracle's search as it stands, OpenMP over queries on all host cores."""
     import oracle
-    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
+    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["codes"].shape[1])
     Q = w["queries"][:sample]
     t0 = time.perf_counter()
     r = ix.search(Q, K, L, log2z=log2z)
     dt = time.perf_counter() - t0
     return {"value": len(Q) / dt, "unit": "queries/s", "cores": oracle.max_threads(),
             "kind": "oracle",
-            "sample": "%d of the %d queries at L=%d (same index, same Bloom size); recall@10 %.4f"
-                      % (len(Q), w["queries"].shape[0], L, recall(r["ids"], w["gt_ids"][:len(Q)]))}
+            "sample": "%d of the %d queries at L=%d (same index, same Bloom size); recall@%d %.4f"
+                      % (len(Q), w["queries"].shape[0], L, K, recall(r["ids"], w["gt_ids"][:len(Q)]))}
 
 
 def run_reference(args):
@@ -226,12 +247,12 @@ def run_reference(args):
     import workload  # noqa: F401
     w = load_workload(args, 0, 1, lambda: None)
     import oracle
-    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
+    ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["codes"].shape[1])
     nq = w["queries"].shape[0]
     L = args.L
     if L is None:
-        L = L_SWEEP[-1]
-        for Lc in L_SWEEP:
+        L = sweep_values()[-1]
+        for Lc in sweep_values():
             r = ix.search(w["queries"][:1000], K, Lc, log2z=args.bloom_log2)
             if recall(r["ids"], w["gt_ids"][:1000]) >= TARGET_RECALL:
                 L = Lc
@@ -245,11 +266,11 @@ def run_reference(args):
         ix.search(Q, K, L, log2z=args.bloom_log2)
     dt = time.perf_counter() - t0
     v = sample * args.steps / dt
-    line = {"metric": "queries/s at recall@10=0.9", "value": v, "unit": "queries/s",
+    line = {"metric": metric_name(), "value": v, "unit": "queries/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L, "bloom_log2": args.bloom_log2,
+            "config": {"workload": workload_name(args), "L": L, "bloom_log2": args.bloom_log2,
                        "step": "%d queries (bounded sample of the 10k batch)" % sample},
             "impl": "reference",
             "cpu_baseline": {"value": v, "unit": "queries/s", "cores": oracle.max_threads(),
@@ -301,7 +322,7 @@ def main():
     import paper_2401_11324_gb300 as bang
     w = load_workload(args, rank, world, barrier)
     nq, d = w["queries"].shape
-    M = 32
+    M = w["codes"].shape[1]
     R = w["adj"].shape[1]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M, device=local)
     stream = torch.cuda.Stream(device=dev)
@@ -326,18 +347,18 @@ def main():
         ix.search(q_dev, K, L, ids, dist_out, p, stream=sptr)
 
     def operating_point(mode, tsrc=0, lz=None):
-        """Smallest L of the sweep with recall@10 >= 0.9 (or --L)."""
+        """Smallest L of the sweep with recall@k >= 0.9 (or --L)."""
         sweep = []
         if args.L is not None:
             return args.L, sweep
-        for Lc in L_SWEEP:
+        for Lc in sweep_values():
             search(Lc, mode, tsrc=tsrc, lz=lz)
             stream.synchronize()
             rc = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
-            sweep.append({"L": Lc, "recall@10": round(rc, 4)})
+            sweep.append({"L": Lc, "recall@%d" % K: round(rc, 4)})
             if rc >= TARGET_RECALL:
                 return Lc, sweep
-        return L_SWEEP[-1], sweep
+        return sweep_values()[-1], sweep
 
     def timed(L, mode, steps, tsrc=0, lz=None):
         for _ in range(args.warmup):
@@ -374,8 +395,8 @@ def main():
                                                tune["bloom_log2"], tune["L"],
                                                tune.get("placement", 0), [])
             what = ("autotuned (bang_autotune): %s table%s, Bloom filter 2^%d bits, smallest L "
-                    "reaching recall@10 0.9" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
-                                                " from the tensor cores" if tsrc else "", lz))
+                    "reaching recall@%d 0.9" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
+                                                " from the tensor cores" if tsrc else "", lz, K))
             if flags:
                 what = "In-memory variant (§5.1), graph and vectors in HBM, with the " + what
             place(flags)
@@ -391,7 +412,7 @@ def main():
                     launch_s=statistics.mean(step_ms) / 1e3, t_wall=t_wall)
 
     # ---- the two forms of the paper's base method (host graph): time both,
-    # report the faster at recall@10 >= 0.9 with the plain form beside it
+    # report the fastest at recall@k >= 0.9 with the plain form beside it
     with ClockSampler(local) as clk:
         res = {f: measure(f, args.steps) for f in ("fp32", "bf16", "bf16_tc", "q8")}
         tune = None
@@ -450,16 +471,16 @@ def main():
 
     def brief(r):
         return {"what": r["what"], "value": r["value"], "ms_per_step": r["ms_per_step"],
-                "L": r["L"], "recall@10": r["recall"], "sweep": r["sweep"],
+                "L": r["L"], "recall@%d" % K: r["recall"], "sweep": r["sweep"],
                 "mean_iterations": float(r["iters"].mean())}
 
     line = {
-        "metric": "queries/s at recall@10=0.9", "value": head["value"], "unit": "queries/s",
+        "metric": metric_name(), "value": head["value"], "unit": "queries/s",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {1: "bf16-table/f32", 3: "u8-table/int32"}.get(mode, "f32"), "data": "synthetic",
-        "config": {"workload": WORKLOAD, "form": head["form"], "form_what": head["what"],
-                   "L": L, "recall@10": head["recall"], "k": K,
+        "config": {"workload": workload_name(args), "form": head["form"], "form_what": head["what"],
+                   "L": L, "recall@%d" % K: head["recall"], "k": K,
                    "bloom_log2": lz, "sweep": head["sweep"], "autotune": tune,
                    "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
                    "phase_share": phases,
