@@ -43,9 +43,13 @@ L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024)
 TARGET_RECALL = 0.9
 K = 10                      # k of the search and of recall@k (--k)
 def workload_name(args):
+    if args.config == 3:
+        return ("precision form: n=%d f32 d=96 unit-normalised, 1024 components, %d queries, "
+                "PQ M=%d, R=68 (64 in-cluster + 4 medoid links), k=%d" % (
+                    args.n or 10_000_000, args.nq or 10_000, args.M or 48, K))
     n = args.n or 1_000_000
     return "mid-scale plain method: n=%s u8 d=128, %d queries, PQ M=%d, R=64, k=%d" % (
-        "1M" if n == 1_000_000 else str(n), args.nq or 10_000, args.M, K)
+        "1M" if n == 1_000_000 else str(n), args.nq or 10_000, args.M or 32, K)
 
 
 def parse():
@@ -63,7 +67,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--k", type=int, default=10, help="k of the search and of k-recall@k")
-    ap.add_argument("--M", type=int, default=32, help="PQ subspaces (bytes per code)")
+    ap.add_argument("--M", type=int, default=None, help="PQ subspaces (bytes per code)")
+    ap.add_argument("--config", type=int, default=2, choices=(2, 3),
+                    help="2: mid-scale u8 (the headline); 3: the precision form (f32 d=96)")
     args = ap.parse_args()
     global K
     K = args.k
@@ -100,14 +106,26 @@ def job_throughput(units_per_rank, steps, total_ms_local, world, dist=None, devi
 def load_workload(args, rank, world, barrier):
     import workload
     kw = dict(n=args.n, nq=args.nq, ncomp=args.ncomp, k=max(100, K))
-    if args.M != 32:
+    if args.M is not None:
         kw["M"] = args.M
     if rank == 0:
-        w = workload.clustered_workload(2, verbose=True, **kw)
+        w = workload.clustered_workload(args.config, verbose=True, **kw)
     barrier()
     if rank != 0:
-        w = workload.clustered_workload(2, **kw)
+        w = workload.clustered_workload(args.config, **kw)
     return w
+
+
+def dist_error(ids, dist, base, queries):
+    """Max and mean relative error of returned distances against FP64 exact
+    squared distances of the same ids."""
+    ids = np.asarray(ids).astype(np.int64)
+    ok = ids != 0xFFFFFFFF
+    q = np.repeat(np.arange(ids.shape[0]), ids.shape[1]).reshape(ids.shape)[ok]
+    ex = ((base[ids[ok]].astype(np.float64) - queries[q].astype(np.float64)) ** 2).sum(1)
+    err = np.abs(np.asarray(dist, np.float64)[ok] - ex) / np.maximum(ex, 1e-300)
+    return {"max_rel": float(err.max()) if err.size else 0.0,
+            "mean_rel": float(err.mean()) if err.size else 0.0}
 
 
 def recall(found, truth, k=None):
@@ -403,10 +421,13 @@ def main():
         search(L, mode, with_stats=True, tsrc=tsrc, lz=lz)
         stream.synchronize()
         rec = recall(ids.cpu().numpy().view(np.uint32), w["gt_ids"])
+        derr = dist_error(ids.cpu().numpy().view(np.uint32), dist_out.cpu().numpy(), w["base"],
+                          w["queries"])
         it = iters.cpu().numpy().astype(np.int64)
         nd = ndist.cpu().numpy().astype(np.int64)
         total_ms, step_ms, t_wall = timed(L, mode, steps, tsrc, lz)
         return dict(form=name, what=what, mode=mode, placement=flags, L=L, tsrc=tsrc, lz=lz,
+                    dist_error=derr,
                     recall=round(rec, 4), sweep=sweep, iters=it, ndist=nd,
                     value=nq * world * steps / (total_ms / 1e3), ms_per_step=total_ms / steps,
                     launch_s=statistics.mean(step_ms) / 1e3, t_wall=t_wall)
@@ -444,8 +465,9 @@ def main():
     phases["cycles_per_expansion"] = round(float(ph[-1] / max(1, it.sum())), 1)
 
     # ---- algorithmic bytes per launch (one launch = the whole batch)
-    host_bytes = int(it.sum()) * (R * 4 + d * 1)           # neighbour row + full vector per expansion
-    hbm_bytes = int(nd.sum()) * M + nq * d + nq * K * 8 + 256 * d * 4
+    esz = w["base"].dtype.itemsize
+    host_bytes = int(it.sum()) * (R * 4 + d * esz)         # neighbour row + full vector per expansion
+    hbm_bytes = int(nd.sum()) * M + nq * d * esz + nq * K * 8 + 256 * d * 4
     launch_s = head["launch_s"]
 
     # ---- end to end through the C ABI: pinned host queries and results
@@ -472,7 +494,8 @@ def main():
     def brief(r):
         return {"what": r["what"], "value": r["value"], "ms_per_step": r["ms_per_step"],
                 "L": r["L"], "recall@%d" % K: r["recall"], "sweep": r["sweep"],
-                "mean_iterations": float(r["iters"].mean())}
+                "mean_iterations": float(r["iters"].mean()),
+                "dist_error_vs_fp64": r["dist_error"]}
 
     line = {
         "metric": metric_name(), "value": head["value"], "unit": "queries/s",
@@ -505,7 +528,7 @@ def main():
                       "algorithmic_bytes_per_launch": host_bytes,
                       "note": "binding link: neighbour rows and full vectors read in place from "
                               "page-locked host memory"},
-        "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d,
+        "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d * esz,
                 "d2h_bytes_per_step": nq * K * 8},
         "gpu_launches": args.steps * (2 if tsrc else 1),
         "clocks": clk.summary(),

@@ -16,6 +16,9 @@ Configurations (the recipe of each is in ``CONFIGS``):
      low-rank like SIFT descriptors: x = c + A z + 4 e, A (d x 12) with
      N(0, 20^2/12) entries, z ~ N(0, I_12), e ~ N(0, I_d); rounded and
      clipped to 0..255; 10,000 queries; PQ M=32; clustered graph R=64.
+  3  n=10,000,000 f32 d=96, 1,024 components, centres ~N(0, I) scaled to unit
+     length, x = normalise(c + 0.1 z); 10,000 queries; PQ M=48; clustered
+     graph with 64 in-cluster neighbours and 4 medoid links (R=68).
 Seeds: data 1000+cfg, queries 2000+cfg, PQ 3000+cfg, graph 4000+cfg.
 """
 import ctypes
@@ -37,6 +40,11 @@ CONFIGS = {
     2: dict(n=1_000_000, nq=10_000, d=128, dtype="u8", ncomp=256, centre="uniform255",
             centre_scale=None, sigma=20.0, rank=12, noise=4.0, M=32, R=64, alpha=1.2, nx=4,
             nh=32, k=10, L=64),
+    # precision form: unit-normalised mixture under L2; 64 in-cluster
+    # neighbours plus 4 links to other clusters' medoids (degree <= 68)
+    3: dict(n=10_000_000, nq=10_000, d=96, dtype="f32", ncomp=1024, centre="unitnormal",
+            centre_scale=None, sigma=0.1, normalise=True, M=48, R=68, alpha=1.2, nx=4, nh=32,
+            k=10, L=128),
 }
 
 _DTN = {"u8": np.uint8, "i8": np.int8, "f32": np.float32}
@@ -85,11 +93,13 @@ def chunk_offsets(d, M):
         np.uint32)
 
 
-def _mixture(rng, n, d, centres, sigma, dtype, factors=None, noise=0.0, chunk=131072):
+def _mixture(rng, n, d, centres, sigma, dtype, factors=None, noise=0.0, chunk=131072,
+             normalise=False):
     """Equal-weight Gaussian mixture; integer types are rounded and clipped.
     Isotropic components (sigma per dimension), or, with ``factors``
     (ncomp x d x r), low-rank components x = c + A z + noise*e with
-    z ~ N(0, I_r) and e ~ N(0, I_d)."""
+    z ~ N(0, I_r) and e ~ N(0, I_d).  ``normalise`` scales every point to
+    unit length."""
     lab = rng.integers(0, centres.shape[0], size=n).astype(np.uint32)
     out = np.empty((n, d), dtype=_DTN[dtype])
     for i in range(0, n, chunk):
@@ -100,6 +110,8 @@ def _mixture(rng, n, d, centres, sigma, dtype, factors=None, noise=0.0, chunk=13
             z = rng.standard_normal((j - i, factors.shape[2]), dtype=np.float32)
             x = centres[lab[i:j]] + np.einsum("ndr,nr->nd", factors[lab[i:j]], z)
             x += noise * rng.standard_normal((j - i, d), dtype=np.float32)
+        if normalise:
+            x /= np.maximum(np.linalg.norm(x, axis=1, keepdims=True), np.float32(1e-30))
         if dtype == "u8":
             out[i:j] = np.clip(np.rint(x), 0, 255).astype(np.uint8)
         elif dtype == "i8":
@@ -114,6 +126,9 @@ def _centres(rng, c):
         cen = rng.standard_normal((c["ncomp"], c["d"]), dtype=np.float32) * c["centre_scale"]
     elif c["centre"] == "uniform255":
         cen = rng.uniform(0.0, 255.0, size=(c["ncomp"], c["d"])).astype(np.float32)
+    elif c["centre"] == "unitnormal":
+        cen = rng.standard_normal((c["ncomp"], c["d"]), dtype=np.float32)
+        cen /= np.linalg.norm(cen, axis=1, keepdims=True)
     elif c["centre"] == "uniform100":
         cen = rng.uniform(-100.0, 100.0, size=(c["ncomp"], c["d"])).astype(np.float32)
     else:
@@ -138,9 +153,11 @@ def make_data(cfg, n=None, nq=None, ncomp=None, **over):
     if c.get("rank", 0):
         fac = (rng.standard_normal((c["ncomp"], c["d"], c["rank"]), dtype=np.float32) *
                np.float32(c["sigma"] / np.sqrt(c["rank"])))
-    base, lab = _mixture(rng, c["n"], c["d"], cen, c["sigma"], c["dtype"], fac, c.get("noise", 0))
+    nrm = c.get("normalise", False)
+    base, lab = _mixture(rng, c["n"], c["d"], cen, c["sigma"], c["dtype"], fac, c.get("noise", 0),
+                         normalise=nrm)
     queries, _ = _mixture(np.random.default_rng(2000 + cfg), c["nq"], c["d"], cen, c["sigma"],
-                          c["dtype"], fac, c.get("noise", 0))
+                          c["dtype"], fac, c.get("noise", 0), normalise=nrm)
     return dict(cfg=cfg, params=c, base=base, labels=lab, queries=queries)
 
 
