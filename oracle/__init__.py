@@ -10,6 +10,9 @@ no code with the CUDA implementation.
 Parity status of each function (see the C file for the passage it follows):
   pq_train, pq_encode, medoid, adc_table, adc_dist, adc_table_q8, adc_dist_q8, exact_dist, bloom,
   search, bruteforce_knn : pinned by tests/test_oracle_*.py
+  cluster_graph          : pinned by closed forms (a line with alpha = 1 gives
+                           the chain; a huge alpha gives the exact nearest
+                           lists) and by the generator's independent build
   vamana_build           : invariants only ("parity unpinned" beyond degree,
                            self-loop, duplicate, pruning-rule and reachability
                            checks; the paper takes the graph from DiskANN and
@@ -73,6 +76,9 @@ def lib():
         L.orc_robust_prune.restype = u32
         L.orc_vamana_build.argtypes = [vp, u64, u32, u32, u32, f32, u32, vp, vp, vp]
         L.orc_vamana_build.restype = i32
+        L.orc_cluster_graph.argtypes = [vp, i32, u32, u64, vp, vp, u32, vp, u32, f32, u32, vp,
+                                        u32, vp, vp]
+        L.orc_cluster_graph.restype = i32
         L.orc_adc_table_f32.argtypes = [vp, u32, vp, vp, vp]
         L.orc_adc_dist_f32.argtypes = [vp, u32, vp]
         L.orc_adc_dist_f32.restype = f32
@@ -162,6 +168,23 @@ def vamana_build(X, R, Lb, alpha, medoid_id, init_adj, order):
     adj = np.zeros((n, R), np.uint32)
     rc = lib().orc_vamana_build(_p(X), n, d, R, Lb, alpha, medoid_id, _p(init_adj), _p(order),
                                 _p(adj))
+    assert rc == 0
+    return adj
+
+
+def cluster_graph(X, members, gstart, medoids, R, alpha, nx=0, xclu=None, nh=0, hclu=None):
+    """Clustered construction (see orc_cluster_graph): n x R adjacency."""
+    X = np.ascontiguousarray(X)
+    n, d = X.shape
+    members = _c(members, np.uint32)
+    gstart = _c(gstart, np.uint64)
+    medoids = _c(medoids, np.uint32)
+    ng = len(medoids)
+    xclu = _c(xclu if xclu is not None else np.zeros((n, 0)), np.uint32)
+    hclu = _c(hclu if hclu is not None else np.zeros((ng, 0)), np.uint32)
+    adj = np.zeros((n, R), np.uint32)
+    rc = lib().orc_cluster_graph(_p(X), _DT[X.dtype], d, n, _p(members), _p(gstart), ng,
+                                 _p(medoids), R, alpha, nx, _p(xclu), nh, _p(hclu), _p(adj))
     assert rc == 0
     return adj
 

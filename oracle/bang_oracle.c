@@ -25,6 +25,9 @@
  *   orc_vamana_build         §2.2, §6.3 (R, L, pruning parameter); parity unpinned
  *                            beyond invariants: the paper takes the graph from
  *                            DiskANN and does not state its construction
+ *   orc_cluster_graph        the clustered construction of the large synthetic
+ *                            indexes (per-cluster candidates, RobustPrune of §2.2,
+ *                            reverse edges, medoid links); not from the paper
  *   orc_adc_table_f32        §4.1 (PQDistTable: squared distance of each query
  *                            sub-vector to each centroid)
  *   orc_adc_dist_f32         §4.4 (asymmetric distance = sum of table entries)
@@ -354,6 +357,192 @@ int orc_vamana_build(const float *X, uint64_t n, uint32_t d, uint32_t R, uint32_
         }
     }
     free(seen); free(touched); free(Lst); free(exp); free(V); free(cand); free(pr);
+    return 0;
+}
+
+/* ---------------------------------------------------------------------- */
+/* Clustered graph.  The paper searches a graph it takes from DiskANN (§1)  */
+/* and gives no construction; the large synthetic indexes here use this    */
+/* one, restated plainly so that the GPU builder can be checked against it. */
+/* For each cluster (members given in ascending id; b = local position):   */
+/*  1. candidates of member a: the K = min(2 Rin, m - 1) other members      */
+/*     nearest to a, by (distance, b), Rin = R - nx;                        */
+/*  2. RobustPrune (Vamana, §2.2): walk the candidates in (distance, b)     */
+/*     order; a candidate still alive is kept (up to Rin) and removes every */
+/*     later candidate j with alpha^2 * d(kept, j) <= d(a, j), alpha^2 and  */
+/*     the product rounded to FP32;                                         */
+/*  3. reverse edges: the kept list plus every member that kept a, without  */
+/*     repeats, pruned again the same way;                                  */
+/*  4. repair, members in ascending b: a member nobody links to (and that   */
+/*     has neighbours) is appended to the first of its neighbours that has  */
+/*     room, or replaces that neighbour's last entry when the entry's       */
+/*     target keeps another in-link; in-degrees are updated as it goes;     */
+/*  5. the global row of a member: its list (a cluster medoid keeps at most */
+/*     R - nh), then the medoids of the clusters in xclu (nx per point) or, */
+/*     for a cluster medoid, hclu (nh per cluster), skipping its own        */
+/*     cluster and out-of-range ids; repeated ids are dropped keeping the   */
+/*     first; the rest of the row is 0xFFFFFFFF.                            */
+/* Distances are squared L2: exact integers for u8/i8; for f32 the sum in   */
+/* ascending j of (x_j - y_j)^2, each difference, product and sum rounded   */
+/* to FP32.                                                                 */
+/* ---------------------------------------------------------------------- */
+
+static float cg_dist(const void *X, int dtype, uint32_t d, uint64_t a, uint64_t b)
+{
+    uint32_t j;
+    if (dtype == ORC_F32) {
+        const float *x = (const float *)X + a * d, *y = (const float *)X + b * d;
+        float acc = 0.0f;
+        for (j = 0; j < d; j++) {
+            float t = x[j] - y[j];
+            float sq = t * t;
+            acc = acc + sq;
+        }
+        return acc;
+    } else {
+        int64_t acc = 0;
+        for (j = 0; j < d; j++) {
+            int64_t t = (int64_t)elem_i(X, dtype, a * d + j) - (int64_t)elem_i(X, dtype, b * d + j);
+            acc += t * t;
+        }
+        return (float)acc;
+    }
+}
+
+typedef struct { float dist; uint32_t b; } cg_cand;
+
+static int cg_cmp(const void *pa, const void *pb)
+{
+    const cg_cand *x = (const cg_cand *)pa, *y = (const cg_cand *)pb;
+    if (x->dist < y->dist) return -1;
+    if (x->dist > y->dist) return 1;
+    return (x->b < y->b) ? -1 : (x->b > y->b);
+}
+
+/* RobustPrune of step 2 over nc candidates (sorted here); P maps local
+ * positions to point ids.  Returns the number kept (written to out). */
+static uint32_t cg_prune(const void *X, int dtype, uint32_t d, const uint32_t *P, cg_cand *c,
+                         uint32_t nc, float alpha, uint32_t Rin, uint32_t *out)
+{
+    uint32_t i, j, nout = 0;
+    float a2 = alpha * alpha;
+    unsigned char *dead = (unsigned char *)calloc(nc ? nc : 1, 1);
+    qsort(c, nc, sizeof(cg_cand), cg_cmp);
+    for (i = 0; i < nc && nout < Rin; i++) {
+        if (dead[i]) continue;
+        out[nout++] = c[i].b;
+        for (j = i + 1; j < nc; j++) {
+            if (dead[j]) continue;
+            float lhs = a2 * cg_dist(X, dtype, d, P[c[i].b], P[c[j].b]);
+            if (lhs <= c[j].dist) dead[j] = 1;
+        }
+    }
+    free(dead);
+    return nout;
+}
+
+int orc_cluster_graph(const void *X, int dtype, uint32_t d, uint64_t n, const uint32_t *members,
+                      const uint64_t *gstart, uint32_t ng, const uint32_t *medoids, uint32_t R,
+                      float alpha, uint32_t nx, const uint32_t *xclu, uint32_t nh,
+                      const uint32_t *hclu, uint32_t *adj)
+{
+    uint32_t g, Rin;
+    uint64_t i;
+    if (nx >= R || nh >= R) return -1;
+    Rin = R - nx;
+    for (i = 0; i < n * (uint64_t)R; i++) adj[i] = ORC_NONE;
+    for (g = 0; g < ng; g++) {
+        uint32_t m = (uint32_t)(gstart[g + 1] - gstart[g]), a, b, t, K;
+        const uint32_t *P = members + gstart[g];
+        uint32_t *fwd, *fwd2, *deg, *deg2, *indeg;
+        cg_cand *cand;
+        if (m == 0) continue;
+        K = 2 * Rin < m - 1 ? 2 * Rin : m - 1;
+        fwd = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * Rin);
+        fwd2 = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)m * Rin);
+        deg = (uint32_t *)calloc(m, sizeof(uint32_t));
+        deg2 = (uint32_t *)calloc(m, sizeof(uint32_t));
+        indeg = (uint32_t *)calloc(m, sizeof(uint32_t));
+        cand = (cg_cand *)malloc(sizeof(cg_cand) * (m + Rin + 1));
+        if (!fwd || !fwd2 || !deg || !deg2 || !indeg || !cand) {
+            free(fwd); free(fwd2); free(deg); free(deg2); free(indeg); free(cand);
+            return -2;
+        }
+        /* steps 1-2 */
+        for (a = 0; a < m; a++) {
+            uint32_t nc = 0;
+            for (b = 0; b < m; b++) {
+                if (b == a) continue;
+                cand[nc].dist = cg_dist(X, dtype, d, P[a], P[b]);
+                cand[nc].b = b;
+                nc++;
+            }
+            qsort(cand, nc, sizeof(cg_cand), cg_cmp);
+            deg[a] = cg_prune(X, dtype, d, P, cand, K, alpha, Rin, fwd + (size_t)a * Rin);
+        }
+        /* step 3 */
+        for (a = 0; a < m; a++) {
+            uint32_t nc = 0;
+            for (t = 0; t < deg[a]; t++) {
+                cand[nc].b = fwd[(size_t)a * Rin + t];
+                cand[nc].dist = cg_dist(X, dtype, d, P[a], P[cand[nc].b]);
+                nc++;
+            }
+            for (b = 0; b < m; b++) {
+                int chose = 0, have = 0;
+                for (t = 0; t < deg[b]; t++) if (fwd[(size_t)b * Rin + t] == a) chose = 1;
+                if (!chose) continue;
+                for (t = 0; t < deg[a]; t++) if (fwd[(size_t)a * Rin + t] == b) have = 1;
+                if (have) continue;
+                cand[nc].b = b;
+                cand[nc].dist = cg_dist(X, dtype, d, P[a], P[b]);
+                nc++;
+            }
+            deg2[a] = cg_prune(X, dtype, d, P, cand, nc, alpha, Rin, fwd2 + (size_t)a * Rin);
+        }
+        /* step 4 */
+        for (a = 0; a < m; a++)
+            for (t = 0; t < deg2[a]; t++) indeg[fwd2[(size_t)a * Rin + t]]++;
+        for (a = 0; a < m; a++) {
+            if (indeg[a] != 0 || deg2[a] == 0) continue;
+            for (t = 0; t < deg2[a]; t++) {
+                uint32_t j = fwd2[(size_t)a * Rin + t];
+                uint32_t *lj = fwd2 + (size_t)j * Rin;
+                if (deg2[j] < Rin) {
+                    lj[deg2[j]] = a;
+                    deg2[j]++;
+                    indeg[a]++;
+                    break;
+                }
+                if (indeg[lj[deg2[j] - 1]] > 1) {
+                    indeg[lj[deg2[j] - 1]]--;
+                    lj[deg2[j] - 1] = a;
+                    indeg[a]++;
+                    break;
+                }
+            }
+        }
+        /* step 5 */
+        for (a = 0; a < m; a++) {
+            uint32_t *row = adj + (uint64_t)P[a] * R, w = 0, r, q;
+            int is_med = P[a] == medoids[g];
+            uint32_t keep = deg2[a];
+            if (is_med && keep > R - nh) keep = R - nh;
+            for (t = 0; t < keep; t++) row[w++] = P[fwd2[(size_t)a * Rin + t]];
+            for (t = 0; t < (is_med ? nh : nx); t++) {
+                uint32_t c2 = is_med ? hclu[(size_t)g * nh + t] : xclu[(uint64_t)P[a] * nx + t];
+                if (c2 >= ng || c2 == g || medoids[c2] == ORC_NONE) continue;
+                row[w++] = medoids[c2];
+            }
+            for (r = 0; r < w; r++)
+                for (q = 0; q < r; q++)
+                    if (row[q] != ORC_NONE && row[q] == row[r]) { row[r] = ORC_NONE; break; }
+            q = 0;
+            for (r = 0; r < w; r++) if (row[r] != ORC_NONE) row[q++] = row[r];
+            for (r = q; r < R; r++) row[r] = ORC_NONE;
+        }
+        free(fwd); free(fwd2); free(deg); free(deg2); free(indeg); free(cand);
+    }
     return 0;
 }
 

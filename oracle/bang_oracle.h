@@ -41,6 +41,10 @@ uint32_t orc_robust_prune(const float *X, uint32_t d, uint32_t p, const uint32_t
 int orc_vamana_build(const float *X, uint64_t n, uint32_t d, uint32_t R, uint32_t Lb,
                      float alpha, uint32_t medoid, const uint32_t *init_adj,
                      const uint32_t *order, uint32_t *adj);
+int orc_cluster_graph(const void *X, int dtype, uint32_t d, uint64_t n, const uint32_t *members,
+                      const uint64_t *gstart, uint32_t ng, const uint32_t *medoids, uint32_t R,
+                      float alpha, uint32_t nx, const uint32_t *xclu, uint32_t nh,
+                      const uint32_t *hclu, uint32_t *adj);
 void orc_adc_table_f32(const float *q, uint32_t M, const uint32_t *off,
                        const float *codebook, float *T);
 float orc_adc_dist_f32(const float *T, uint32_t M, const uint8_t *code);

@@ -36,6 +36,11 @@ MUTANTS = [
     ("q8_last_subspace_scale", "if (w > g) g = w;", "g = w;", 0),
     ("q8_search_uses_exact", "if (mode == 2) return (float)orc_adc_dist_q8(",
      "if (mode == 9) return (float)orc_adc_dist_q8(", 0),
+    ("cg_kill_strict", "if (lhs <= c[j].dist) dead[j] = 1;", "if (lhs < c[j].dist) dead[j] = 1;", 0),
+    ("cg_K_is_Rin", "K = 2 * Rin < m - 1 ? 2 * Rin : m - 1;", "K = Rin < m - 1 ? Rin : m - 1;", 0),
+    ("cg_no_reverse_edges", "if (!chose) continue;", "if (1) continue;", 0),
+    ("cg_no_repair", "if (indeg[a] != 0 || deg2[a] == 0) continue;", "if (1) continue;", 0),
+    ("cg_alpha_unsquared", "float a2 = alpha * alpha;", "float a2 = alpha;", 0),
     ("exact_mode_keeps_rerank", "if (mode == 1) {                    /* Alg. 1",
      "if (mode == 7) {                    /* Alg. 1", 0),
 ]

@@ -2,6 +2,7 @@
 the mathematics fixes (closed forms, published hash vectors, the paper's
 worked example, invariants, brute force on tiny inputs), never against a
 retyped copy of itself."""
+import ctypes
 import math
 import os
 from fractions import Fraction
@@ -573,6 +574,122 @@ def test_robust_prune_rule():
             if c in kept:
                 continue
             assert any(alpha ** 2 * d(b, c) <= d(p, c) for b in kept if (d(p, b), b) < (d(p, c), c))
+
+
+# ---------------------------------------------------------------- clustered graph construction
+
+def test_cluster_graph_line_alpha1_is_chain():
+    # Points on a line (d = 1), one cluster, alpha = 1: the nearest candidate
+    # removes every candidate beyond it on its side, so each point keeps its
+    # nearest neighbour on either side, the nearer first (ties: smaller id).
+    rng = np.random.default_rng(31)
+    n = 40
+    pos = np.cumsum(rng.integers(1, 4, size=n))             # distinct, gaps 1..3
+    assert pos.max() < 256
+    ids_by_pos = rng.permutation(n)                         # id of the i-th point from the left
+    X = np.zeros((n, 1), np.uint8)
+    X[ids_by_pos, 0] = pos
+    adj = oracle.cluster_graph(X, np.arange(n), [0, n], [0], R=6, alpha=1.0)
+    for i in range(n):
+        a = ids_by_pos[i]
+        nb = [(int(pos[j] - pos[i]) ** 2, int(ids_by_pos[j])) for j in (i - 1, i + 1) if 0 <= j < n]
+        want = [b for _, b in sorted(nb)]
+        assert adj[a].tolist() == want + [NONE] * (6 - len(want)), (i, adj[a], want)
+
+
+def test_cluster_graph_huge_alpha_gives_nearest_lists_and_links():
+    # alpha = 1e4 removes nothing (distinct points), so every in-cluster list
+    # is the exact R - nx nearest members, except where step 4 gave a point
+    # nobody linked to a place at the end of a neighbour's full list.  Rows end
+    # with the medoids of the listed clusters, own cluster skipped.
+    rng = np.random.default_rng(32)
+    ng, per, d, R, nx, nh = 3, 30, 4, 10, 2, 2
+    n = ng * per
+    X = np.unique(rng.integers(0, 256, size=(n + 20, d)), axis=0)[:n].astype(np.uint8)
+    X = X[rng.permutation(n)]
+    lab = np.repeat(np.arange(ng), per)[rng.permutation(n)]
+    members = np.argsort(lab, kind="stable").astype(np.uint32)
+    gstart = np.concatenate([[0], np.cumsum(np.bincount(lab, minlength=ng))])
+    medoids = np.array([members[gstart[g]] for g in range(ng)], np.uint32)
+    xclu = rng.integers(0, ng, size=(n, nx))
+    hclu = np.array([[(g + 1) % ng, (g + 2) % ng] for g in range(ng)])
+    adj = oracle.cluster_graph(X, members, gstart, medoids, R, 1e4, nx, xclu, nh, hclu)
+    Rin = R - nx
+    for g in range(ng):
+        P = members[gstart[g]:gstart[g + 1]]
+        D = ((X[P].astype(np.int64)[:, None] - X[P].astype(np.int64)[None]) ** 2).sum(-1)
+        knn = []
+        for a in range(len(P)):
+            o = [b for b in np.lexsort((np.arange(len(P)), D[a])) if b != a][:Rin]
+            knn.append(o)
+        indeg = np.zeros(len(P), int)
+        for o in knn:
+            indeg[o] += 1
+        orphans = set(P[np.where(indeg == 0)[0]].tolist())
+        for a in range(len(P)):
+            row = adj[P[a]]
+            is_med = P[a] == medoids[g]
+            keep = min(Rin, R - nh) if is_med else Rin
+            exp = [P[b] for b in knn[a]][:keep]
+            assert row[:keep - 1].tolist() == exp[:keep - 1]
+            assert row[keep - 1] == exp[keep - 1] or int(row[keep - 1]) in orphans
+            links = [int(medoids[c]) for c in (hclu[g] if is_med else xclu[P[a]]) if c != g]
+            tail = []
+            for x in links:
+                if x not in tail and x not in row[:keep].tolist():
+                    tail.append(x)
+            assert row[keep:keep + len(tail)].tolist() == tail
+            assert (row[keep + len(tail):] == NONE).all()
+
+
+def test_cluster_graph_repair_links_an_outlier():
+    # A tight group plus one far point: no member keeps the far point (alpha
+    # huge: lists are the exact nearest), so step 4 puts it at the end of its
+    # nearest neighbour's full list, in place of an entry that keeps another
+    # in-link.
+    rng = np.random.default_rng(34)
+    m, R = 25, 6
+    X = np.unique(rng.integers(100, 140, size=(m + 10, 3)), axis=0)[:m - 1].astype(np.uint8)
+    X = np.vstack([X, np.array([[250, 250, 250]], np.uint8)])     # outlier = id m-1
+    adj = oracle.cluster_graph(X, np.arange(m), [0, m], [0], R=R, alpha=1e4)
+    D = ((X.astype(np.int64)[:, None] - X.astype(np.int64)[None]) ** 2).sum(-1)
+    knn = [[b for b in np.lexsort((np.arange(m), D[a])) if b != a][:R] for a in range(m)]
+    assert all(m - 1 not in knn[a] for a in range(m - 1))
+    j = knn[m - 1][0]
+    indeg = np.bincount(np.concatenate(knn), minlength=m)
+    assert indeg[knn[j][-1]] > 1
+    assert adj[j].tolist() == knn[j][:-1] + [m - 1]
+    assert adj[m - 1].tolist() == knn[m - 1]
+
+
+def test_cluster_graph_matches_independent_generator_build():
+    # the workload generator builds the same construction with its own code
+    # (quickselect, OpenMP over clusters); both must agree bit for bit,
+    # including alpha = 1 on small-range integers, where distance ties decide
+    import workload
+    rng = np.random.default_rng(33)
+    for dt, alpha, hi in (("u8", 1.0, 6), ("u8", 1.2, 256), ("i8", 1.2, 128), ("f32", 1.2, 0)):
+        ng, n, d, R, nx, nh = 4, 400, 8, 12, 2, 3
+        if dt == "f32":
+            X = rng.normal(size=(n, d)).astype(np.float32)
+        elif dt == "i8":
+            X = rng.integers(-hi, hi, size=(n, d)).astype(np.int8)
+        else:
+            X = rng.integers(0, hi, size=(n, d)).astype(np.uint8)
+        lab = rng.integers(0, ng, size=n)
+        members = np.argsort(lab, kind="stable").astype(np.uint32)
+        gstart = np.concatenate([[0], np.cumsum(np.bincount(lab, minlength=ng))]).astype(np.uint64)
+        medoids = np.array([members[gstart[g]] for g in range(ng)], np.uint32)
+        xclu = rng.integers(0, ng, size=(n, nx)).astype(np.uint32)
+        hclu = rng.integers(0, ng, size=(ng, nh)).astype(np.uint32)
+        ref = oracle.cluster_graph(X, members, gstart, medoids, R, alpha, nx, xclu, nh, hclu)
+        gen = np.zeros((n, R), np.uint32)
+        rc = workload.lib().wl_cluster_graph(
+            workload._p(X), {"u8": 0, "i8": 1, "f32": 2}[dt], d, n, workload._p(members),
+            workload._p(gstart), ng, workload._p(medoids), R, ctypes.c_float(alpha), nx,
+            workload._p(xclu), nh, workload._p(hclu), workload._p(gen))
+        assert rc == 0
+        assert (gen == ref).all(), (dt, alpha, np.argwhere(gen != ref)[:5])
 
 
 def test_vamana_invariants():
