@@ -233,6 +233,62 @@ int bang_pq_tables(bang_index *ix, const void *queries, uint32_t nq, void *out, 
 int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M, uint32_t *R,
                     int32_t *dtype);
 
+/* ---- Index build on the GPU.  The paper searches an index built
+ * beforehand (its graph comes from DiskANN, §1; PQ with 256 centroids per
+ * subspace, §4); these calls build the same kinds of arrays on the device.
+ *
+ * Clustered graph: for every cluster (members listed in ascending id, local
+ * position b = index within the cluster):
+ *   1. candidates of member a: the K = min(2 Rin, m - 1) other members
+ *      nearest to a by (distance, b), with Rin = R - nx;
+ *   2. RobustPrune (Vamana, §2.2): in (distance, b) order a live candidate is
+ *      kept (at most Rin) and removes every later candidate j with
+ *      alpha^2 * d(kept, j) <= d(a, j), alpha^2 and the product in FP32;
+ *   3. the kept list plus every member that kept a, pruned again;
+ *   4. repair, members in ascending b: a member nobody links to (with
+ *      neighbours of its own) is appended to the first of its neighbours with
+ *      room, or replaces that neighbour's last entry when that entry's target
+ *      keeps another in-link;
+ *   5. row of member a: its list (a cluster medoid keeps at most R - nh),
+ *      then medoids[xclu[a][t]] for t < nx (for a cluster medoid
+ *      medoids[hclu[g][t]], t < nh), skipping its own cluster, ids >= ng and
+ *      medoids 0xFFFFFFFF; repeated ids dropped keeping the first; padding
+ *      0xFFFFFFFF.
+ * Distances are squared L2 rounded to FP32: integer data summed exactly then
+ * converted; f32 summed in ascending dimension order, each difference,
+ * product and sum rounded (no fused multiply-add).  Deterministic: the same
+ * inputs give the same bytes on any run.
+ *   base     n*d elements of dtype, host or device.
+ *   members  host, n ids: a permutation of 0..n-1 grouped by cluster, each
+ *            cluster in ascending id; gstart host, ng+1 offsets from 0 to n.
+ *   medoids  host, ng ids (< n, or 0xFFFFFFFF for none).
+ *   xclu     host, n*nx cluster ids (row = point id); hclu host, ng*nh.
+ *   adj      n*R output, host or device.
+ * Limits: R <= 128, nx < R, nh < R, rows of at most 2048 bytes.  Allocates
+ * its own device scratch (about n*(d*elem + 12*Rin + 40) bytes) and blocks
+ * until done on `stream`.  BANG_EINVAL for inconsistent index arrays. */
+int bang_build_cluster_graph(int device, const void *base, bang_dtype dtype, uint64_t n, uint32_t d,
+                             const uint32_t *members, const uint64_t *gstart, uint32_t ng,
+                             const uint32_t *medoids, uint32_t R, float alpha, uint32_t nx,
+                             const uint32_t *xclu, uint32_t nh, const uint32_t *hclu,
+                             uint32_t *adj, void *stream);
+
+/* PQ codebook and codes on the GPU (§4): M contiguous subspaces, the first
+ * d mod M one dimension wider (§6.3); 256 centroids per subspace by k-means:
+ * centroids start at the points init[s*256 + c]; each of `iters` Lloyd
+ * iterations assigns every training point (rows `sample`) to its nearest
+ * centroid (FP64 distance in ascending dimension order, each difference,
+ * product and sum rounded; ties to the smaller centroid) and moves each
+ * centroid to the FP64 mean of its points summed in sample order (no points:
+ * it stays).  The FP32 codebook (256*d floats; subspace s at 256*off[s],
+ * centroid c at +c*dsub_s) then encodes all n points the same way (codes
+ * n*M).  Deterministic.  base host or device; sample (ns ids) and init
+ * (M*256 ids) host, all < n; codebook and codes host or device.  Subspaces
+ * of at most 16 dimensions.  Blocks until done. */
+int bang_build_pq(int device, const void *base, bang_dtype dtype, uint64_t n, uint32_t d, uint32_t M,
+                  const uint64_t *sample, uint64_t ns, const uint64_t *init, uint32_t iters,
+                  float *codebook, uint8_t *codes, void *stream);
+
 /* ---- Autotuner (not in the paper).  Picks, for this GPU and index, the
  * settings that change speed but not the method: the PQ table's precision
  * (bang_mode; bit m of `modes` admits mode m), whether mode 1's tables come

@@ -103,6 +103,9 @@ def _load():
     L.bang_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.c_int32, vp, vp,
                                    ctypes.POINTER(ctypes.c_double)]
     L.bang_server_stop.argtypes = [vp]
+    L.bang_build_cluster_graph.argtypes = [i32, vp, i32, u64, u32, vp, vp, u32, vp, u32,
+                                           ctypes.c_float, u32, vp, u32, vp, vp, vp]
+    L.bang_build_pq.argtypes = [i32, vp, i32, u64, u32, u32, vp, u64, vp, u32, vp, vp, vp]
     L.bang_autotune.argtypes = [vp, vp, u32, u32, u32, vp, ctypes.POINTER(bang_autotune_opts),
                                 ctypes.POINTER(bang_autotune_result), vp]
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
@@ -111,7 +114,8 @@ def _load():
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
               "bang_search_batched_noalloc", "bang_index_info", "bang_server_start", "bang_pq_tables",
-              "bang_server_submit", "bang_server_wait", "bang_server_stop", "bang_autotune"):
+              "bang_server_submit", "bang_server_wait", "bang_server_stop", "bang_autotune",
+              "bang_build_cluster_graph", "bang_build_pq"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -223,6 +227,40 @@ def bang_autotune(ix, queries, nq, k, L, truth=None, modes=0, bloom_min=0, bloom
     _check(lib().bang_autotune(ix, _ptr(queries), nq, k, L, _ptr(t), ctypes.byref(o),
                                ctypes.byref(r), s))
     return {f: getattr(r, f) for f, _ in bang_autotune_result._fields_}
+
+
+def bang_build_cluster_graph(base, members, gstart, medoids, R, alpha, nx=0, xclu=None, nh=0,
+                             hclu=None, adj=None, device=0, stream=None):
+    """Clustered graph built on the GPU; returns adj (n x R uint32, numpy
+    unless a device tensor is passed)."""
+    n, d = base.shape
+    dt = _DTYPES[np.dtype(str(base.dtype).replace("torch.", ""))]
+    members = np.ascontiguousarray(members, np.uint32)
+    gstart = np.ascontiguousarray(gstart, np.uint64)
+    medoids = np.ascontiguousarray(medoids, np.uint32)
+    xclu = np.ascontiguousarray(xclu if xclu is not None else np.zeros((n, 0)), np.uint32)
+    hclu = np.ascontiguousarray(hclu if hclu is not None else np.zeros((len(medoids), 0)), np.uint32)
+    if adj is None:
+        adj = np.zeros((n, R), np.uint32)
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    _check(lib().bang_build_cluster_graph(device, _ptr(base), dt, n, d, _ptr(members), _ptr(gstart),
+                                          len(medoids), _ptr(medoids), R, alpha, nx, _ptr(xclu), nh,
+                                          _ptr(hclu), _ptr(adj), s))
+    return adj
+
+
+def bang_build_pq(base, M, sample, init, iters=10, device=0, stream=None):
+    """PQ codebook (256*d float32) and codes (n x M uint8) built on the GPU."""
+    n, d = base.shape
+    dt = _DTYPES[np.dtype(str(base.dtype).replace("torch.", ""))]
+    sample = np.ascontiguousarray(sample, np.uint64)
+    init = np.ascontiguousarray(init, np.uint64)
+    cb = np.zeros(256 * d, np.float32)
+    codes = np.zeros((n, M), np.uint8)
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    _check(lib().bang_build_pq(device, _ptr(base), dt, n, d, M, _ptr(sample), len(sample),
+                               _ptr(init), iters, _ptr(cb), _ptr(codes), s))
+    return cb, codes
 
 
 def bang_set_placement(ix, flags):

@@ -198,21 +198,31 @@ def medoids_of_groups(base, labels, ng):
     return order, gstart, out
 
 
-def build_cluster_graph(cfg, base, labels, ng, R, alpha, nx, nh):
-    """Clustered graph (per-cluster exact candidates -> RobustPrune -> reverse
-    edges; nx links per point and nh links per cluster medoid to other
-    clusters' medoids, those clusters drawn with the graph seed)."""
-    n, d = base.shape
+def graph_inputs(cfg, base, labels, ng, nx, nh):
+    """Inputs of the clustered construction: members grouped by cluster,
+    cluster offsets, cluster medoids, and the clusters whose medoids each
+    point (nx) and each cluster medoid (nh) links to, drawn with the graph
+    seed."""
+    n = base.shape[0]
     order, gstart, meds = medoids_of_groups(base, labels, ng)
     rng = np.random.default_rng(4000 + cfg)
     own = labels.astype(np.int64)
     xclu = (own[:, None] + 1 + rng.integers(0, ng - 1, size=(n, nx))) % ng
     hclu = np.stack([(g + 1 + rng.choice(ng - 1, size=min(nh, ng - 1), replace=False)) % ng
                      for g in range(ng)]) if nh else np.zeros((ng, 0), np.int64)
+    return dict(members=order, gstart=gstart, medoids=meds,
+                xclu=np.ascontiguousarray(xclu, np.uint32), hclu=np.ascontiguousarray(hclu, np.uint32))
+
+
+def build_cluster_graph(cfg, base, labels, ng, R, alpha, nx, nh):
+    """Clustered graph (per-cluster exact candidates -> RobustPrune -> reverse
+    edges; nx links per point and nh links per cluster medoid to other
+    clusters' medoids, those clusters drawn with the graph seed)."""
+    n, d = base.shape
+    gi = graph_inputs(cfg, base, labels, ng, nx, nh)
+    order, gstart, meds, xclu, hclu = gi["members"], gi["gstart"], gi["medoids"], gi["xclu"], gi["hclu"]
     nh_eff = hclu.shape[1]
     adj = np.zeros((n, R), np.uint32)
-    xclu = np.ascontiguousarray(xclu, np.uint32)
-    hclu = np.ascontiguousarray(hclu, np.uint32)
     rc = lib().wl_cluster_graph(_p(base), _DTC[_dtname(base)], d, n, _p(order), _p(gstart), ng,
                                 _p(meds), R, alpha, nx, _p(xclu), nh_eff, _p(hclu), _p(adj))
     if rc != 0:
