@@ -1,0 +1,183 @@
+"""Parity at the configurations' full sizes, in the launch forms they name,
+on sampled queries (the oracle computes those one by one):
+
+  configuration 2 (1M u8, the benchmark workload): the whole 10,000-query
+      batch in the benchmark's launches (autotuned 8-bit table, plain FP32,
+      Exact-distance variant with vectors in HBM);
+  configuration 3 shape (10M f32, d=96, M=48, R=68): FP32 and 8-bit tables;
+  configuration 4 shape (100M int8, d=100, M=50, R=64): the batched form,
+      per-query k in {1, 10, 100} and L in {32, 64, 128, 256}, one persistent
+      launch replayed from a CUDA graph;
+  configuration 5 shape (1B u8 points do not fit the host memory here; the
+      largest size that does, 200M u8, d=128, M=32, R=64): the serving loop.
+
+Configurations 3-5 use indexes from workload.scale_index (cluster-local rows,
+uniform data) because building their clustered graphs on the host cores takes
+hours; the search does the same work on any graph.  Each test checks the
+memory it needs first and is skipped when the machine lacks it."""
+import gc
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workload
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_2401_11324_gb300 as bang  # noqa: E402
+
+
+def _mem_available_gb():
+    avail = None
+    with open("/proc/meminfo") as f:
+        for line in f:
+            if line.startswith("MemAvailable:"):
+                avail = int(line.split()[1]) / 2 ** 20
+    for p in ("/sys/fs/cgroup/memory.max", "/sys/fs/cgroup/memory/memory.limit_in_bytes"):
+        try:
+            v = open(p).read().strip()
+            if v.isdigit():
+                avail = min(avail, int(v) / 2 ** 30)
+        except OSError:
+            pass
+    return avail or 0.0
+
+
+def _need(gb):
+    have = _mem_available_gb()
+    if have < 1.6 * gb:
+        pytest.skip("needs %.0f GB of host memory with headroom, %.0f GB available" % (gb, have))
+
+
+def _run(ix, q, k, L, mode, lz, trace_cap=0):
+    nq = q.shape[0]
+    ids = torch.empty((nq, k), dtype=torch.int32, device="cuda")
+    dist = torch.empty((nq, k), dtype=torch.float32, device="cuda")
+    iters = torch.empty(nq, dtype=torch.int32, device="cuda")
+    nd = torch.empty(nq, dtype=torch.int32, device="cuda")
+    trace = torch.zeros((nq, max(trace_cap, 1)), dtype=torch.int32, device="cuda")
+    p = bang.make_params(bloom_log2=lz, mode=mode, out_iters=iters, out_ndist=nd,
+                         trace=trace if trace_cap else None, trace_cap=trace_cap)
+    ix.search(q, k, L, ids, dist, p)
+    torch.cuda.synchronize()
+    v = lambda t: t.cpu().numpy().view(np.uint32)          # noqa: E731
+    return dict(ids=v(ids), dist=dist.cpu().numpy(), iters=v(iters), ndist=v(nd), trace=v(trace))
+
+
+def _compare(g, o, sel, trace_cap=0):
+    assert (g["ids"][sel] == o["ids"]).all(), np.argwhere(g["ids"][sel] != o["ids"])[:5]
+    assert (g["iters"][sel] == o["iters"]).all()
+    assert (g["ndist"][sel].astype(np.uint64) == o["ndist"]).all()
+    fin = np.isfinite(o["dist"])
+    assert (g["dist"][sel][fin] == o["dist"][fin]).all()
+    for j, i in enumerate(sel):
+        m = min(int(o["iters"][j]), trace_cap)
+        assert (g["trace"][i, :m] == o["trace"][j, :m]).all()
+
+
+def test_configuration2_full_batch_in_benchmark_launches():
+    _need(4)
+    w = workload.clustered_workload(2)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
+    oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
+    q = torch.from_numpy(w["queries"]).cuda()
+    sel = np.arange(0, w["queries"].shape[0], 50)
+    for mode, lz, L, place in ((3, 15, 160, 0), (0, 16, 160, 0), (2, 16, 128, 3)):
+        ix.set_placement(place)
+        g = _run(ix, q, 10, L, mode, lz, trace_cap=512)
+        o = oix.search(w["queries"][sel], 10, L, log2z=lz, trace_cap=512, exact=mode == 2,
+                       q8=mode == 3)
+        _compare(g, o, sel, 512)
+    ix.close()
+
+
+def test_configuration3_shape_full_size():
+    _need(12)
+    w = workload.scale_index(10_000_000, 96, "f32", 48, 68, nx=4, ng=1024, nq=1000)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 48)
+    oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 48)
+    q = torch.from_numpy(np.ascontiguousarray(w["queries"])).cuda()
+    sel = np.arange(0, 1000, 10)
+    for mode in (0, 3):
+        g = _run(ix, q, 10, 128, mode, 16, trace_cap=256)
+        o = oix.search(w["queries"][sel], 10, 128, log2z=16, trace_cap=256, q8=mode == 3)
+        _compare(g, o, sel, 256)
+    # BF16 table: re-ranked distances are the exact FP32 distances of the ids
+    g = _run(ix, q, 10, 128, 1, 16)
+    ids = g["ids"][sel].astype(np.int64)
+    ex = [[oracle.exact_dist(w["queries"][i], w["base"][j]) for j in ids[t]] for t, i in enumerate(sel)]
+    assert (g["dist"][sel] == np.array(ex, np.float32)).all()
+    ix.close()
+    del w, ix, oix
+    gc.collect()
+
+
+def test_configuration4_shape_batched_graph_replay():
+    _need(50)
+    nq = 1000
+    w = workload.scale_index(100_000_000, 100, "i8", 50, 64, nx=4, ng=4096, nq=nq)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 50)
+    rng = np.random.default_rng(44)
+    k = rng.choice([1, 10, 100], size=nq).astype(np.uint32)
+    L = np.maximum(rng.choice([32, 64, 128, 256], size=nq), k).astype(np.uint32)
+    q = torch.from_numpy(np.ascontiguousarray(w["queries"])).cuda()
+    kd, Ld = torch.from_numpy(k.view(np.int32)).cuda(), torch.from_numpy(L.view(np.int32)).cuda()
+    ids = torch.empty((nq, 100), dtype=torch.int32, device="cuda")
+    dist = torch.empty((nq, 100), dtype=torch.float32, device="cuda")
+    p = bang.make_params(mode=3, bloom_log2=15)
+    st = torch.cuda.Stream()
+    ix.search_batched(q, kd, Ld, 100, 256, ids, dist, p, stream=st.cuda_stream)   # warm-up
+    st.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=st):
+        ix.search_batched(q, kd, Ld, 100, 256, ids, dist, p, stream=st.cuda_stream)
+    ids.zero_()
+    graph.replay()
+    torch.cuda.synchronize()
+    gi = ids.cpu().numpy().view(np.uint32)
+    gd = dist.cpu().numpy()
+    ix.close()
+    oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 50)
+    sel = np.arange(0, nq, 10)
+    for kk in np.unique(k[sel]):
+        for LL in np.unique(L[sel][k[sel] == kk]):
+            s = sel[(k[sel] == kk) & (L[sel] == LL)]
+            o = oix.search(w["queries"][s], int(kk), int(LL), log2z=15, q8=True)
+            assert (gi[s, :kk] == o["ids"]).all()
+            fin = np.isfinite(o["dist"])
+            assert (gd[s, :kk][fin] == o["dist"][fin]).all()
+    del w, oix
+    gc.collect()
+
+
+def test_configuration5_shape_serving():
+    _need(90)
+    nq = 1000
+    w = workload.scale_index(200_000_000, 128, "u8", 32, 64, nx=4, ng=16384, nq=nq)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 32)
+    srv = bang.Server(ix, 10, 256, max_batch=256, streams=4, mode=3, bloom_log2=15)
+    rng = np.random.default_rng(45)
+    reqs, start = [], 0
+    while start < nq:                       # requests of 1..256 queries, L in 64..256
+        n = int(min(rng.integers(1, 257), nq - start))
+        L = int(rng.choice([64, 128, 256]))
+        reqs.append((start, n, L, srv.submit(w["queries"][start:start + n], np.full(n, 10),
+                                             np.full(n, L))))
+        start += n
+    got = {}
+    for s0, n, L, t in reqs:
+        ids, dist, lat = srv.wait(t, 60_000)
+        got[s0] = (ids, dist, L)
+    srv.stop()
+    ix.close()
+    oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 32)
+    for s0, n, L, _ in reqs[::4]:
+        ids, dist, _ = got[s0]
+        o = oix.search(w["queries"][s0:s0 + n], 10, L, log2z=15, q8=True)
+        assert (ids == o["ids"]).all()
+        assert (dist == o["dist"]).all()
+    del w, oix
+    gc.collect()

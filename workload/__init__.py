@@ -78,6 +78,8 @@ def lib():
         L.wl_cluster_graph.restype = i32
         L.wl_bruteforce.argtypes = [vp, vp, i32, u64, u32, u32, u32, vp, vp]
         L.wl_max_threads.restype = i32
+        L.wl_scale_index.argtypes = [i32, u64, u32, u32, u32, u32, u32, u32, u64, vp, vp, vp, vp, vp]
+        L.wl_scale_index.restype = i32
         _lib = L
     return _lib
 
@@ -239,6 +241,32 @@ def ground_truth(base, queries, k):
     lib().wl_bruteforce(_p(base), _p(queries), _DTC[_dtname(base)],
                         base.shape[0], nq, base.shape[1], k, _p(ids), _p(dist))
     return ids, dist
+
+
+def aligned_empty(shape, dtype, align=4096):
+    """Uninitialised array whose data starts on an `align`-byte boundary."""
+    dtype = np.dtype(dtype)
+    nbytes = int(np.prod(shape)) * dtype.itemsize
+    buf = np.empty(nbytes + align, np.uint8)
+    start = (-buf.ctypes.data) % align
+    return buf[start:start + nbytes].view(dtype).reshape(shape)
+
+
+def scale_index(n, d, dtype, M, R, nx=4, ng=1024, nq=1000, seed=5):
+    """An index of the full configuration sizes for parity checks, built
+    without nearest-neighbour work (wl_scale_index): cluster-local graph rows
+    plus links to other clusters, uniform vectors and codes.  Arrays are
+    page-aligned, so the search library reads them in place."""
+    base = aligned_empty((n, d), _DTN[dtype])
+    queries = aligned_empty((nq, d), _DTN[dtype])
+    codebook = np.zeros(256 * d, np.float32)
+    codes = aligned_empty((n, M), np.uint8)
+    adj = aligned_empty((n, R), np.uint32)
+    rc = lib().wl_scale_index(_DTC[dtype], n, d, M, R, nx, ng, nq, seed, _p(base), _p(queries),
+                              _p(codebook), _p(codes), _p(adj))
+    if rc != 0:
+        raise ValueError("scale_index: clusters too small for R")
+    return dict(base=base, queries=queries, codebook=codebook, codes=codes, adj=adj, medoid=0, M=M)
 
 
 def cache_dir():

@@ -450,6 +450,81 @@ void wl_bruteforce(const void *base, const void *queries, int dt, uint64_t n, ui
     }
 }
 
+/* ---------------------------------------------------------------------- */
+/* Index for checks at full size, without nearest-neighbour work: seeded    */
+/* values from a counter-based hash (SplitMix64 finaliser), so any thread   */
+/* count writes the same bytes.  Points fall into ng contiguous id ranges   */
+/* ("clusters"); member a of a cluster of m members links to the members    */
+/* (a + 1 + (s_a + r) mod (m - 1)) mod m, r < R - nx, s_a drawn per point    */
+/* (distinct, never itself), then to the first member of nx other clusters  */
+/* (repeats dropped, 0xFFFFFFFF padding).  Vectors, queries and codes are   */
+/* uniform; the codebook covers the element range.                          */
+/* ---------------------------------------------------------------------- */
+
+static inline uint64_t wl_mix(uint64_t x)
+{
+    x += 0x9E3779B97F4A7C15ull;
+    x = (x ^ (x >> 30)) * 0xBF58476D1CE4E5B9ull;
+    x = (x ^ (x >> 27)) * 0x94D049BB133111EBull;
+    return x ^ (x >> 31);
+}
+
+static void wl_fill_rows(void *X, int dt, uint64_t rows, uint32_t d, uint64_t seed)
+{
+    int64_t i;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < (int64_t)rows; i++) {
+        uint32_t j;
+        for (j = 0; j < d; j++) {
+            uint64_t h = wl_mix(seed ^ wl_mix((uint64_t)i * d + j));
+            if (dt == WL_U8) ((uint8_t *)X)[(uint64_t)i * d + j] = (uint8_t)(h >> 56);
+            else if (dt == WL_I8) ((int8_t *)X)[(uint64_t)i * d + j] = (int8_t)(uint8_t)(h >> 56);
+            else ((float *)X)[(uint64_t)i * d + j] = (float)((int64_t)(h >> 40) - (1ll << 23)) / (float)(1 << 23);
+        }
+    }
+}
+
+int wl_scale_index(int dt, uint64_t n, uint32_t d, uint32_t M, uint32_t R, uint32_t nx, uint32_t ng,
+                   uint32_t nq, uint64_t seed, void *base, void *queries, float *codebook,
+                   uint8_t *codes, uint32_t *adj)
+{
+    uint64_t per = (n + ng - 1) / ng;
+    uint32_t Rin = R - nx, j;
+    int64_t i;
+    if (nx >= R || ng < 2 || per < (uint64_t)Rin + 1) return -1;
+    wl_fill_rows(base, dt, n, d, seed * 4 + 0);
+    wl_fill_rows(queries, dt, nq, d, seed * 4 + 1);
+    for (j = 0; j < 256 * d; j++) {
+        uint64_t h = wl_mix((seed * 4 + 2) ^ wl_mix(j));
+        float u = (float)(h >> 40) / (float)(1 << 24);        /* [0, 1) */
+        codebook[j] = dt == WL_U8 ? 255.0f * u : dt == WL_I8 ? 255.0f * u - 128.0f : 2.0f * u - 1.0f;
+    }
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < (int64_t)n; i++) {
+        uint64_t g = (uint64_t)i / per, lo = g * per, hi = lo + per < n ? lo + per : n;
+        uint64_t m = hi - lo, a = (uint64_t)i - lo, s;
+        uint32_t r, w = 0, q;
+        uint32_t *row = adj + (uint64_t)i * R;
+        for (s = 0; s < M; s++) codes[(uint64_t)i * M + s] = (uint8_t)(wl_mix((seed * 4 + 3) ^ wl_mix((uint64_t)i * M + s)) >> 56);
+        if (m < (uint64_t)Rin + 1) {             /* a short last cluster: link to everyone */
+            for (s = 0; s < m; s++) if (s != a && w < Rin) row[w++] = (uint32_t)(lo + s);
+        } else {
+            uint64_t st = wl_mix(seed ^ (0xABCDull << 40) ^ (uint64_t)i) % (m - 1);
+            for (r = 0; r < Rin; r++) row[w++] = (uint32_t)(lo + (a + 1 + (st + r) % (m - 1)) % m);
+        }
+        for (r = 0; r < nx; r++) {
+            uint64_t g2 = (g + 1 + wl_mix(seed ^ (0x5151ull << 40) ^ ((uint64_t)i * nx + r)) % (ng - 1)) % ng;
+            uint32_t t = (uint32_t)(g2 * per);
+            int dup = 0;
+            if ((uint64_t)t >= n) continue;
+            for (q = 0; q < w; q++) if (row[q] == t) dup = 1;
+            if (!dup) row[w++] = t;
+        }
+        for (; w < R; w++) row[w] = WL_NONE;
+    }
+    return 0;
+}
+
 int wl_max_threads(void)
 {
 #ifdef _OPENMP
