@@ -104,9 +104,16 @@ struct SmemLayout {
         off_Nk = o;     o += up16(rw * 8u);
         off_Nid = o;    o += up16(rw * 4u);
         off_Ck = o;     o += up16(k > (uint32_t)kRegK && mode != kModeExact ? k * 8u : 0u);
-        off_q = o;      o += up16(mode != kModeExact ? d * 4u : 0u);
-        off_offs = o;   o += up16((M + 1u) * 4u);
-        off_lo = o;     o += up16(mode == kModeQ8 ? M * 4u : 0u);
+        // table-build scratch (query, subspace offsets, 8-bit-table minima):
+        // dead once the table is built, so it shares the worklist's space
+        // when that is large enough
+        const uint32_t sq = up16(mode != kModeExact ? d * 4u : 0u), so = up16((M + 1u) * 4u),
+                       sl = up16(mode == kModeQ8 ? M * 4u : 0u);
+        uint32_t b = up16(L * 8u) >= sq + so + sl ? off_L : o;
+        off_q = b;      b += sq;
+        off_offs = b;   b += so;
+        off_lo = b;     b += sl;
+        if (off_q != off_L) o = b;
         total = o;
     }
 };
@@ -492,8 +499,6 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     const uint32_t zmask = (1u << a.log2z) - 1u;
     const uint32_t nwords = (1u << a.log2z) >= 32u ? (1u << a.log2z) / 32u : 1u;
 
-    for (uint32_t i = lane; i <= a.M; i += kWarp) offs[i] = a.off[i];
-
     uint32_t next_static = blockIdx.x;
     for (;;) {
         // ---- next query: from the work counter (persistent launch) or by grid stride
@@ -529,8 +534,10 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         const unsigned long long t_start = clk.t;
         // ---- query: FP32 copy in shared memory, this lane's share in registers
         const E *qp = static_cast<const E *>(a.queries) + static_cast<uint64_t>(q) * d;
-        if (kPQ)
+        if (kPQ) {
             for (uint32_t j = lane; j < d; j += kWarp) qv[j] = static_cast<float>(qp[j]);
+            for (uint32_t i = lane; i <= a.M; i += kWarp) offs[i] = a.off[i];
+        }
         VecShare<DT, DCH> qs;
         load_share<DT, DCH>(qp, d, a.vec_ok != 0, lane, qs);
         for (uint32_t w = lane; w < nwords; w += kWarp) bloom[w] = 0u;
@@ -593,7 +600,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 cur = u;
                 load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
             }
-            const VecShare<DT, DCH> xu = nd.x;   // u*'s vector, for the re-rank below (PQ modes)
+            VecShare<DT, DCH> xu;                // u*'s vector, for the re-rank below (PQ modes)
             clk.mark(kPhSelect);
 
             // ---- filter seen neighbours, §4.3: test all, then insert all
@@ -681,6 +688,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 // the best new neighbour can still fall off the end of a full
                 // worklist of expanded entries; whether a next node exists is
                 // settled by the merge below
+                if (kPQ) xu = nd.x;              // wait for the vector only here
                 if (best != ~0ull) {
                     cur = key_id(best);
                     load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
