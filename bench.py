@@ -304,8 +304,8 @@ def run_reference(args):
 # kernel version at the default workload, keyed by (mode, bloom_log2, L):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and host-memory
 # bytes (32-byte sysmem read sectors).  Cleared whenever the kernel changes.
-NCU_TRAFFIC = {(3, 15, 160): 33478400 + 0}
-NCU_HOST_TRAFFIC = {(3, 15, 160): 24429028 * 32}
+NCU_TRAFFIC = {(3, 15, 160): 33477888 + 0}
+NCU_HOST_TRAFFIC = {(3, 15, 160): 24410000 * 32}
 
 FORMS = {
     # name: (distance mode, placement flags, what it is)
