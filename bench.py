@@ -301,11 +301,11 @@ def run_reference(args):
 
 
 # Traffic per launch of the head kernel from one ncu capture of the current
-# kernel version at the default workload, keyed by (mode, bloom_log2, L):
+# kernel version at the default workload, keyed by (mode, bloom_log2, L, placement):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and host-memory
 # bytes (32-byte sysmem read sectors).  Cleared whenever the kernel changes.
-NCU_TRAFFIC = {(3, 15, 160): 33477888 + 0}
-NCU_HOST_TRAFFIC = {(3, 15, 160): 24410000 * 32}
+NCU_TRAFFIC = {(3, 15, 160, 0): 33477888 + 0}
+NCU_HOST_TRAFFIC = {(3, 15, 160, 0): 24410000 * 32}
 
 FORMS = {
     # name: (distance mode, placement flags, what it is)
@@ -409,13 +409,15 @@ def main():
             place(flags)
             L, sweep = operating_point(mode, tsrc)
         else:                       # settings chosen by bang_autotune
-            mode, tsrc, lz, L, flags, sweep = (tune["mode"], tune["table_source"],
-                                               tune["bloom_log2"], tune["L"],
-                                               tune.get("placement", 0), [])
+            mode, tsrc, lz, L, sweep = (tune["mode"], tune["table_source"], tune["bloom_log2"],
+                                        tune["L"], [])
+            flags = tune.get("placement", 0) | (bang.BANG_GRAPH_PACKED if tune["graph_packed"] else 0)
             what = ("autotuned (bang_autotune): %s table%s, Bloom filter 2^%d bits, smallest L "
-                    "reaching recall@%d 0.9" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
-                                                " from the tensor cores" if tsrc else "", lz, K))
-            if flags:
+                    "reaching recall@%d 0.9%s" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
+                                                  " from the tensor cores" if tsrc else "", lz, K,
+                                                  ", graph rows packed to %d-bit ids" % tune["adj_bits"]
+                                                  if tune["graph_packed"] else ""))
+            if flags & (bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
                 what = "In-memory variant (§5.1), graph and vectors in HBM, with the " + what
             place(flags)
         search(L, mode, with_stats=True, tsrc=tsrc, lz=lz)
@@ -443,7 +445,8 @@ def main():
             try:
                 tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
                                    target_recall=TARGET_RECALL, bloom_min=14, bloom_max=19,
-                                   stream=sptr)
+                                   try_packed_graph=1, stream=sptr)
+                tune["adj_bits"] = int(np.ceil(np.log2(w["base"].shape[0] + 1)))
             except bang.BangError as e:        # no setting reaches the target within L <= 1024
                 tune = {"failed": str(e)}
             tune["seconds"] = round(time.perf_counter() - t0, 2)
@@ -456,7 +459,7 @@ def main():
     if tune is not None and "failed" not in tune:
         variants["in_memory_autotuned"] = measure("in_memory_autotuned", max(5, args.steps // 5),
                                                   dict(tune, placement=3))
-    place(0)
+    place(head["placement"])
     L, mode, tsrc, lz = head["L"], head["mode"], head["tsrc"], head["lz"]
     it, nd = head["iters"], head["ndist"]
 
@@ -471,7 +474,11 @@ def main():
 
     # ---- algorithmic bytes per launch (one launch = the whole batch)
     esz = w["base"].dtype.itemsize
-    host_bytes = int(it.sum()) * (R * 4 + d * esz)         # neighbour row + full vector per expansion
+    row_bytes = R * 4
+    if head["placement"] & bang.BANG_GRAPH_PACKED:          # ids packed to the fewest bits
+        b = int(np.ceil(np.log2(w["base"].shape[0] + 1)))
+        row_bytes = ((R * b + 31) // 32 + 7) // 8 * 8 * 4
+    host_bytes = int(it.sum()) * (row_bytes + d * esz)     # neighbour row + full vector per expansion
     hbm_bytes = int(nd.sum()) * M + nq * d * esz + nq * K * 8 + 256 * d * 4
     launch_s = head["launch_s"]
 
@@ -519,18 +526,20 @@ def main():
         "forms": {f: brief(r) for f, r in list(res.items()) + list(variants.items())},
         "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": hbm_gbs / hbm_peak,
-                     "traffic": NCU_TRAFFIC.get((mode, lz, L)) if args.n is None else None,
+                     "traffic": NCU_TRAFFIC.get((mode, lz, L, head["placement"])) if args.n is None else None,
                      "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                      "algorithmic_bytes_per_launch": hbm_bytes},
         "host_link": {"bound": "host_link", "achieved": host_bytes / launch_s / 1e9,
                       "peak": link["gather_gbs"], "unit": "GB/s",
                       "frac": host_bytes / launch_s / 1e9 / link["gather_gbs"],
-                      "traffic": NCU_HOST_TRAFFIC.get((mode, lz, L)) if args.n is None else None,
+                      "traffic": NCU_HOST_TRAFFIC.get((mode, lz, L, head["placement"])) if args.n is None
+                      else None,
                       "peak_source": "measured in this run: random %d-byte row gathers in place "
                                      "from mapped host memory" % link["gather_row_bytes"],
                       "copy_engine_gbs": link["h2d_copy_gbs"],
                       "load_latency_ns": link["latency_ns"],
                       "algorithmic_bytes_per_launch": host_bytes,
+                      "row_bytes": row_bytes,
                       "note": "binding link: neighbour rows and full vectors read in place from "
                               "page-locked host memory"},
         "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d * esz,

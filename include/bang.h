@@ -99,7 +99,7 @@ typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,
                BANG_MODE_PQ_Q8 = 3 } bang_mode;
 
 /* Placement flags for bang_set_placement. */
-enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2 };
+enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2, BANG_GRAPH_PACKED = 4 };
 
 /* Create an empty index bound to CUDA device `device`.  *out receives an
  * opaque handle owned by the library; free it with bang_destroy. */
@@ -214,7 +214,15 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
  * (the paper's In-memory variant, §5.1; BANG_MODE_EXACT usually wants the
  * vectors there too).  The copies are owned by the library and dropped when
  * the corresponding array is registered again or the flag is cleared.
- * Blocks until the copies are done.  BANG_ENOMEM if the device is full. */
+ * BANG_GRAPH_PACKED (not in the paper, whose rows hold 32-bit ids) makes the
+ * search read a copy of the graph with every id packed into b bits, b the
+ * fewest with 2^b - 1 >= n (the all-ones value marks an empty slot), rows
+ * padded to 32 bytes: 160 bytes instead of 256 per row at n = 1M, R = 64, so
+ * fewer bytes cross the host link per expansion (in HBM with
+ * BANG_GRAPH_IN_HBM).  The copy is page-locked host memory owned by the
+ * index, built once from the registered rows; results are unchanged.
+ * Blocks until the copies are done.  BANG_ENOMEM if the device or the host
+ * memory is full. */
 int bang_set_placement(bang_index *ix, uint32_t flags);
 
 /* PQ distance tables of nq queries on the tensor cores (§4.1 as a dense
@@ -293,8 +301,9 @@ int bang_build_pq(int device, const void *base, bang_dtype dtype, uint64_t n, ui
  * settings that change speed but not the method: the PQ table's precision
  * (bang_mode; bit m of `modes` admits mode m), whether mode 1's tables come
  * from the tensor cores (table_source), the Bloom filter size 2^bloom_log2
- * (the paper's z, §4.3) and, for the batched form, the persistent grid
- * multiple.  Every candidate searches the given queries on `stream`; its
+ * (the paper's z, §4.3), for the batched form the persistent grid
+ * multiple, and optionally whether the graph rows are packed
+ * (BANG_GRAPH_PACKED; the index's placement is restored on return).  Every candidate searches the given queries on `stream`; its
  * accuracy is recall@k against `truth` (host, nq*k ids; 0xFFFFFFFF entries
  * are skipped) or, when truth is NULL, against an FP32 search with worklist
  * 2L (at most 1024) and a 2^18-bit filter.  Speed is the mean of `reps`
@@ -322,6 +331,7 @@ typedef struct bang_autotune_opts {
     float target_recall;         /* 0: fixed L; else the recall to reach */
     float recall_tolerance;      /* fixed L: allowed recall loss; 0 = 0.005 */
     const char *cache_path;      /* JSON-lines decision cache, or NULL */
+    uint32_t try_packed_graph;   /* also try BANG_GRAPH_PACKED rows */
 } bang_autotune_opts;
 
 typedef struct bang_autotune_result {
@@ -330,6 +340,7 @@ typedef struct bang_autotune_result {
     float ref_ms, ref_recall;    /* FP32 form, 2^16-bit filter */
     uint32_t candidates;         /* candidates evaluated */
     uint32_t from_cache;         /* 1 when read from cache_path */
+    uint32_t graph_packed;       /* 1: the choice reads packed rows (set the flag) */
 } bang_autotune_result;
 
 int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,

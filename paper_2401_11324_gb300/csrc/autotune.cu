@@ -2,8 +2,9 @@
 // computes, only how fast and how accurately this GPU runs it: the PQ table's
 // precision and where it is built (§4.1: FP32, BF16 or 8-bit; per warp or on
 // the tensor cores for the whole batch), the Bloom filter's size (§4.3, the
-// paper's z), the persistent grid of the batched form, and optionally the
-// worklist size L that reaches a target recall.  Candidates are timed with
+// paper's z), the persistent grid of the batched form, whether the graph rows
+// are read packed, and optionally the worklist size L that reaches a target
+// recall.  Candidates are timed with
 // CUDA events on the caller's stream and judged by recall@k against the
 // caller's ground truth or, without one, against a high-accuracy FP32 search
 // (2L, Bloom 2^18).  Decisions can be cached as JSON lines keyed by the GPU
@@ -26,7 +27,7 @@
 namespace {
 
 struct Cfg {
-    uint32_t mode, log2z, tsrc, grid_mult, L;
+    uint32_t mode, log2z, tsrc, grid_mult, L, packed;
 };
 
 struct Runner {
@@ -149,6 +150,7 @@ std::string cache_key(bang_index *ix, uint32_t nq, uint32_t k, uint32_t L, const
       << "|nq=" << nq << "|k=" << k << "|L=" << L << "|target=" << o.target_recall
       << "|tol=" << o.recall_tolerance << "|modes=" << o.modes << "|bloom=" << o.bloom_min << "-"
       << o.bloom_max << "|tc=" << o.try_tensor_tables << "|batched=" << o.batched
+      << "|packed=" << o.try_packed_graph
       << "|truth=" << (truth ? 1 : 0);
     std::string r = s.str();
     for (char &c : r)
@@ -175,10 +177,10 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     while (std::getline(f, line))
         if (line.compare(0, kpat.size(), kpat) == 0) hit = line;    // the last entry wins
     if (hit.empty()) return false;
-    double v[10];
-    const char *names[10] = {"mode", "bloom_log2", "table_source", "grid_mult", "L",
-                             "ms", "recall", "ref_ms", "ref_recall", "candidates"};
-    for (int i = 0; i < 10; ++i)
+    double v[11];
+    const char *names[11] = {"mode", "bloom_log2", "table_source", "grid_mult", "L",
+                             "ms", "recall", "ref_ms", "ref_recall", "candidates", "graph_packed"};
+    for (int i = 0; i < 11; ++i)
         if (!field(hit, names[i], &v[i])) return false;
     out->mode = static_cast<uint32_t>(v[0]);
     out->bloom_log2 = static_cast<uint32_t>(v[1]);
@@ -190,6 +192,7 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     out->ref_ms = static_cast<float>(v[7]);
     out->ref_recall = static_cast<float>(v[8]);
     out->candidates = static_cast<uint32_t>(v[9]);
+    out->graph_packed = static_cast<uint32_t>(v[10]);
     out->from_cache = 1;
     return true;
 }
@@ -203,9 +206,9 @@ void store(const char *path, const std::string &key, const bang_autotune_result 
     std::snprintf(buf, sizeof buf,
                   "\"mode\": %u, \"bloom_log2\": %u, \"table_source\": %u, \"grid_mult\": %u, "
                   "\"L\": %u, \"ms\": %.6g, \"recall\": %.6g, \"ref_ms\": %.6g, \"ref_recall\": %.6g, "
-                  "\"candidates\": %u}",
+                  "\"candidates\": %u, \"graph_packed\": %u}",
                   r.mode, r.bloom_log2, r.table_source, r.grid_mult, r.L, r.ms, r.recall, r.ref_ms,
-                  r.ref_recall, r.candidates);
+                  r.ref_recall, r.candidates, r.graph_packed);
     f << "{\"key\": \"" << key << "\", " << buf << "\n";
 }
 
@@ -265,30 +268,40 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
         const uint32_t Lr = std::min(1024u, std::max(2u * L_hi, k));
         Runner wide{ix, queries, nq, k, false, static_cast<cudaStream_t>(stream)};
         if ((rc = wide.init(Lr))) return tfail(rc, "bang_autotune: scratch allocation failed");
-        if ((rc = wide.run({BANG_MODE_PQ_F32, 18u, 0u, 0u, Lr})) || (rc = wide.fetch())) return rc;
+        if ((rc = wide.run({BANG_MODE_PQ_F32, 18u, 0u, 0u, Lr, 0u})) || (rc = wide.fetch())) return rc;
         pseudo = wide.ids;
         ref_ids = pseudo.data();
     }
 
     // candidates
     std::vector<Cfg> cands;
-    for (uint32_t m = 0; m < 4; ++m) {
-        if (!(o.modes & (1u << m))) continue;
-        for (uint32_t z = o.bloom_min; z <= o.bloom_max; ++z) {
-            std::vector<uint32_t> gms = {0u};
-            if (o.batched) gms = {1u, 2u, 4u};
-            for (uint32_t gm : gms) {
-                cands.push_back({m, z, 0u, gm, 0u});
-                if (m == BANG_MODE_PQ_BF16 && o.try_tensor_tables) cands.push_back({m, z, 1u, gm, 0u});
+    for (uint32_t pk = 0; pk < (o.try_packed_graph ? 2u : 1u); ++pk)
+        for (uint32_t m = 0; m < 4; ++m) {
+            if (!(o.modes & (1u << m))) continue;
+            for (uint32_t z = o.bloom_min; z <= o.bloom_max; ++z) {
+                std::vector<uint32_t> gms = {0u};
+                if (o.batched) gms = {1u, 2u, 4u};
+                for (uint32_t gm : gms) {
+                    cands.push_back({m, z, 0u, gm, 0u, pk});
+                    if (m == BANG_MODE_PQ_BF16 && o.try_tensor_tables) cands.push_back({m, z, 1u, gm, 0u, pk});
+                }
             }
         }
-    }
+    // the caller's placement, restored on every way out; packed rows are a
+    // candidate dimension
+    const uint32_t place0 = bang::index_placement(ix);
+    struct Restore {
+        bang_index *ix;
+        uint32_t flags;
+        ~Restore() { if (bang::index_placement(ix) != flags) bang_set_placement(ix, flags); }
+    } restore{ix, place0};
+    uint32_t cur_packed = (place0 & BANG_GRAPH_PACKED) ? 1u : 0u;
 
     // the plain form at the default filter: the reference for the tolerance
     // (fixed L) and for the reported speed-up
     float ref_ms = 0.f, ref_acc = 0.f;
     {
-        Cfg c{BANG_MODE_PQ_F32, 16u, 0u, o.batched ? 1u : 0u, Ls[0]};
+        Cfg c{BANG_MODE_PQ_F32, 16u, 0u, o.batched ? 1u : 0u, Ls[0], cur_packed};
         if (o.target_recall > 0.f) {
             for (uint32_t Lc : Ls) {
                 c.L = Lc;
@@ -306,6 +319,11 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
     bool found = false;
     uint32_t tried = 0;
     for (Cfg c : cands) {
+        if (o.try_packed_graph && c.packed != cur_packed) {
+            const uint32_t fl = c.packed ? (place0 | BANG_GRAPH_PACKED) : (place0 & ~(uint32_t)BANG_GRAPH_PACKED);
+            if ((rc = bang_set_placement(ix, fl))) return rc;
+            cur_packed = c.packed;
+        }
         bool ok = false;
         float acc = 0.f;
         for (uint32_t Lc : Ls) {
@@ -331,6 +349,7 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
             out->L = c.L;
             out->ms = ms;
             out->recall = acc;
+            out->graph_packed = cur_packed;
         }
     }
     out->ref_ms = ref_ms;

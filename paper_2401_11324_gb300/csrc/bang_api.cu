@@ -206,6 +206,10 @@ struct bang_index {
     uint32_t *off = nullptr;
     uint8_t *codes = nullptr;
     HostView adj, base;
+    // Packed graph rows (BANG_GRAPH_PACKED): ids of adj_bits bits, rows of
+    // adj_row_words words, page-locked and owned by the index.
+    HostView adj_packed;
+    uint32_t adj_bits = 0, adj_row_words = 0;
     bool have_pq = false, have_graph = false, have_vectors = false;
     DevBuf staging;
     // In-memory placement (§5.1): device copies of the graph and/or vectors.
@@ -342,6 +346,69 @@ bool validate_graph(const uint32_t *adj, uint64_t n, uint32_t R, uint64_t *bad_r
     return true;
 }
 
+// Packs the registered rows: b = the fewest bits with 2^b - 1 >= n (the
+// all-ones value marks an empty slot), rows rounded up to 8 words (32 bytes)
+// so that every row starts on a sector boundary.
+int build_packed_rows(bang_index *ix)
+{
+    if (ix->adj_packed.host) return BANG_OK;
+    uint32_t b = 1;
+    while (((1ull << b) - 1ull) < ix->n) ++b;
+    if (b > 31) return fail(BANG_EINVAL, "bang_set_placement: ids need more than 31 bits");
+    const uint32_t words = ((ix->R * b + 31u) / 32u + 7u) & ~7u;
+    const size_t bytes = (size_t)ix->n * words * 4u;
+    void *h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BANG_ENOMEM, "packed graph rows: %zu bytes of page-locked memory: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    const uint32_t *src = static_cast<const uint32_t *>(ix->adj.host);
+    const uint64_t n = ix->n;
+    const uint32_t R = ix->R, mask = (1u << b) - 1u;
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([=]() {
+            for (uint64_t i = n * t / nt; i < n * (t + 1) / nt; ++i) {
+                uint32_t *out = static_cast<uint32_t *>(h) + i * words;
+                std::memset(out, 0, words * 4u);
+                for (uint32_t r = 0; r < R; ++r) {
+                    const uint32_t v = src[i * R + r] == bang::kNone ? mask : src[i * R + r];
+                    const uint64_t bit = (uint64_t)r * b;
+                    const uint32_t wi = (uint32_t)(bit >> 5), o = (uint32_t)(bit & 31u);
+                    out[wi] |= v << o;
+                    if (o + b > 32u) out[wi + 1] |= v >> (32u - o);
+                }
+            }
+        });
+    for (auto &x : th) x.join();
+    void *dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, h, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+    }
+    ix->adj_packed.host = h;
+    ix->adj_packed.dev = dp;
+    ix->adj_packed.copied = true;
+    ix->adj_bits = b;
+    ix->adj_row_words = words;
+    return BANG_OK;
+}
+
+// Where and how the kernel reads the graph rows.
+void set_graph_args(const bang_index *ix, bang::SearchArgs &a)
+{
+    const bool pk = (ix->placement & BANG_GRAPH_PACKED) != 0;
+    if (ix->placement & BANG_GRAPH_IN_HBM) a.adj = static_cast<const uint32_t *>(ix->adj_hbm.p);
+    else a.adj = static_cast<const uint32_t *>(pk ? ix->adj_packed.dev : ix->adj.dev);
+    a.adj_bits = pk ? ix->adj_bits : 0u;
+    a.adj_row_words = pk ? ix->adj_row_words : ix->R;
+}
+
 }  // namespace
 
 extern "C" {
@@ -429,7 +496,9 @@ int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_
     if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
     ix->adj.release();
     ix->adj_hbm.release();
-    ix->placement &= ~(uint32_t)BANG_GRAPH_IN_HBM;
+    ix->adj_packed.release();
+    ix->adj_bits = ix->adj_row_words = 0;
+    ix->placement &= ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED);
     ix->have_graph = false;
     int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->adj);
     if (rc) return rc;
@@ -587,7 +656,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.codebook = ix->codebook;
     a.off = ix->off;
     a.codes = ix->codes;
-    a.adj = static_cast<const uint32_t *>((ix->placement & BANG_GRAPH_IN_HBM) ? ix->adj_hbm.p : ix->adj.dev);
+    set_graph_args(ix, a);
     a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
     a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
     a.medoid = ix->medoid;
@@ -700,19 +769,26 @@ int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M,
 int bang_set_placement(bang_index *ix, uint32_t flags)
 {
     if (!ix) return fail(BANG_EINVAL, "bang_set_placement: index is NULL");
-    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM))
+    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM | BANG_GRAPH_PACKED))
         return fail(BANG_EINVAL, "bang_set_placement: unknown flags 0x%x", flags);
-    if ((flags & BANG_GRAPH_IN_HBM) && !ix->have_graph)
+    if ((flags & (BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED)) && !ix->have_graph)
         return fail(BANG_ESTATE, "bang_set_placement: register the graph first");
     if ((flags & BANG_VECTORS_IN_HBM) && !ix->have_vectors)
         return fail(BANG_ESTATE, "bang_set_placement: register the vectors first");
     DeviceGuard g(ix->device);
     if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
     CUDA_TRY(cudaDeviceSynchronize());
+    if (flags & BANG_GRAPH_PACKED) {
+        const int rc = build_packed_rows(ix);
+        if (rc) return rc;
+    }
     if (flags & BANG_GRAPH_IN_HBM) {
-        const size_t bytes = (size_t)ix->n * ix->R * sizeof(uint32_t);
+        const bool pk = (flags & BANG_GRAPH_PACKED) != 0;
+        const size_t bytes = (size_t)ix->n * (pk ? ix->adj_row_words : ix->R) * sizeof(uint32_t);
+        ix->adj_hbm.release();
         CUDA_TRY(ix->adj_hbm.ensure(bytes));
-        CUDA_TRY(cudaMemcpy(ix->adj_hbm.p, ix->adj.host, bytes, cudaMemcpyHostToDevice));
+        CUDA_TRY(cudaMemcpy(ix->adj_hbm.p, pk ? ix->adj_packed.host : ix->adj.host, bytes,
+                            cudaMemcpyHostToDevice));
     } else {
         ix->adj_hbm.release();
     }
@@ -736,6 +812,7 @@ int bang_destroy(bang_index *ix)
         if (ix->off) cudaFree(ix->off);
         if (ix->codes) cudaFree(ix->codes);
         ix->adj.release();
+        ix->adj_packed.release();
         ix->base.release();
         ix->staging.release();
         ix->adj_hbm.release();
@@ -894,7 +971,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.codebook = ix->codebook;
     a.off = ix->off;
     a.codes = ix->codes;
-    a.adj = static_cast<const uint32_t *>((ix->placement & BANG_GRAPH_IN_HBM) ? ix->adj_hbm.p : ix->adj.dev);
+    set_graph_args(ix, a);
     a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
     a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
     a.medoid = ix->medoid;

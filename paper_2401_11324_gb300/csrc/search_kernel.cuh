@@ -58,7 +58,9 @@ struct SearchArgs {
     const float *codebook;    // device, 256*d
     const uint32_t *off;      // device, M+1
     const uint8_t *codes;     // device, n*Mpad
-    const uint32_t *adj;      // device-accessible (mapped host), n*R
+    const uint32_t *adj;      // device-accessible (mapped host), n rows of adj_row_words words
+    uint32_t adj_bits;        // 0: rows of R ids; else ids packed to adj_bits bits, all ones = none
+    uint32_t adj_row_words;   // 32-bit words per row (R when not packed)
     const void *base;         // device-accessible (mapped host), n*d
     uint32_t n, d, M, Mpad, R, medoid;
     uint32_t nq, k, L, log2z, iter_cap;
@@ -338,15 +340,45 @@ __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int l
                                           NodeData<DT, RPL, DCH> &nd)
 {
     using E = typename Elem<DT>::T;
-    const uint32_t *row = a.adj + static_cast<uint64_t>(u) * a.R;
+    const uint32_t W = a.adj_bits ? a.adj_row_words : a.R;     // words per row
+    const uint32_t *row = a.adj + static_cast<uint64_t>(u) * W;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
-        nd.nb[r] = i < a.R ? row[i] : kNone;
+        nd.nb[r] = i < W ? row[i] : kNone;
     }
     if (WITH_VECTOR) {
         const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
         load_share<DT, DCH>(x, a.d, a.vecb_ok != 0, lane, nd.x);
+    }
+}
+
+// Packed rows: neighbour r occupies bits [r*b, r*b + b) of the row's word
+// stream (little-endian), all ones meaning an empty slot.  Lane l holds words
+// l + 32 t in nb[t]; each lane gathers the two words its ids straddle with
+// shuffles and leaves ids (or kNone) in nb.
+template <int RPL>
+__device__ __forceinline__ void unpack_ids(const SearchArgs &a, int lane, uint32_t (&nb)[RPL])
+{
+    if (!a.adj_bits) return;
+    const uint32_t b = a.adj_bits, mask = (1u << b) - 1u;
+    uint32_t w[RPL];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) w[t] = nb[t];
+#pragma unroll
+    for (int t = 0; t < RPL; ++t) {
+        const uint32_t r = static_cast<uint32_t>(lane + kWarp * t);
+        const uint32_t bit = r * b, wi = bit >> 5, o = bit & 31u;
+        uint32_t lo = 0, hi = 0;
+#pragma unroll
+        for (int s = 0; s < RPL; ++s) {
+            const uint32_t v0 = __shfl_sync(0xFFFFFFFFu, w[s], static_cast<int>(wi & 31u));
+            const uint32_t v1 = __shfl_sync(0xFFFFFFFFu, w[s], static_cast<int>((wi + 1u) & 31u));
+            if (static_cast<uint32_t>(s) == (wi >> 5)) lo = v0;
+            if (static_cast<uint32_t>(s) == ((wi + 1u) >> 5)) hi = v1;
+        }
+        const uint32_t v = ((lo >> o) | (o ? hi << (32u - o) : 0u)) & mask;
+        nb[t] = (r < a.R && v != mask) ? v : kNone;
     }
 }
 
@@ -603,6 +635,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             VecShare<DT, DCH> xu;                // u*'s vector, for the re-rank below (PQ modes)
             clk.mark(kPhSelect);
 
+            unpack_ids<RPL>(a, lane, nd.nb);
             // ---- filter seen neighbours, §4.3: test all, then insert all
             bool fresh[RPL];
             uint32_t p1[RPL], p2[RPL];

@@ -75,6 +75,16 @@ def test_batched_grid(setup):
     assert r["grid_mult"] in (1, 2, 4) and r["mode"] == 1
 
 
+def test_packed_rows_as_a_candidate(setup):
+    w, ix, q = setup
+    truth = np.ascontiguousarray(w["gt_ids"][:, :10])
+    r = ix.autotune(q, 10, 64, truth=truth, modes=(1 << 3), bloom_min=15, bloom_max=15,
+                    try_packed_graph=1)
+    assert r["graph_packed"] in (0, 1) and r["candidates"] == 2
+    # the index's own placement is back: unpacked results as before
+    assert abs(_recall_with(ix, q, w, r) - r["recall"]) < 1e-6
+
+
 def test_rejects_bad_options(setup):
     w, ix, q = setup
     for kw in (dict(target_recall=1.5), dict(bloom_min=17, bloom_max=14), dict(modes=1 << 7)):

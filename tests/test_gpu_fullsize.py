@@ -85,7 +85,8 @@ def test_configuration2_full_batch_in_benchmark_launches():
     oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 32)
     q = torch.from_numpy(w["queries"]).cuda()
     sel = np.arange(0, w["queries"].shape[0], 50)
-    for mode, lz, L, place in ((3, 15, 160, 0), (0, 16, 160, 0), (2, 16, 128, 3)):
+    for mode, lz, L, place in ((3, 15, 160, 0), (3, 15, 160, bang.BANG_GRAPH_PACKED), (0, 16, 160, 0),
+                               (2, 16, 128, 3)):
         ix.set_placement(place)
         g = _run(ix, q, 10, L, mode, lz, trace_cap=512)
         o = oix.search(w["queries"][sel], 10, L, log2z=lz, trace_cap=512, exact=mode == 2,
@@ -139,6 +140,11 @@ def test_configuration4_shape_batched_graph_replay():
     torch.cuda.synchronize()
     gi = ids.cpu().numpy().view(np.uint32)
     gd = dist.cpu().numpy()
+    # 27-bit packed rows (BANG_GRAPH_PACKED): the same results
+    ix.set_placement(bang.BANG_GRAPH_PACKED)
+    ix.search_batched(q, kd, Ld, 100, 256, ids, dist, p)
+    torch.cuda.synchronize()
+    assert (ids.cpu().numpy().view(np.uint32) == gi).all()
     ix.close()
     oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 50)
     sel = np.arange(0, nq, 10)

@@ -215,6 +215,28 @@ def test_in_memory_placement_matches_host_placement(u8small):
             assert (g[f] == ref[f]).all()
 
 
+@pytest.mark.parametrize("mode", [0, 2, 3])
+def test_packed_graph_rows_give_identical_results(u8small, cfg1, mode):
+    # ids packed to the fewest bits (15 at n = 20,000; 14 at n = 10,000),
+    # read from host memory or HBM: the same visits and results
+    for w, Q, L in ((u8small, u8small["queries"][:120], 64), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode)
+        for flags in (bang.BANG_GRAPH_PACKED, bang.BANG_GRAPH_PACKED | bang.BANG_GRAPH_IN_HBM):
+            g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags)
+            for f in ("ids", "dist", "iters", "ndist", "trace"):
+                assert (g[f] == ref[f]).all(), (mode, flags, f)
+
+
+def test_packed_graph_rows_wide_rows():
+    # R = 68 (four neighbours per lane), 13-bit ids straddling word boundaries
+    w = cases.clustered(n=6_000, nq=50, ncomp=4, dtype="f32", d=96, M=48, R=68,
+                        centre="uniform255")
+    Q = w["queries"]
+    o = oracle_search(w, Q, 10, 64, trace_cap=300)
+    g = gpu_search(w, Q, 10, 64, trace_cap=300, placement=bang.BANG_GRAPH_PACKED)
+    assert_parity(g, o, trace_cap=300)
+
+
 def _placed(a, offset):
     """Copy of `a` starting `offset` bytes past a 4096-byte boundary."""
     buf = np.empty(a.nbytes + 8192, np.uint8)
