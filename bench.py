@@ -68,6 +68,8 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--k", type=int, default=10, help="k of the search and of k-recall@k")
     ap.add_argument("--M", type=int, default=None, help="PQ subspaces (bytes per code)")
+    ap.add_argument("--packed", action="store_true",
+                    help="fixed forms read packed graph rows (BANG_GRAPH_PACKED)")
     ap.add_argument("--config", type=int, default=2, choices=(2, 3),
                     help="2: mid-scale u8 (the headline); 3: the precision form (f32 d=96)")
     args = ap.parse_args()
@@ -304,8 +306,8 @@ def run_reference(args):
 # kernel version at the default workload, keyed by (mode, bloom_log2, L, placement):
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) and host-memory
 # bytes (32-byte sysmem read sectors).  Cleared whenever the kernel changes.
-NCU_TRAFFIC = {(3, 15, 160, 0): 33477888 + 0}
-NCU_HOST_TRAFFIC = {(3, 15, 160, 0): 24410000 * 32}
+NCU_TRAFFIC = {(3, 15, 160, 0): 33477888 + 0, (3, 15, 160, 4): 33477120 + 0}
+NCU_HOST_TRAFFIC = {(3, 15, 160, 0): 24410000 * 32, (3, 15, 160, 4): 18307348 * 32}
 
 FORMS = {
     # name: (distance mode, placement flags, what it is)
@@ -406,6 +408,9 @@ def main():
             mode, flags, what = FORMS[name]
             tsrc = 1 if name.endswith("_tc") else 0
             lz = args.bloom_log2
+            if args.packed and not flags:
+                flags = bang.BANG_GRAPH_PACKED
+                what += "; graph rows packed"
             place(flags)
             L, sweep = operating_point(mode, tsrc)
         else:                       # settings chosen by bang_autotune
