@@ -68,6 +68,10 @@ def parse():
     ap.add_argument("--no-serving", action="store_true")
     ap.add_argument("--k", type=int, default=10, help="k of the search and of k-recall@k")
     ap.add_argument("--M", type=int, default=None, help="PQ subspaces (bytes per code)")
+    ap.add_argument("--gpu-build", action="store_true",
+                    help="build the PQ codes and the clustered graph with the library's GPU "
+                         "builder instead of the host generator (data and ground truth stay on "
+                         "the host)")
     ap.add_argument("--packed", action="store_true",
                     help="fixed forms read packed graph rows (BANG_GRAPH_PACKED)")
     ap.add_argument("--config", type=int, default=2, choices=(2, 3),
@@ -105,11 +109,34 @@ def job_throughput(units_per_rank, steps, total_ms_local, world, dist=None, devi
     return units_per_rank * world * steps / (t / 1e3), t
 
 
+def gpu_built_workload(args, kw, device):
+    """Data and ground truth from the host generator; PQ codebook, codes and
+    the clustered graph from bang_build_pq / bang_build_cluster_graph."""
+    import workload
+    import paper_2401_11324_gb300 as bang
+    w = workload.clustered_data(args.config, verbose=True, **kw)
+    c = w["params"]
+    t0 = time.perf_counter()
+    cb, codes = bang.bang_build_pq(w["base"], c["M"], w["pq_sample"],
+                                   w["pq_init"].reshape(c["M"], 256), 10, device=device)
+    t1 = time.perf_counter()
+    adj = bang.bang_build_cluster_graph(w["base"], w["members"], w["gstart"], w["medoids"], c["R"],
+                                        c["alpha"], c["nx"], w["xclu"], w["hclu"].shape[1],
+                                        w["hclu"], device=device)
+    t2 = time.perf_counter()
+    w.update(codebook=cb, codes=codes, adj=adj,
+             index_build={"pq_s": round(t1 - t0, 2), "graph_s": round(t2 - t1, 2),
+                          "where": "GPU (bang_build_pq, bang_build_cluster_graph)"})
+    return w
+
+
 def load_workload(args, rank, world, barrier):
     import workload
     kw = dict(n=args.n, nq=args.nq, ncomp=args.ncomp, k=max(100, K))
     if args.M is not None:
         kw["M"] = args.M
+    if args.gpu_build:
+        return gpu_built_workload(args, kw, int(os.environ.get("LOCAL_RANK", "0")))
     if rank == 0:
         w = workload.clustered_workload(args.config, verbose=True, **kw)
     barrier()
@@ -526,7 +553,8 @@ def main():
                    "phase_share": phases,
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "l2": "512 MB flush written between timed steps",
-                   "n": int(w["base"].shape[0]), "nq": nq},
+                   "n": int(w["base"].shape[0]), "nq": nq,
+                   "index_build": w.get("index_build", "host generator (workload/)")},
         "plain_form": brief(res["fp32"]),
         "forms": {f: brief(r) for f, r in list(res.items()) + list(variants.items())},
         "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",

@@ -269,6 +269,49 @@ def scale_index(n, d, dtype, M, R, nx=4, ng=1024, nq=1000, seed=5):
     return dict(base=base, queries=queries, codebook=codebook, codes=codes, adj=adj, medoid=0, M=M)
 
 
+def clustered_data(cfg=2, n=None, nq=None, ncomp=None, k=100, train_n=256_000, verbose=False,
+                   **over):
+    """Data, exact ground truth and the inputs of the index construction
+    (PQ sample and initial centroids as rows of base; clustered-graph inputs)
+    of a clustered configuration, for building the index elsewhere.  Cached
+    on disk by its parameters."""
+    c = dict(CONFIGS[cfg])
+    c.update(over)
+    n = n or c["n"]
+    nq = nq or c["nq"]
+    ncomp = ncomp or c["ncomp"]
+    key = hashlib.sha1(repr(("data", cfg, n, nq, ncomp, k, train_n, sorted(c.items()),
+                             os.path.getmtime(_SRC) // 1, 1)).encode()).hexdigest()[:16]
+    path = os.path.join(cache_dir(), "cfg%d_data_%s.npz" % (cfg, key))
+    if os.path.exists(path):
+        z = np.load(path)
+        out = {f: z[f] for f in z.files}
+        out["medoid"] = int(out["medoid"])
+        out["params"] = dict(c, n=n, nq=nq, ncomp=ncomp)
+        return out
+    t0 = time.time()
+    w = make_data(cfg, n=n, nq=nq, ncomp=ncomp, **over)
+    sample, init = pq_random_choices(cfg, n, c["M"], train_n)
+    gi = graph_inputs(cfg, w["base"], w["labels"], ncomp, c["nx"], c["nh"])
+    _, _, gmed = medoids_of_groups(w["base"], np.zeros(n, np.uint32), 1)
+    t1 = time.time()
+    gt_ids, gt_dist = ground_truth(w["base"], w["queries"], k)
+    t2 = time.time()
+    if verbose:
+        print("data cfg%d n=%d: data %.1fs gt %.1fs (threads %d)" % (
+            cfg, n, t1 - t0, t2 - t1, lib().wl_max_threads()), flush=True)
+    out = dict(base=w["base"], queries=w["queries"], labels=w["labels"], gt_ids=gt_ids,
+               gt_dist=gt_dist, pq_sample=sample, pq_init=sample[init.astype(np.int64)],
+               members=gi["members"], gstart=gi["gstart"], medoids=gi["medoids"], xclu=gi["xclu"],
+               hclu=gi["hclu"], medoid=np.int64(gmed[0]))
+    tmp = path + ".tmp.npz"
+    np.savez(tmp, **out)
+    os.replace(tmp, path)
+    out["medoid"] = int(gmed[0])
+    out["params"] = dict(c, n=n, nq=nq, ncomp=ncomp)
+    return out
+
+
 def cache_dir():
     d = os.environ.get("BANG_WORKLOAD_CACHE", "/tmp/bang_workload_cache")
     os.makedirs(d, exist_ok=True)
