@@ -530,7 +530,7 @@ def main():
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
 
-    link = bang.bang_probe_host_link(local, 1 << 30, R * 4)
+    link = bang.bang_probe_host_link(local, 1 << 30, row_bytes)    # the head's own row size
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_gbs = hbm_bytes / launch_s / 1e9
@@ -570,6 +570,8 @@ def main():
                       "peak_source": "measured in this run: random %d-byte row gathers in place "
                                      "from mapped host memory" % link["gather_row_bytes"],
                       "copy_engine_gbs": link["h2d_copy_gbs"],
+                      "host_threads_gather_gbs": link["cpu_gather_gbs"],
+                      "host_threads": link["cpu_threads"],
                       "load_latency_ns": link["latency_ns"],
                       "algorithmic_bytes_per_launch": host_bytes,
                       "row_bytes": row_bytes,

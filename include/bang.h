@@ -391,6 +391,10 @@ typedef struct bang_link_probe {
     double gather_gbs;          /* kernel reads of random rows in place from mapped host memory */
     double latency_ns;          /* one dependent 4-byte load from mapped host memory */
     uint32_t gather_row_bytes;  /* row size used for gather_gbs */
+    double cpu_gather_gbs;      /* host threads gathering random rows into a page-locked
+                                   staging buffer: the paper's FetchNeighbors path (Alg. 2),
+                                   whose rows would then cross by copy engine */
+    uint32_t cpu_threads;       /* threads used for cpu_gather_gbs */
 } bang_link_probe;
 
 /* Measure the host link of `device` with a page-locked buffer of `bytes`

@@ -40,14 +40,16 @@ class bang_search_params(ctypes.Structure):
 
 class bang_link_probe(ctypes.Structure):
     _fields_ = [("h2d_copy_gbs", ctypes.c_double), ("gather_gbs", ctypes.c_double),
-                ("latency_ns", ctypes.c_double), ("gather_row_bytes", ctypes.c_uint32)]
+                ("latency_ns", ctypes.c_double), ("gather_row_bytes", ctypes.c_uint32),
+                ("cpu_gather_gbs", ctypes.c_double), ("cpu_threads", ctypes.c_uint32)]
 
 
 def bang_probe_host_link(device=0, nbytes=1 << 30, row_bytes=256):
     out = bang_link_probe()
     _check(lib().bang_probe_host_link(device, nbytes, row_bytes, ctypes.byref(out)))
     return dict(h2d_copy_gbs=out.h2d_copy_gbs, gather_gbs=out.gather_gbs,
-                latency_ns=out.latency_ns, gather_row_bytes=out.gather_row_bytes)
+                latency_ns=out.latency_ns, gather_row_bytes=out.gather_row_bytes,
+                cpu_gather_gbs=out.cpu_gather_gbs, cpu_threads=out.cpu_threads)
 
 
 class bang_server_config(ctypes.Structure):

@@ -3,11 +3,18 @@
 // 32 GB/s peak in §6.1; NVLink-C2C on a Grace-hosted GB300).  Three figures:
 // copy-engine bandwidth of page-locked host-to-device copies, bandwidth of a
 // kernel that gathers random rows in place from mapped host memory (the
-// search's own access pattern), and the latency of dependent single loads.
+// search's own access pattern), the latency of dependent single loads, and
+// the rate at which the host's own cores gather random rows into a staging
+// buffer (the paper's FetchNeighbors path, Alg. 2, whose rows then cross by
+// copy engine: that path moves at most the smaller of the two rates).
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <atomic>
+#include <chrono>
 #include <cstdint>
 #include <cstring>
+#include <thread>
 #include <vector>
 
 #include "bang.h"
@@ -128,6 +135,37 @@ extern "C" int bang_probe_host_link(int device, uint64_t bytes, uint32_t row_byt
         }
         out->gather_gbs = best;
         out->gather_row_bytes = row_bytes;
+
+        {   // host threads gathering random rows into a page-locked staging ring
+            const unsigned nt = std::max(1u, std::thread::hardware_concurrency());
+            const uint64_t ring_rows = 4096;       // per thread
+            void *stage = nullptr;
+            if (cudaHostAlloc(&stage, (size_t)nt * ring_rows * row_bytes, cudaHostAllocDefault) == cudaSuccess) {
+                std::atomic<uint64_t> moved{0};
+                std::vector<std::thread> th;
+                const auto t0 = std::chrono::steady_clock::now();
+                for (unsigned t = 0; t < nt; ++t)
+                    th.emplace_back([&, t]() {
+                        const uint8_t *src = static_cast<const uint8_t *>(h);
+                        uint8_t *dst = static_cast<uint8_t *>(stage) + (size_t)t * ring_rows * row_bytes;
+                        uint64_t s = 0x9E3779B97F4A7C15ull * (t + 1), done = 0;
+                        for (int rep = 0; rep < 64; ++rep)
+                            for (uint64_t r = 0; r < ring_rows; ++r) {
+                                s ^= s << 13; s ^= s >> 7; s ^= s << 17;
+                                std::memcpy(dst + r * row_bytes, src + (s % nrows) * row_bytes, row_bytes);
+                                done += row_bytes;
+                            }
+                        moved += done;
+                    });
+                for (auto &x : th) x.join();
+                const double sec = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+                out->cpu_gather_gbs = sec > 0 ? (double)moved.load() / sec / 1e9 : 0.0;
+                out->cpu_threads = nt;
+                cudaFreeHost(stage);
+            } else {
+                cudaGetLastError();
+            }
+        }
 
         const uint32_t steps = 20000;              // dependent loads
         chase<<<1, 1>>>(static_cast<const uint32_t *>(hd), stride, 200, dout);
