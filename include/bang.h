@@ -365,7 +365,9 @@ typedef struct bang_server_config {
 } bang_server_config;
 
 /* Start a server on the calling thread's current device for a fully loaded
- * index (which must outlive the server).  BANG_ENOMEM if the slots do not fit. */
+ * index (which must outlive the server).  While the server runs, its
+ * dispatcher thread is the index's caller: make no other call on that index
+ * until bang_server_stop returns.  BANG_ENOMEM if the slots do not fit. */
 int bang_server_start(bang_index *ix, const bang_server_config *cfg, bang_server **out);
 /* Queue nq (1..max_batch) host queries with their k and L (host arrays,
  * copied before return); *ticket identifies the request. */
