@@ -443,12 +443,15 @@ def main():
         else:                       # settings chosen by bang_autotune
             mode, tsrc, lz, L, sweep = (tune["mode"], tune["table_source"], tune["bloom_log2"],
                                         tune["L"], [])
-            flags = tune.get("placement", 0) | (bang.BANG_GRAPH_PACKED if tune["graph_packed"] else 0)
+            flags = (tune.get("placement", 0) | (bang.BANG_GRAPH_PACKED if tune["graph_packed"] else 0)
+                     | (bang.BANG_NEIGHBOR_CODES if tune["neighbor_codes"] else 0))
             what = ("autotuned (bang_autotune): %s table%s, Bloom filter 2^%d bits, smallest L "
                     "reaching recall@%d 0.9%s" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
                                                   " from the tensor cores" if tsrc else "", lz, K,
-                                                  ", graph rows packed to %d-bit ids" % tune["adj_bits"]
-                                                  if tune["graph_packed"] else ""))
+                                                  (", graph rows packed to %d-bit ids" % tune["adj_bits"]
+                                                   if tune["graph_packed"] else "") +
+                                                  (", neighbours' codes side by side in HBM"
+                                                   if tune["neighbor_codes"] else "")))
             if flags & (bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
                 what = "In-memory variant (§5.1), graph and vectors in HBM, with the " + what
             place(flags)
@@ -477,7 +480,7 @@ def main():
             try:
                 tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
                                    target_recall=TARGET_RECALL, bloom_min=14, bloom_max=19,
-                                   try_packed_graph=1, stream=sptr)
+                                   try_packed_graph=1, try_neighbor_codes=1, stream=sptr)
                 tune["adj_bits"] = int(np.ceil(np.log2(w["base"].shape[0] + 1)))
             except bang.BangError as e:        # no setting reaches the target within L <= 1024
                 tune = {"failed": str(e)}

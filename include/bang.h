@@ -99,7 +99,7 @@ typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,
                BANG_MODE_PQ_Q8 = 3 } bang_mode;
 
 /* Placement flags for bang_set_placement. */
-enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2, BANG_GRAPH_PACKED = 4 };
+enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2, BANG_GRAPH_PACKED = 4, BANG_NEIGHBOR_CODES = 8 };
 
 /* Create an empty index bound to CUDA device `device`.  *out receives an
  * opaque handle owned by the library; free it with bang_destroy. */
@@ -221,6 +221,11 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
  * fewer bytes cross the host link per expansion (in HBM with
  * BANG_GRAPH_IN_HBM).  The copy is page-locked host memory owned by the
  * index, built once from the registered rows; results are unchanged.
+ * BANG_NEIGHBOR_CODES (not in the paper) keeps in HBM, for every node, the PQ
+ * code rows of its R neighbours side by side (n*R*32 bytes: 2 GB at n = 1M,
+ * R = 64), so that the codes of the next node's neighbours are requested
+ * together with its row instead of after it; needs R <= 64, d <= 128 and
+ * M <= 32; results are unchanged.
  * Blocks until the copies are done.  BANG_ENOMEM if the device or the host
  * memory is full. */
 int bang_set_placement(bang_index *ix, uint32_t flags);
@@ -302,8 +307,8 @@ int bang_build_pq(int device, const void *base, bang_dtype dtype, uint64_t n, ui
  * (bang_mode; bit m of `modes` admits mode m), whether mode 1's tables come
  * from the tensor cores (table_source), the Bloom filter size 2^bloom_log2
  * (the paper's z, §4.3), for the batched form the persistent grid
- * multiple, and optionally whether the graph rows are packed
- * (BANG_GRAPH_PACKED; the index's placement is restored on return).  Every candidate searches the given queries on `stream`; its
+ * multiple, and optionally the graph layout (BANG_GRAPH_PACKED,
+ * BANG_NEIGHBOR_CODES; the index's placement is restored on return).  Every candidate searches the given queries on `stream`; its
  * accuracy is recall@k against `truth` (host, nq*k ids; 0xFFFFFFFF entries
  * are skipped) or, when truth is NULL, against an FP32 search with worklist
  * 2L (at most 1024) and a 2^18-bit filter.  Speed is the mean of `reps`
@@ -332,6 +337,7 @@ typedef struct bang_autotune_opts {
     float recall_tolerance;      /* fixed L: allowed recall loss; 0 = 0.005 */
     const char *cache_path;      /* JSON-lines decision cache, or NULL */
     uint32_t try_packed_graph;   /* also try BANG_GRAPH_PACKED rows */
+    uint32_t try_neighbor_codes; /* also try BANG_NEIGHBOR_CODES (where the index allows it) */
 } bang_autotune_opts;
 
 typedef struct bang_autotune_result {
@@ -341,6 +347,7 @@ typedef struct bang_autotune_result {
     uint32_t candidates;         /* candidates evaluated */
     uint32_t from_cache;         /* 1 when read from cache_path */
     uint32_t graph_packed;       /* 1: the choice reads packed rows (set the flag) */
+    uint32_t neighbor_codes;     /* 1: the choice uses the neighbour-code layout (set the flag) */
 } bang_autotune_result;
 
 int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,

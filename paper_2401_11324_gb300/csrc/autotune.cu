@@ -27,7 +27,7 @@
 namespace {
 
 struct Cfg {
-    uint32_t mode, log2z, tsrc, grid_mult, L, packed;
+    uint32_t mode, log2z, tsrc, grid_mult, L, layout;    // layout: BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES bits
 };
 
 struct Runner {
@@ -150,7 +150,7 @@ std::string cache_key(bang_index *ix, uint32_t nq, uint32_t k, uint32_t L, const
       << "|nq=" << nq << "|k=" << k << "|L=" << L << "|target=" << o.target_recall
       << "|tol=" << o.recall_tolerance << "|modes=" << o.modes << "|bloom=" << o.bloom_min << "-"
       << o.bloom_max << "|tc=" << o.try_tensor_tables << "|batched=" << o.batched
-      << "|packed=" << o.try_packed_graph
+      << "|packed=" << o.try_packed_graph << "|ncodes=" << o.try_neighbor_codes
       << "|truth=" << (truth ? 1 : 0);
     std::string r = s.str();
     for (char &c : r)
@@ -177,10 +177,10 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     while (std::getline(f, line))
         if (line.compare(0, kpat.size(), kpat) == 0) hit = line;    // the last entry wins
     if (hit.empty()) return false;
-    double v[11];
-    const char *names[11] = {"mode", "bloom_log2", "table_source", "grid_mult", "L",
-                             "ms", "recall", "ref_ms", "ref_recall", "candidates", "graph_packed"};
-    for (int i = 0; i < 11; ++i)
+    double v[12];
+    const char *names[12] = {"mode", "bloom_log2", "table_source", "grid_mult", "L", "ms", "recall",
+                             "ref_ms", "ref_recall", "candidates", "graph_packed", "neighbor_codes"};
+    for (int i = 0; i < 12; ++i)
         if (!field(hit, names[i], &v[i])) return false;
     out->mode = static_cast<uint32_t>(v[0]);
     out->bloom_log2 = static_cast<uint32_t>(v[1]);
@@ -193,6 +193,7 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     out->ref_recall = static_cast<float>(v[8]);
     out->candidates = static_cast<uint32_t>(v[9]);
     out->graph_packed = static_cast<uint32_t>(v[10]);
+    out->neighbor_codes = static_cast<uint32_t>(v[11]);
     out->from_cache = 1;
     return true;
 }
@@ -206,9 +207,9 @@ void store(const char *path, const std::string &key, const bang_autotune_result 
     std::snprintf(buf, sizeof buf,
                   "\"mode\": %u, \"bloom_log2\": %u, \"table_source\": %u, \"grid_mult\": %u, "
                   "\"L\": %u, \"ms\": %.6g, \"recall\": %.6g, \"ref_ms\": %.6g, \"ref_recall\": %.6g, "
-                  "\"candidates\": %u, \"graph_packed\": %u}",
+                  "\"candidates\": %u, \"graph_packed\": %u, \"neighbor_codes\": %u}",
                   r.mode, r.bloom_log2, r.table_source, r.grid_mult, r.L, r.ms, r.recall, r.ref_ms,
-                  r.ref_recall, r.candidates, r.graph_packed);
+                  r.ref_recall, r.candidates, r.graph_packed, r.neighbor_codes);
     f << "{\"key\": \"" << key << "\", " << buf << "\n";
 }
 
@@ -274,34 +275,50 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
     }
 
     // candidates
+    // graph layouts to try: the caller's, plus packed rows and/or neighbour
+    // codes when asked for (the latter only where the index allows it)
+    const uint32_t place0 = bang::index_placement(ix);
+    const uint32_t kLay = BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES;
+    std::vector<uint32_t> layouts = {place0 & kLay};
+    {
+        uint64_t n_ = 0;
+        uint32_t d_ = 0, M_ = 0, R_ = 0;
+        int32_t dt_ = -1;
+        bang_index_info(ix, &n_, &d_, &M_, &R_, &dt_);
+        const bool nc_ok = R_ <= 64 && d_ <= 128 && M_ <= 32;
+        for (uint32_t pk = 0; pk < 2; ++pk)
+            for (uint32_t nc = 0; nc < 2; ++nc) {
+                if ((pk && !o.try_packed_graph) || (nc && !(o.try_neighbor_codes && nc_ok))) continue;
+                const uint32_t l = (pk ? BANG_GRAPH_PACKED : 0u) | (nc ? BANG_NEIGHBOR_CODES : 0u);
+                if (std::find(layouts.begin(), layouts.end(), l) == layouts.end()) layouts.push_back(l);
+            }
+    }
     std::vector<Cfg> cands;
-    for (uint32_t pk = 0; pk < (o.try_packed_graph ? 2u : 1u); ++pk)
+    for (uint32_t lay : layouts)
         for (uint32_t m = 0; m < 4; ++m) {
             if (!(o.modes & (1u << m))) continue;
             for (uint32_t z = o.bloom_min; z <= o.bloom_max; ++z) {
                 std::vector<uint32_t> gms = {0u};
                 if (o.batched) gms = {1u, 2u, 4u};
                 for (uint32_t gm : gms) {
-                    cands.push_back({m, z, 0u, gm, 0u, pk});
-                    if (m == BANG_MODE_PQ_BF16 && o.try_tensor_tables) cands.push_back({m, z, 1u, gm, 0u, pk});
+                    cands.push_back({m, z, 0u, gm, 0u, lay});
+                    if (m == BANG_MODE_PQ_BF16 && o.try_tensor_tables) cands.push_back({m, z, 1u, gm, 0u, lay});
                 }
             }
         }
-    // the caller's placement, restored on every way out; packed rows are a
-    // candidate dimension
-    const uint32_t place0 = bang::index_placement(ix);
+    // the caller's placement, restored on every way out
     struct Restore {
         bang_index *ix;
         uint32_t flags;
         ~Restore() { if (bang::index_placement(ix) != flags) bang_set_placement(ix, flags); }
     } restore{ix, place0};
-    uint32_t cur_packed = (place0 & BANG_GRAPH_PACKED) ? 1u : 0u;
+    uint32_t cur_lay = place0 & kLay;
 
     // the plain form at the default filter: the reference for the tolerance
     // (fixed L) and for the reported speed-up
     float ref_ms = 0.f, ref_acc = 0.f;
     {
-        Cfg c{BANG_MODE_PQ_F32, 16u, 0u, o.batched ? 1u : 0u, Ls[0], cur_packed};
+        Cfg c{BANG_MODE_PQ_F32, 16u, 0u, o.batched ? 1u : 0u, Ls[0], cur_lay};
         if (o.target_recall > 0.f) {
             for (uint32_t Lc : Ls) {
                 c.L = Lc;
@@ -319,10 +336,9 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
     bool found = false;
     uint32_t tried = 0;
     for (Cfg c : cands) {
-        if (o.try_packed_graph && c.packed != cur_packed) {
-            const uint32_t fl = c.packed ? (place0 | BANG_GRAPH_PACKED) : (place0 & ~(uint32_t)BANG_GRAPH_PACKED);
-            if ((rc = bang_set_placement(ix, fl))) return rc;
-            cur_packed = c.packed;
+        if (c.layout != cur_lay) {
+            if ((rc = bang_set_placement(ix, (place0 & ~kLay) | c.layout))) return rc;
+            cur_lay = c.layout;
         }
         bool ok = false;
         float acc = 0.f;
@@ -349,7 +365,8 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
             out->L = c.L;
             out->ms = ms;
             out->recall = acc;
-            out->graph_packed = cur_packed;
+            out->graph_packed = (cur_lay & BANG_GRAPH_PACKED) ? 1u : 0u;
+            out->neighbor_codes = (cur_lay & BANG_NEIGHBOR_CODES) ? 1u : 0u;
         }
     }
     out->ref_ms = ref_ms;

@@ -214,6 +214,10 @@ struct bang_index {
     DevBuf staging;
     // In-memory placement (§5.1): device copies of the graph and/or vectors.
     DevBuf adj_hbm, base_hbm;
+    // Neighbour-code layout (BANG_NEIGHBOR_CODES): for every node the code
+    // rows of its R neighbours, 32 bytes each, in HBM.
+    DevBuf ncodes;
+    bool ncodes_ok = false;
     uint32_t placement = 0;
     // Batched form: per-stream work counter, query order and staged k / L.
     std::map<cudaStream_t, DevBuf> work;
@@ -399,9 +403,29 @@ int build_packed_rows(bang_index *ix)
     return BANG_OK;
 }
 
+// One thread per (node, slot): the slot's neighbour's code row (zeros for an
+// empty slot), padded to 32 bytes.
+__global__ void gather_neighbor_codes(const uint32_t *adj, uint64_t n, uint32_t R, const uint8_t *codes,
+                                      uint32_t Mpad, uint4 *out)
+{
+    for (uint64_t e = blockIdx.x * static_cast<uint64_t>(blockDim.x) + threadIdx.x; e < n * R;
+         e += static_cast<uint64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t id = adj[e];
+        uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = c0;
+        if (id != bang::kNone) {
+            const uint4 *src = reinterpret_cast<const uint4 *>(codes + static_cast<uint64_t>(id) * Mpad);
+            c0 = src[0];
+            if (Mpad > 16u) c1 = src[1];
+        }
+        out[2 * e] = c0;
+        out[2 * e + 1] = c1;
+    }
+}
+
 // Where and how the kernel reads the graph rows.
 void set_graph_args(const bang_index *ix, bang::SearchArgs &a)
 {
+    a.ncodes = (ix->placement & BANG_NEIGHBOR_CODES) ? static_cast<const uint8_t *>(ix->ncodes.p) : nullptr;
     const bool pk = (ix->placement & BANG_GRAPH_PACKED) != 0;
     if (ix->placement & BANG_GRAPH_IN_HBM) a.adj = static_cast<const uint32_t *>(ix->adj_hbm.p);
     else a.adj = static_cast<const uint32_t *>(pk ? ix->adj_packed.dev : ix->adj.dev);
@@ -446,6 +470,9 @@ int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
     if (ix->off) cudaFree(ix->off);
     if (ix->codes) cudaFree(ix->codes);
     ix->codebook = nullptr; ix->off = nullptr; ix->codes = nullptr;
+    ix->ncodes.release();
+    ix->ncodes_ok = false;
+    ix->placement &= ~(uint32_t)BANG_NEIGHBOR_CODES;
     ix->adj.release();
     ix->base.release();
     ix->have_pq = ix->have_graph = ix->have_vectors = false;
@@ -498,7 +525,9 @@ int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_
     ix->adj_hbm.release();
     ix->adj_packed.release();
     ix->adj_bits = ix->adj_row_words = 0;
-    ix->placement &= ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED);
+    ix->ncodes.release();
+    ix->ncodes_ok = false;
+    ix->placement &= ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES);
     ix->have_graph = false;
     int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->adj);
     if (rc) return rc;
@@ -769,9 +798,12 @@ int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M,
 int bang_set_placement(bang_index *ix, uint32_t flags)
 {
     if (!ix) return fail(BANG_EINVAL, "bang_set_placement: index is NULL");
-    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM | BANG_GRAPH_PACKED))
+    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES))
         return fail(BANG_EINVAL, "bang_set_placement: unknown flags 0x%x", flags);
-    if ((flags & (BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED)) && !ix->have_graph)
+    if ((flags & BANG_NEIGHBOR_CODES) && (ix->R > 64 || ix->d > 128 || ix->Mpad > 32))
+        return fail(BANG_EINVAL, "bang_set_placement: the neighbour-code layout needs R <= 64, d <= 128 "
+                    "and M <= 32");
+    if ((flags & (BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES)) && !ix->have_graph)
         return fail(BANG_ESTATE, "bang_set_placement: register the graph first");
     if ((flags & BANG_VECTORS_IN_HBM) && !ix->have_vectors)
         return fail(BANG_ESTATE, "bang_set_placement: register the vectors first");
@@ -781,6 +813,17 @@ int bang_set_placement(bang_index *ix, uint32_t flags)
     if (flags & BANG_GRAPH_PACKED) {
         const int rc = build_packed_rows(ix);
         if (rc) return rc;
+    }
+    if ((flags & BANG_NEIGHBOR_CODES) && !ix->ncodes_ok) {
+        CUDA_TRY(ix->ncodes.ensure((size_t)ix->n * ix->R * 32u));
+        gather_neighbor_codes<<<1024, 256>>>(static_cast<const uint32_t *>(ix->adj.dev), ix->n, ix->R,
+                                             ix->codes, ix->Mpad, static_cast<uint4 *>(ix->ncodes.p));
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaDeviceSynchronize());
+        ix->ncodes_ok = true;
+    } else if (!(flags & BANG_NEIGHBOR_CODES)) {
+        ix->ncodes.release();
+        ix->ncodes_ok = false;
     }
     if (flags & BANG_GRAPH_IN_HBM) {
         const bool pk = (flags & BANG_GRAPH_PACKED) != 0;
@@ -813,6 +856,7 @@ int bang_destroy(bang_index *ix)
         if (ix->codes) cudaFree(ix->codes);
         ix->adj.release();
         ix->adj_packed.release();
+        ix->ncodes.release();
         ix->base.release();
         ix->staging.release();
         ix->adj_hbm.release();

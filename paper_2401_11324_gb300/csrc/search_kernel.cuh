@@ -61,6 +61,7 @@ struct SearchArgs {
     const uint32_t *adj;      // device-accessible (mapped host), n rows of adj_row_words words
     uint32_t adj_bits;        // 0: rows of R ids; else ids packed to adj_bits bits, all ones = none
     uint32_t adj_row_words;   // 32-bit words per row (R when not packed)
+    const uint8_t *ncodes;    // device or null: for every node, its R neighbours' code rows, 32 bytes each
     const void *base;         // device-accessible (mapped host), n*d
     uint32_t n, d, M, Mpad, R, medoid;
     uint32_t nq, k, L, log2z, iter_cap;
@@ -187,14 +188,15 @@ template <int MODE> __device__ __forceinline__ float table_entry(const void *T, 
 
 // PQ distance of one code row on the 8-bit table: the exact integer sum of
 // the selected entries (any order gives the same sum).
-__device__ __forceinline__ uint32_t adc_distance_q8(const uint8_t *__restrict__ T,
-                                                    const uint8_t *__restrict__ row, uint32_t M,
+// `get(c16)` returns the code row's 16-byte chunk c16 (from memory, or from
+// registers loaded earlier).
+template <typename Get>
+__device__ __forceinline__ uint32_t adc_distance_q8(const uint8_t *__restrict__ T, Get get, uint32_t M,
                                                     uint32_t Mpad)
 {
     uint32_t p[4] = {0u, 0u, 0u, 0u};
-    const uint4 *row16 = reinterpret_cast<const uint4 *>(row);
     for (uint32_t c16 = 0; c16 < Mpad / 16u; ++c16) {
-        uint4 v = __ldg(row16 + c16);
+        uint4 v = get(c16);
         uint32_t w[4] = {v.x, v.y, v.z, v.w};
         const uint8_t *tc = T + c16 * 16u * 256u;
         if (c16 * 16u + 16u <= M) {
@@ -210,17 +212,15 @@ __device__ __forceinline__ uint32_t adc_distance_q8(const uint8_t *__restrict__ 
 }
 
 // PQ distance of one code row (§4.4), in the fixed order described above.
-template <int MODE>
-__device__ __forceinline__ float adc_distance(const void *__restrict__ T,
-                                              const uint8_t *__restrict__ row, uint32_t M,
+template <int MODE, typename Get>
+__device__ __forceinline__ float adc_distance(const void *__restrict__ T, Get get, uint32_t M,
                                               uint32_t Mpad)
 {
     float p[8];
 #pragma unroll
     for (int r = 0; r < 8; ++r) p[r] = 0.0f;
-    const uint4 *row16 = reinterpret_cast<const uint4 *>(row);
     for (uint32_t c16 = 0; c16 < Mpad / 16u; ++c16) {
-        uint4 v = __ldg(row16 + c16);
+        uint4 v = get(c16);
         uint32_t w[4] = {v.x, v.y, v.z, v.w};
         const uint32_t tc = c16 * 16u * 256u;
         if (c16 * 16u + 16u <= M) {
@@ -250,14 +250,21 @@ __device__ __forceinline__ float adc_distance(const void *__restrict__ T,
 // word (int8 biased by 0x80 so that byte differences are unsigned).
 // Ordering bits of a PQ distance: FP32 distances (all >= +0) through their
 // bit patterns, 8-bit-table sums as integers.
+template <int MODE, typename Get>
+__device__ __forceinline__ uint32_t pq_dist_bits_g(const void *T, Get get, uint32_t M, uint32_t Mpad)
+{
+    if constexpr (MODE == kModeQ8)
+        return adc_distance_q8(static_cast<const uint8_t *>(T), get, M, Mpad);
+    else
+        return __float_as_uint(adc_distance<MODE>(T, get, M, Mpad));
+}
+
 template <int MODE>
 __device__ __forceinline__ uint32_t pq_dist_bits(const void *T, const uint8_t *row, uint32_t M,
                                                  uint32_t Mpad)
 {
-    if constexpr (MODE == kModeQ8)
-        return adc_distance_q8(static_cast<const uint8_t *>(T), row, M, Mpad);
-    else
-        return __float_as_uint(adc_distance<MODE>(T, row, M, Mpad));
+    const uint4 *row16 = reinterpret_cast<const uint4 *>(row);
+    return pq_dist_bits_g<MODE>(T, [row16](uint32_t c16) { return __ldg(row16 + c16); }, M, Mpad);
 }
 
 template <int DT, int DCH> struct VecShare {
@@ -329,15 +336,18 @@ __device__ __forceinline__ uint32_t exact_distance_bits(const VecShare<DT, DCH> 
     }
 }
 
-// The expanded node's neighbour ids and this lane's share of its vector.
-template <int DT, int RPL, int DCH> struct NodeData {
+// The expanded node's neighbour ids, this lane's share of its vector and,
+// with the neighbour-code layout (NC), the code rows of this lane's
+// neighbours (slots lane + 32 r, two 16-byte chunks each).
+template <int DT, int RPL, int DCH, bool NC = false> struct NodeData {
     uint32_t nb[RPL];
     VecShare<DT, DCH> x;
+    uint4 code[NC ? 2 * RPL : 1];
 };
 
-template <int DT, int RPL, int DCH, bool WITH_VECTOR>
+template <int DT, int RPL, int DCH, bool WITH_VECTOR, bool NC>
 __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int lane,
-                                          NodeData<DT, RPL, DCH> &nd)
+                                          NodeData<DT, RPL, DCH, NC> &nd)
 {
     using E = typename Elem<DT>::T;
     const uint32_t W = a.adj_bits ? a.adj_row_words : a.R;     // words per row
@@ -350,6 +360,15 @@ __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int l
     if (WITH_VECTOR) {
         const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
         load_share<DT, DCH>(x, a.d, a.vecb_ok != 0, lane, nd.x);
+    }
+    if constexpr (NC) {
+        const uint4 *c = reinterpret_cast<const uint4 *>(a.ncodes) + static_cast<uint64_t>(u) * a.R * 2u;
+#pragma unroll
+        for (int r = 0; r < RPL; ++r) {
+            const uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
+            nd.code[2 * r] = i < a.R ? __ldg(c + 2u * i) : make_uint4(0u, 0u, 0u, 0u);
+            nd.code[2 * r + 1] = i < a.R ? __ldg(c + 2u * i + 1u) : make_uint4(0u, 0u, 0u, 0u);
+        }
     }
 }
 
@@ -509,7 +528,7 @@ struct PhaseClock {
     }
 };
 
-template <int DT, int RPL, int DCH, int MODE>
+template <int DT, int RPL, int DCH, int MODE, bool NC>
 __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 {
     using E = typename Elem<DT>::T;
@@ -608,8 +627,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         int32_t status = table_failed ? 2 : 0;
         uint64_t ck = ~0ull;               // register top-k (k <= kRegK): lane i holds rank i
         uint32_t cur = a.medoid;
-        NodeData<DT, RPL, DCH> nd;
-        load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
+        NodeData<DT, RPL, DCH, NC> nd;
+        load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
         __syncwarp();
 
         while (have_next) {
@@ -630,7 +649,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             ++iters;
             if (u != cur) {  // the prefetched node is always u*; reload if not
                 cur = u;
-                load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
+                load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
             }
             VecShare<DT, DCH> xu;                // u*'s vector, for the re-rank below (PQ modes)
             clk.mark(kPhSelect);
@@ -638,7 +657,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             unpack_ids<RPL>(a, lane, nd.nb);
             // ---- filter seen neighbours, §4.3: test all, then insert all
             bool fresh[RPL];
-            uint32_t p1[RPL], p2[RPL];
+            uint32_t p1[RPL], p2[RPL], slot[RPL];
 #pragma unroll
             for (int r = 0; r < RPL; ++r) {
                 const uint32_t id = nd.nb[r];
@@ -661,7 +680,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     atomicOr(&bloom[p2[r] >> 5], 1u << (p2[r] & 31u));
                 }
                 const uint32_t bal = __ballot_sync(0xFFFFFFFFu, fresh[r]);
-                if (fresh[r]) Nid[nn + __popc(bal & ((1u << lane) - 1u))] = nd.nb[r];
+                slot[r] = nn + __popc(bal & ((1u << lane) - 1u));
+                if (fresh[r]) Nid[slot[r]] = nd.nb[r];
                 nn += __popc(bal);
             }
             __syncwarp();
@@ -670,7 +690,15 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             // ---- distances of the new neighbours: PQ (§4.4), one lane per
             // neighbour; or exact (§5.2), the warp per neighbour, four
             // neighbours' vectors requested at a time
-            if (kPQ) {
+            if constexpr (NC) {              // code rows arrived with the node: the lane that holds them
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    if (!fresh[r]) continue;
+                    const uint4 c0 = nd.code[2 * r], c1 = nd.code[2 * r + 1];
+                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(T, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
+                                                                a.M, a.Mpad), nd.nb[r]);
+                }
+            } else if (kPQ) {
                 for (uint32_t j = lane; j < nn; j += kWarp) {
                     const uint32_t id = Nid[j];
                     Nk[j] = make_key(pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
@@ -724,7 +752,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 if (kPQ) xu = nd.x;              // wait for the vector only here
                 if (best != ~0ull) {
                     cur = key_id(best);
-                    load_node<DT, RPL, DCH, kPQ>(a, cur, lane, nd);
+                    load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
                 }
             }
             clk.mark(kPhNext);
@@ -936,10 +964,10 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 
 // Launch for one mode: dispatch on element type, neighbours per lane
 // (R <= 64 or <= 128) and 128-dimension chunks per lane (d <= 128 or <= 512).
-template <int DT, int RPL, int DCH, int MODE>
+template <int DT, int RPL, int DCH, int MODE, bool NC = false>
 cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE>,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, NC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     uint32_t grid = a.nq;
@@ -947,20 +975,27 @@ cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE, NC>,
                                                                32, smem)) != cudaSuccess)
             return e;
         const uint64_t want = static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1) *
                               (a.grid_mult ? a.grid_mult : 1u);
         grid = static_cast<uint32_t>(want < a.nq ? want : a.nq);
     }
-    search_kernel<DT, RPL, DCH, MODE><<<grid, 32, smem, st>>>(a);
+    search_kernel<DT, RPL, DCH, MODE, NC><<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st)
 {
     const bool narrow = a.d <= 128, wide_r = a.R > 64;
+    if constexpr (MODE != kModeExact) {
+        if (a.ncodes) {                // neighbour-code layout: R <= 64, d <= 128, checked by the caller
+            if (dtype == 0) return launch_one<0, 2, 1, MODE, true>(a, smem, st);
+            if (dtype == 1) return launch_one<1, 2, 1, MODE, true>(a, smem, st);
+            return launch_one<2, 2, 1, MODE, true>(a, smem, st);
+        }
+    }
 #define BANG_DISPATCH(DT)                                                                    \
     return wide_r ? (narrow ? launch_one<DT, 4, 1, MODE>(a, smem, st) : launch_one<DT, 4, 4, MODE>(a, smem, st)) \
                   : (narrow ? launch_one<DT, 2, 1, MODE>(a, smem, st) : launch_one<DT, 2, 4, MODE>(a, smem, st))

@@ -227,6 +227,28 @@ def test_packed_graph_rows_give_identical_results(u8small, cfg1, mode):
                 assert (g[f] == ref[f]).all(), (mode, flags, f)
 
 
+@pytest.mark.parametrize("mode", [0, 1, 3])
+def test_neighbor_code_layout_gives_identical_results(u8small, cfg1, mode):
+    # the codes of every node's neighbours side by side in HBM, alone or with
+    # packed rows or the graph in HBM: the same visits and results
+    for w, Q, L in ((u8small, u8small["queries"][:120], 64), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode)
+        for flags in (bang.BANG_NEIGHBOR_CODES, bang.BANG_NEIGHBOR_CODES | bang.BANG_GRAPH_PACKED,
+                      bang.BANG_NEIGHBOR_CODES | bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
+            g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags)
+            for f in ("ids", "dist", "iters", "ndist", "trace"):
+                assert (g[f] == ref[f]).all(), (mode, flags, f)
+
+
+def test_neighbor_code_layout_limits():
+    w = cases.clustered(n=6_000, nq=5, ncomp=4, dtype="f32", d=96, M=48, R=68,
+                        centre="uniform255")
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], 48)
+    with pytest.raises(bang.BangError):
+        ix.set_placement(bang.BANG_NEIGHBOR_CODES)        # R = 68 > 64 and M = 48 > 32
+    ix.close()
+
+
 def test_packed_graph_rows_wide_rows():
     # R = 68 (four neighbours per lane), 13-bit ids straddling word boundaries
     w = cases.clustered(n=6_000, nq=50, ncomp=4, dtype="f32", d=96, M=48, R=68,
