@@ -240,6 +240,37 @@ def test_neighbor_code_layout_gives_identical_results(u8small, cfg1, mode):
                 assert (g[f] == ref[f]).all(), (mode, flags, f)
 
 
+def test_placement_transitions_and_reregistration(u8small):
+    # one index moved through every layout and back, then given its graph
+    # again (which drops the layouts built from the old rows): same results
+    w = u8small
+    Q = np.ascontiguousarray(w["queries"][:64])
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    q = torch.from_numpy(Q).cuda()
+
+    def run():
+        ids = torch.empty((len(Q), 10), dtype=torch.int32, device="cuda")
+        dist = torch.empty((len(Q), 10), dtype=torch.float32, device="cuda")
+        ix.search(q, 10, 64, ids, dist, bang.make_params(mode=3, bloom_log2=15))
+        torch.cuda.synchronize()
+        return ids.cpu().numpy(), dist.cpu().numpy()
+
+    ref = run()
+    P, H, V, N = (bang.BANG_GRAPH_PACKED, bang.BANG_GRAPH_IN_HBM, bang.BANG_VECTORS_IN_HBM,
+                  bang.BANG_NEIGHBOR_CODES)
+    for flags in (P, P | H, H, N | H | V, N | P, 0, N, P | N | H | V, 0):
+        ix.set_placement(flags)
+        got = run()
+        assert (got[0] == ref[0]).all() and (got[1] == ref[1]).all(), flags
+    ix.set_placement(P | N)
+    bang.bang_register_graph(ix.h, ix.adj, ix.R, ix.medoid)      # drops packed rows and codes
+    got = run()
+    assert (got[0] == ref[0]).all()
+    with pytest.raises(bang.BangError):
+        ix.set_placement(16)                                     # unknown flag
+    ix.close()
+
+
 def test_neighbor_code_layout_limits():
     w = cases.clustered(n=6_000, nq=5, ncomp=4, dtype="f32", d=96, M=48, R=68,
                         centre="uniform255")
