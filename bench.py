@@ -387,10 +387,13 @@ def main():
             ix.set_placement(flags)
             placement[0] = flags
 
+    depth = [1]                       # prefetch depth of the form being measured
+
     def search(L, mode, with_stats=False, phase=None, tsrc=0, lz=None):
         p = bang.make_params(bloom_log2=lz or args.bloom_log2, mode=mode, table_source=tsrc,
                              out_iters=iters if with_stats else None,
-                             out_ndist=ndist if with_stats else None, out_phase_cycles=phase)
+                             out_ndist=ndist if with_stats else None, out_phase_cycles=phase,
+                             prefetch_depth=depth[0])
         ix.search(q_dev, K, L, ids, dist_out, p, stream=sptr)
 
     def operating_point(mode, tsrc=0, lz=None):
@@ -431,6 +434,7 @@ def main():
         return total_ms, step_ms, t_wall
 
     def measure(name, steps, tune=None):
+        depth[0] = tune.get("prefetch_depth", 1) if tune is not None else 1
         if tune is None:
             mode, flags, what = FORMS[name]
             tsrc = 1 if name.endswith("_tc") else 0
@@ -464,6 +468,7 @@ def main():
         nd = ndist.cpu().numpy().astype(np.int64)
         total_ms, step_ms, t_wall = timed(L, mode, steps, tsrc, lz)
         return dict(form=name, what=what, mode=mode, placement=flags, L=L, tsrc=tsrc, lz=lz,
+                    depth=depth[0],
                     dist_error=derr,
                     recall=round(rec, 4), sweep=sweep, iters=it, ndist=nd,
                     value=nq * world * steps / (total_ms / 1e3), ms_per_step=total_ms / steps,
@@ -480,7 +485,8 @@ def main():
             try:
                 tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
                                    target_recall=TARGET_RECALL, bloom_min=14, bloom_max=19,
-                                   try_packed_graph=1, try_neighbor_codes=1, stream=sptr)
+                                   try_packed_graph=1, try_neighbor_codes=1, try_prefetch_depth=1,
+                                   stream=sptr)
                 tune["adj_bits"] = int(np.ceil(np.log2(w["base"].shape[0] + 1)))
             except bang.BangError as e:        # no setting reaches the target within L <= 1024
                 tune = {"failed": str(e)}
@@ -495,6 +501,7 @@ def main():
         variants["in_memory_autotuned"] = measure("in_memory_autotuned", max(5, args.steps // 5),
                                                   dict(tune, placement=3))
     place(head["placement"])
+    depth[0] = head["depth"]
     L, mode, tsrc, lz = head["L"], head["mode"], head["tsrc"], head["lz"]
     it, nd = head["iters"], head["ndist"]
 
@@ -521,7 +528,7 @@ def main():
     q_host = torch.from_numpy(w["queries"]).pin_memory()
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-    hp = bang.make_params(bloom_log2=lz, mode=mode, table_source=tsrc)
+    hp = bang.make_params(bloom_log2=lz, mode=mode, table_source=tsrc, prefetch_depth=depth[0])
     for _ in range(2):
         ix.search(q_host, K, L, ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))

@@ -93,6 +93,12 @@ typedef struct bang_search_params {
      * of bang_pq_tables into per-stream device scratch owned by the index
      * (nq*M*512 bytes), then read by the search. */
     uint32_t table_source;
+    /* How many candidates for the next node are requested per iteration: 0
+     * or 1 = the chosen one only, after the distances (§4.5's eager choice);
+     * 2 = also the first unvisited worklist entry after u*, at the start of
+     * the iteration (used when it is chosen, wasted otherwise).  Results do
+     * not depend on it. */
+    uint32_t prefetch_depth;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,
@@ -338,6 +344,7 @@ typedef struct bang_autotune_opts {
     const char *cache_path;      /* JSON-lines decision cache, or NULL */
     uint32_t try_packed_graph;   /* also try BANG_GRAPH_PACKED rows */
     uint32_t try_neighbor_codes; /* also try BANG_NEIGHBOR_CODES (where the index allows it) */
+    uint32_t try_prefetch_depth; /* also time the winner with prefetch_depth 2 */
 } bang_autotune_opts;
 
 typedef struct bang_autotune_result {
@@ -348,6 +355,7 @@ typedef struct bang_autotune_result {
     uint32_t from_cache;         /* 1 when read from cache_path */
     uint32_t graph_packed;       /* 1: the choice reads packed rows (set the flag) */
     uint32_t neighbor_codes;     /* 1: the choice uses the neighbour-code layout (set the flag) */
+    uint32_t prefetch_depth;     /* 1 or 2 (bang_search_params.prefetch_depth) */
 } bang_autotune_result;
 
 int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,

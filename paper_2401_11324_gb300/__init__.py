@@ -35,7 +35,7 @@ class bang_search_params(ctypes.Structure):
                 ("out_ndist", ctypes.c_void_p), ("trace", ctypes.c_void_p),
                 ("trace_cap", ctypes.c_uint32), ("out_phase_cycles", ctypes.c_void_p),
                 ("mode", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32),
-                ("table_source", ctypes.c_uint32)]
+                ("table_source", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32)]
 
 
 class bang_link_probe(ctypes.Structure):
@@ -64,7 +64,7 @@ class bang_autotune_opts(ctypes.Structure):
                 ("batched", ctypes.c_uint32), ("reps", ctypes.c_uint32),
                 ("target_recall", ctypes.c_float), ("recall_tolerance", ctypes.c_float),
                 ("cache_path", ctypes.c_char_p), ("try_packed_graph", ctypes.c_uint32),
-                ("try_neighbor_codes", ctypes.c_uint32)]
+                ("try_neighbor_codes", ctypes.c_uint32), ("try_prefetch_depth", ctypes.c_uint32)]
 
 
 class bang_autotune_result(ctypes.Structure):
@@ -73,7 +73,8 @@ class bang_autotune_result(ctypes.Structure):
                 ("L", ctypes.c_uint32), ("ms", ctypes.c_float), ("recall", ctypes.c_float),
                 ("ref_ms", ctypes.c_float), ("ref_recall", ctypes.c_float),
                 ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_uint32),
-                ("graph_packed", ctypes.c_uint32), ("neighbor_codes", ctypes.c_uint32)]
+                ("graph_packed", ctypes.c_uint32), ("neighbor_codes", ctypes.c_uint32),
+                ("prefetch_depth", ctypes.c_uint32)]
 
 
 def library_path():
@@ -181,10 +182,10 @@ BANG_GRAPH_IN_HBM, BANG_VECTORS_IN_HBM, BANG_GRAPH_PACKED, BANG_NEIGHBOR_CODES =
 
 def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
                 trace=None, trace_cap=0, out_phase_cycles=None, mode=0, grid_mult=0,
-                table_source=0):
+                table_source=0, prefetch_depth=0):
     return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
                               _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles), mode,
-                              grid_mult, table_source)
+                              grid_mult, table_source, prefetch_depth)
 
 
 def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):
@@ -220,13 +221,14 @@ def bang_pq_tables(ix, queries, nq, out, out_bf16=0, stream=None):
 
 def bang_autotune(ix, queries, nq, k, L, truth=None, modes=0, bloom_min=0, bloom_max=0,
                   try_tensor_tables=1, batched=0, reps=0, target_recall=0.0, recall_tolerance=0.0,
-                  cache_path=None, try_packed_graph=0, try_neighbor_codes=0, stream=None):
+                  cache_path=None, try_packed_graph=0, try_neighbor_codes=0, try_prefetch_depth=0,
+                  stream=None):
     """Returns the chosen settings as a dict (fields of bang_autotune_result)."""
     s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
     o = bang_autotune_opts(modes, bloom_min, bloom_max, try_tensor_tables, batched, reps,
                            target_recall, recall_tolerance,
                            cache_path.encode() if cache_path else None, try_packed_graph,
-                           try_neighbor_codes)
+                           try_neighbor_codes, try_prefetch_depth)
     t = None if truth is None else np.ascontiguousarray(truth, np.uint32)
     r = bang_autotune_result()
     _check(lib().bang_autotune(ix, _ptr(queries), nq, k, L, _ptr(t), ctypes.byref(o),

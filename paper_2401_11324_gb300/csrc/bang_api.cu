@@ -695,6 +695,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.order = order;
     a.queue = queue;
     a.grid_mult = p.grid_mult;
+    a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
     a.tables = tables;
     a.tables_err = static_cast<const unsigned int *>(ix->tc_err.p);
     a.out_ids = static_cast<uint32_t *>(dptr(1));
@@ -1033,6 +1034,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.order = scratch + kNoAllocOrder;
     a.queue = scratch;
     a.grid_mult = p.grid_mult;
+    a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
     if (p.table_source != 0)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0 (tables need scratch)");
     const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);

@@ -62,6 +62,7 @@ struct SearchArgs {
     uint32_t adj_bits;        // 0: rows of R ids; else ids packed to adj_bits bits, all ones = none
     uint32_t adj_row_words;   // 32-bit words per row (R when not packed)
     const uint8_t *ncodes;    // device or null: for every node, its R neighbours' code rows, 32 bytes each
+    uint32_t spec;            // also request the first unvisited worklist entry after u* at once
     const void *base;         // device-accessible (mapped host), n*d
     uint32_t n, d, M, Mpad, R, medoid;
     uint32_t nq, k, L, log2z, iter_cap;
@@ -627,7 +628,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         int32_t status = table_failed ? 2 : 0;
         uint64_t ck = ~0ull;               // register top-k (k <= kRegK): lane i holds rank i
         uint32_t cur = a.medoid;
-        NodeData<DT, RPL, DCH, NC> nd;
+        NodeData<DT, RPL, DCH, NC> nd, nd2;   // nd2: the speculative request (a.spec)
         load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
         __syncwarp();
 
@@ -651,6 +652,22 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 cur = u;
                 load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
             }
+            // the first unvisited worklist entry after u*: one of the two
+            // candidates for the next node (§4.5); with a.spec its lists are
+            // requested now, before this iteration's distances are known
+            uint64_t lkey = ~0ull;
+            int lnext = -1;                  // index of that worklist entry
+            for (uint32_t b0 = first + 1; b0 < nl; b0 += kWarp) {
+                const uint32_t i = b0 + lane;
+                const bool v = i < nl && !(Lk[i] & 1ull);
+                const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
+                if (bal) {
+                    lnext = static_cast<int>(b0 + __ffs(bal) - 1);
+                    lkey = Lk[lnext];
+                    break;
+                }
+            }
+            if (a.spec && lkey != ~0ull) load_node<DT, RPL, DCH, kPQ, NC>(a, key_id(lkey), lane, nd2);
             VecShare<DT, DCH> xu;                // u*'s vector, for the re-rank below (PQ modes)
             clk.mark(kPhSelect);
 
@@ -730,21 +747,10 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 
             // ---- eager next node, §4.5: the best of the new neighbours and
             // the first unvisited worklist entry after u*; prefetch its lists
-            uint64_t best = ~0ull, lkey = ~0ull;
-            int lnext = -1;                  // index of that worklist entry
+            uint64_t best = ~0ull;
             {
                 for (uint32_t j = lane; j < nn; j += kWarp) best = Nk[j] < best ? Nk[j] : best;
-                for (uint32_t b0 = first + 1; b0 < nl; b0 += kWarp) {
-                    const uint32_t i = b0 + lane;
-                    const bool v = i < nl && !(Lk[i] & 1ull);
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
-                    if (bal) {
-                        lnext = static_cast<int>(b0 + __ffs(bal) - 1);
-                        lkey = Lk[lnext];
-                        best = lkey < best ? lkey : best;
-                        break;
-                    }
-                }
+                best = lkey < best ? lkey : best;
                 best = warp_min_key(best);
                 // the best new neighbour can still fall off the end of a full
                 // worklist of expanded entries; whether a next node exists is
@@ -752,7 +758,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 if (kPQ) xu = nd.x;              // wait for the vector only here
                 if (best != ~0ull) {
                     cur = key_id(best);
-                    load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
+                    if (a.spec && best == lkey) nd = nd2;           // requested at the start
+                    else load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
                 }
             }
             clk.mark(kPhNext);

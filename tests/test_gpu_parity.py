@@ -18,7 +18,7 @@ RTOL = 1e-5
 
 
 def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
-               placement=0):
+               placement=0, prefetch_depth=0):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     if placement:
@@ -37,7 +37,7 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     trace = torch.zeros((nq, max(trace_cap, 1)), dtype=torch.int32, device=dev)
     p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
                          out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
-                         mode=mode)
+                         mode=mode, prefetch_depth=prefetch_depth)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
@@ -278,6 +278,17 @@ def test_neighbor_code_layout_limits():
     with pytest.raises(bang.BangError):
         ix.set_placement(bang.BANG_NEIGHBOR_CODES)        # R = 68 > 64 and M = 48 > 32
     ix.close()
+
+
+@pytest.mark.parametrize("mode,flags", [(0, 0), (3, 0), (3, 4), (1, 11), (2, 3)])
+def test_speculative_prefetch_gives_identical_results(u8small, cfg1, mode, flags):
+    # prefetch_depth 2 also requests the first unvisited worklist entry at
+    # the start of each iteration; visits and results are unchanged
+    for w, Q, L in ((u8small, u8small["queries"][:120], 64), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags)
+        g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags, prefetch_depth=2)
+        for f in ("ids", "dist", "iters", "ndist", "trace"):
+            assert (g[f] == ref[f]).all(), (mode, flags, f)
 
 
 def test_packed_graph_rows_wide_rows():
