@@ -8,7 +8,8 @@ test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 no code with the CUDA implementation.
 
 Parity status of each function (see the C file for the passage it follows):
-  pq_train, pq_encode, medoid, adc_table, adc_dist, adc_table_q8, adc_dist_q8, exact_dist, bloom,
+  pq_train, pq_encode, medoid, adc_table, adc_dist, adc_table_q8, adc_dist_q8, round_bf16,
+  adc_table_bf16, exact_dist, bloom,
   search, bruteforce_knn : pinned by tests/test_oracle_*.py
   cluster_graph          : pinned by closed forms (a line with alpha = 1 gives
                            the chain; a huge alpha gives the exact nearest
@@ -82,6 +83,9 @@ def lib():
         L.orc_adc_table_f32.argtypes = [vp, u32, vp, vp, vp]
         L.orc_adc_dist_f32.argtypes = [vp, u32, vp]
         L.orc_adc_dist_f32.restype = f32
+        L.orc_round_bf16.argtypes = [f32]
+        L.orc_round_bf16.restype = f32
+        L.orc_adc_table_bf16.argtypes = [vp, u32, vp]
         L.orc_adc_table_q8.argtypes = [vp, u32, vp]
         L.orc_adc_dist_q8.argtypes = [vp, u32, vp]
         L.orc_adc_dist_q8.restype = u32
@@ -205,6 +209,17 @@ def adc_dist(T, code):
     return float(lib().orc_adc_dist_f32(_p(T), T.shape[0], _p(code)))
 
 
+def round_bf16(x):
+    return float(lib().orc_round_bf16(ctypes.c_float(x)))
+
+
+def adc_table_bf16(T):
+    T = _c(T, np.float32)
+    out = np.zeros_like(T)
+    lib().orc_adc_table_bf16(_p(T), T.shape[0], _p(out))
+    return out
+
+
 def adc_table_q8(T):
     """8-bit form of an FP32 table (per-subspace offset, one scale)."""
     T = _c(T, np.float32)
@@ -270,11 +285,11 @@ class Index:
                            self.base.ctypes.data)
 
     def search(self, queries, k, L, log2z=16, iter_cap=None, trace_cap=0, nthreads=0, exact=False,
-               q8=False):
+               q8=False, bf16=False):
         """Alg. 2 search; exact=True runs the Exact-distance variant (§5.2),
-        q8=True the search on the 8-bit table."""
-        assert not (exact and q8)
-        mode = 1 if exact else (2 if q8 else 0)
+        q8=True the search on the 8-bit table, bf16=True on the BF16 table."""
+        assert exact + q8 + bf16 <= 1
+        mode = 1 if exact else (2 if q8 else (3 if bf16 else 0))
         q = np.ascontiguousarray(queries, dtype=self.base.dtype)
         nq = q.shape[0]
         if iter_cap is None:

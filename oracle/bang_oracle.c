@@ -31,6 +31,7 @@
  *   orc_adc_table_f32        §4.1 (PQDistTable: squared distance of each query
  *                            sub-vector to each centroid)
  *   orc_adc_dist_f32         §4.4 (asymmetric distance = sum of table entries)
+ *   orc_adc_table_bf16       the table rounded to BF16 (not in the paper)
  *   orc_adc_table_q8/_dist_q8 an 8-bit form of the §4.1 table that the paper
  *                            does not have (its table is FP32): per-subspace
  *                            offset, one scale per query, integer sums
@@ -39,7 +40,8 @@
  *   orc_exact_dist           §4.8 (exact distance used by the re-rank)
  *   orc_search               Alg. 1, Alg. 2, §4.3-§4.8; mode 1: the Exact-distance
  *                            variant of §5.2 (exact distances, no table, no re-rank);
- *                            mode 2: mode 0 with the 8-bit table
+ *                            mode 2: mode 0 with the 8-bit table; mode 3: with the
+ *                            BF16 table
  *   orc_bruteforce_knn       §6.3 (ground truth S for k-recall@k)
  */
 #include <math.h>
@@ -589,6 +591,35 @@ float orc_adc_dist_f32(const float *T, uint32_t M, const uint8_t *code)
 }
 
 /* ---------------------------------------------------------------------- */
+/* BF16 table.  Not in the paper, whose table is FP32 (§4.1); added as a    */
+/* reduced form with half the table: every FP32 entry is rounded to the     */
+/* nearest BF16 value (8 significant bits; halfway cases to the value whose */
+/* last kept bit is 0), and distances sum the BF16 values, widened back to  */
+/* FP32, in the order of orc_adc_dist_f32.                                  */
+/* ---------------------------------------------------------------------- */
+
+float orc_round_bf16(float x)
+{
+    uint32_t u;
+    memcpy(&u, &x, 4);
+    if ((u & 0x7F800000u) == 0x7F800000u) {
+        if (u & 0x007FFFFFu) u |= 0x00400000u;        /* NaN stays NaN */
+    } else {
+        uint32_t keep_lsb = (u >> 16) & 1u;
+        u += 0x7FFFu + keep_lsb;                      /* may carry into the exponent */
+    }
+    u &= 0xFFFF0000u;
+    memcpy(&x, &u, 4);
+    return x;
+}
+
+void orc_adc_table_bf16(const float *T, uint32_t M, float *Tb)
+{
+    uint32_t i;
+    for (i = 0; i < M * 256u; i++) Tb[i] = orc_round_bf16(T[i]);
+}
+
+/* ---------------------------------------------------------------------- */
 /* 8-bit table.  Not in the paper, whose table is FP32 (§4.1); added as a   */
 /* reduced form whose table is a quarter of the FP32 one.  From the FP32    */
 /* table T of one query:                                                    */
@@ -759,7 +790,7 @@ static float search_dist(const orc_index *ix, int mode, const float *T, const ui
                          const void *q, uint32_t v)
 {
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
-    if (mode == 0) return orc_adc_dist_f32(T, ix->M, ix->codes + (uint64_t)v * ix->M);
+    if (mode == 0 || mode == 3) return orc_adc_dist_f32(T, ix->M, ix->codes + (uint64_t)v * ix->M);
     if (mode == 2) return (float)orc_adc_dist_q8(Q, ix->M, ix->codes + (uint64_t)v * ix->M);
     return (float)orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)v * ix->d * esz,
                                  ix->dtype, ix->d);
@@ -803,6 +834,7 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
     for (i = 0; i < d; i++) qf[i] = elem_f(q, ix->dtype, i);
     if (mode != 1) orc_adc_table_f32(qf, M, ix->off, ix->codebook, T);
     if (mode == 2) orc_adc_table_q8(T, M, Q);
+    if (mode == 3) orc_adc_table_bf16(T, M, T);
 
     Lst[0].id = ix->medoid;
     Lst[0].dist = search_dist(ix, mode, T, Q, q, ix->medoid);
@@ -868,7 +900,7 @@ int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, 
 {
     int64_t qi;
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
-    if (k == 0 || L < k || ix->M == 0 || ix->d == 0 || mode < 0 || mode > 2) return -1;
+    if (k == 0 || L < k || ix->M == 0 || ix->d == 0 || mode < 0 || mode > 3) return -1;
 #ifdef _OPENMP
     if (nthreads <= 0) nthreads = omp_get_max_threads();
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)

@@ -48,6 +48,8 @@ int orc_cluster_graph(const void *X, int dtype, uint32_t d, uint64_t n, const ui
 void orc_adc_table_f32(const float *q, uint32_t M, const uint32_t *off,
                        const float *codebook, float *T);
 float orc_adc_dist_f32(const float *T, uint32_t M, const uint8_t *code);
+float orc_round_bf16(float x);
+void orc_adc_table_bf16(const float *T, uint32_t M, float *Tb);
 void orc_adc_table_q8(const float *T, uint32_t M, uint8_t *Q);
 uint32_t orc_adc_dist_q8(const uint8_t *Q, uint32_t M, const uint8_t *code);
 double orc_exact_dist(const void *q, const void *x, int dtype, uint32_t d);
@@ -58,7 +60,8 @@ int orc_bloom_test(const uint32_t *bits, uint32_t log2z, uint32_t id);
 void orc_bloom_insert(uint32_t *bits, uint32_t log2z, uint32_t id);
 /* mode 0: PQ distances + re-rank of the expanded nodes (§4); mode 1: exact
  * distances in the loop, no re-rank, result = the worklist's first k (§5.2);
- * mode 2: as mode 0 with the 8-bit table (orc_adc_table_q8). */
+ * mode 2: as mode 0 with the 8-bit table (orc_adc_table_q8); mode 3: as mode 0
+ * with the table rounded to BF16 (orc_adc_table_bf16). */
 int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, uint32_t k,
                uint32_t L, uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
                uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,

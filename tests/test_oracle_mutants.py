@@ -41,6 +41,9 @@ MUTANTS = [
     ("cg_no_reverse_edges", "if (!chose) continue;", "if (1) continue;", 0),
     ("cg_no_repair", "if (indeg[a] != 0 || deg2[a] == 0) continue;", "if (1) continue;", 0),
     ("cg_alpha_unsquared", "float a2 = alpha * alpha;", "float a2 = alpha;", 0),
+    ("bf16_truncates", "u += 0x7FFFu + keep_lsb;", "u += 0u * keep_lsb;", 0),
+    ("bf16_ties_up", "u += 0x7FFFu + keep_lsb;", "u += 0x8000u + 0u * keep_lsb;", 0),
+    ("bf16_mode_uses_f32", "if (mode == 3) orc_adc_table_bf16(T, M, T);", "", 0),
     ("exact_mode_keeps_rerank", "if (mode == 1) {                    /* Alg. 1",
      "if (mode == 7) {                    /* Alg. 1", 0),
 ]

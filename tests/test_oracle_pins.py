@@ -108,6 +108,77 @@ def test_adc_dist_is_sum_of_selected_entries():
         assert oracle.adc_dist(T, code) == float(sum(int(T[s, code[s]]) for s in range(M)))
 
 
+def test_bf16_rounding_closed_form():
+    # BF16 keeps 8 significant bits.  Representable values stay; halfway
+    # cases go to the neighbour whose last kept bit is 0; anything above the
+    # halfway point rounds up (worked by hand from the binary expansions).
+    u = 2.0 ** -8                          # half a BF16 step at 1.0 (step 2^-7)
+    for x in (1.0, 1.5, 3.0, 255.0, 2.0 ** -10, 0.0, 2.0 ** 20):
+        assert oracle.round_bf16(x) == x
+    assert oracle.round_bf16(1 + u) == 1.0                        # tie, 1.0 is even
+    assert oracle.round_bf16(1 + 3 * u) == 1 + 4 * u              # tie, 1 + 2^-6 is even
+    assert oracle.round_bf16(1 + u + 2.0 ** -20) == 1 + 2 * u     # above the tie
+    assert oracle.round_bf16(1 + u - 2.0 ** -20) == 1.0           # below the tie
+    assert oracle.round_bf16(257.0) == 256.0                      # 8 bits: steps of 2 at 256
+    assert oracle.round_bf16(259.0) == 260.0                      # tie, 260 = 0b100000100 even
+    assert oracle.round_bf16(65535.0) == 65536.0
+    T = np.array([[1 + u, 1 + 3 * u, 257.0, 259.0] + [0.0] * 252], np.float32)
+    assert oracle.adc_table_bf16(T)[0, :4].tolist() == [1.0, 1 + 4 * u, 256.0, 260.0]
+
+
+def test_bf16_search_equals_fp32_when_entries_are_representable():
+    # On the chain graph every entry the search reads is (13 - c)^2 <= 169,
+    # an integer below 256 and so exact in BF16: the visits equal the FP32
+    # table's (entries of far centroids, up to 242^2, do round).
+    n = 21
+    X = np.arange(n, dtype=np.uint8)[:, None]
+    adj = np.full((n, 2), NONE, np.uint32)
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        adj[i, :len(nb)] = nb
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, 0, 1)
+    q = np.array([[13]], np.uint8)
+    T = oracle.adc_table(q[0].astype(np.float32), 1, cb)
+    assert (oracle.adc_table_bf16(T) != T).any()
+    for L in (1, 2, 3, 5):
+        a = ix.search(q, k=1, L=L, trace_cap=64)
+        b = ix.search(q, k=1, L=L, trace_cap=64, bf16=True)
+        assert b["trace"][0].tolist() == a["trace"][0].tolist() and b["ids"][0, 0] == a["ids"][0, 0]
+
+
+def test_bf16_rounding_changes_the_visit():
+    # Query (0, 0), lossless 1-dimension subspaces.  Point 1 = (17, 0) has
+    # FP32 distance 289, which BF16 rounds to 288 (a tie between 288 and 290
+    # going to the even 288); point 2 = (12, 12) has 144 + 144 = 288 exactly.
+    # With L = 1 the FP32 table keeps point 2 (288 < 289) after expanding the
+    # far medoid 0; the BF16 table sees a tie and keeps the smaller id, 1.
+    # The re-rank returns the nearest expanded node: 2 for FP32, 1 for BF16.
+    X = np.array([[200, 200], [17, 0], [12, 12]], np.uint8)
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, complete_graph(3), 0, 2)
+    q = np.zeros((1, 2), np.uint8)
+    a = ix.search(q, k=1, L=1, trace_cap=8)
+    b = ix.search(q, k=1, L=1, trace_cap=8, bf16=True)
+    assert a["trace"][0][:2].tolist() == [0, 2] and a["ids"][0, 0] == 2 and a["dist"][0, 0] == 288.0
+    assert b["trace"][0][:2].tolist() == [0, 1] and b["ids"][0, 0] == 1 and b["dist"][0, 0] == 289.0
+
+
+def test_bf16_mode_worklist_of_all_points_equals_bruteforce():
+    rng = np.random.default_rng(23)
+    n = 30
+    X = rng.integers(0, 256, size=(n, 16)).astype(np.uint8)
+    cb = rng.normal(128, 40, size=256 * 16).astype(np.float32)
+    codes = rng.integers(0, 256, size=(n, 4)).astype(np.uint8)
+    ix = oracle.Index(X, cb, codes, complete_graph(n), 3, 4)
+    Q = rng.integers(0, 256, size=(6, 16)).astype(np.uint8)
+    r = ix.search(Q, k=5, L=n, log2z=18, bf16=True)
+    for qi in range(len(Q)):
+        ids, dd = brute_ids(X, Q[qi], 5)
+        assert r["ids"][qi].tolist() == ids.tolist()
+        assert r["dist"][qi].tolist() == dd.astype(np.float32).tolist()
+
+
 def test_q8_table_closed_form():
     # Subspace 0: entries 2*pi(c), pi a permutation of 0..255 (width 510);
     # subspace 1: 100 + c (width 255); subspace 2: constant (width 0).  The
