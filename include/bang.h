@@ -75,7 +75,8 @@ typedef struct bang_search_params {
     unsigned long long *out_phase_cycles;
     /* Distance mode (bang_mode): PQ distances from an FP32 table (0, the
      * default, bit-exact with the reference order), from a BF16 table summed
-     * in FP32 (1, the reduced-precision form: half the table's shared memory),
+     * in FP32 (1, the reduced-precision form: half the table's shared memory;
+     * entries rounded to nearest, ties to even, so also deterministic),
      * or exact distances in the loop without table or re-rank (2, the
      * paper's Exact-distance variant, §5.2; results are the first k entries
      * of the final worklist), or from an 8-bit table summed exactly in

@@ -47,11 +47,12 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     return out
 
 
-def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None, exact=False, q8=False):
+def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None, exact=False, q8=False,
+                  bf16=False):
     M = M or w["M"]
     ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap, exact=exact,
-                     q8=q8)
+                     q8=q8, bf16=bf16)
 
 
 def assert_parity(g, o, trace_cap=0, exact_dist=True):
@@ -337,6 +338,29 @@ def test_exact_mode_int8():
     Q = w["queries"]
     g = gpu_search(w, Q, 10, 40, trace_cap=200, mode=bang.BANG_MODE_EXACT)
     assert_parity(g, oracle_search(w, Q, 10, 40, trace_cap=200, exact=True), trace_cap=200)
+
+
+@pytest.mark.parametrize("placement", [0, 3])
+def test_bf16_mode_bit_exact(u8small, cfg1, placement):
+    # the per-warp BF16 table rounds the FP32 entries to nearest (ties to
+    # even) and sums them in the FP32 order: bit-exact with the oracle's mode
+    for w, Q, L in ((u8small, u8small["queries"], 32), (u8small, u8small["queries"][:150], 128),
+                    (cfg1, cfg1["queries"], 64)):
+        g = gpu_search(w, Q, 10, L, trace_cap=600, mode=bang.BANG_MODE_PQ_BF16, placement=placement)
+        o = oracle_search(w, Q, 10, L, trace_cap=600, bf16=True)
+        assert_parity(g, o, trace_cap=600)
+
+
+def test_bf16_mode_uneven_subspaces_and_wide_rows():
+    for w, L in ((cases.clustered(n=8_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40,
+                                  centre="uniform100"), 40),
+                 (cases.clustered(n=6_000, nq=50, ncomp=4, dtype="f32", d=96, M=48, R=68,
+                                  centre="uniform255"), 64)):
+        Q = w["queries"]
+        for k, LL, log2z in ((10, L, 16), (1, 1, 12), (40, 2 * L, 18)):
+            g = gpu_search(w, Q, k, LL, log2z, trace_cap=300, mode=bang.BANG_MODE_PQ_BF16)
+            assert_parity(g, oracle_search(w, Q, k, LL, log2z, trace_cap=300, bf16=True),
+                          trace_cap=300)
 
 
 def test_bf16_table_recall_within_tolerance(u8small):
