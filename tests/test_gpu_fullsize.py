@@ -4,7 +4,7 @@ on sampled queries (the oracle computes those one by one):
   configuration 2 (1M u8, the benchmark workload): the whole 10,000-query
       batch in the benchmark's launches (autotuned 8-bit table, plain FP32,
       Exact-distance variant with vectors in HBM);
-  configuration 3 shape (10M f32, d=96, M=48, R=68): FP32 and 8-bit tables;
+  configuration 3 shape (10M f32, d=96, M=48, R=68): FP32, BF16 and 8-bit tables;
   configuration 4 shape (100M int8, d=100, M=50, R=64): the batched form,
       per-query k in {1, 10, 100} and L in {32, 64, 128, 256}, one persistent
       launch replayed from a CUDA graph;
@@ -102,15 +102,11 @@ def test_configuration3_shape_full_size():
     oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], 0, 48)
     q = torch.from_numpy(np.ascontiguousarray(w["queries"])).cuda()
     sel = np.arange(0, 1000, 10)
-    for mode in (0, 3):
+    for mode in (0, 1, 3):                  # FP32, BF16 and 8-bit tables
         g = _run(ix, q, 10, 128, mode, 16, trace_cap=256)
-        o = oix.search(w["queries"][sel], 10, 128, log2z=16, trace_cap=256, q8=mode == 3)
+        o = oix.search(w["queries"][sel], 10, 128, log2z=16, trace_cap=256, q8=mode == 3,
+                       bf16=mode == 1)
         _compare(g, o, sel, 256)
-    # BF16 table: re-ranked distances are the exact FP32 distances of the ids
-    g = _run(ix, q, 10, 128, 1, 16)
-    ids = g["ids"][sel].astype(np.int64)
-    ex = [[oracle.exact_dist(w["queries"][i], w["base"][j]) for j in ids[t]] for t, i in enumerate(sel)]
-    assert (g["dist"][sel] == np.array(ex, np.float32)).all()
     ix.close()
     del w, ix, oix
     gc.collect()
