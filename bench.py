@@ -231,7 +231,7 @@ def serving(bang, ix, w, L, mode, capacity_qps, log2z, seconds=2.0):
     queries (uniform), k = 10, at fractions of the measured batch throughput:
     achieved queries/s and p50/p99 latency (submit to results on the host)."""
     import threading
-    srv = bang.Server(ix, K, L, max_batch=1024, streams=4, mode=mode, bloom_log2=log2z)
+    srv = bang.Server(ix, K, L, max_batch=1024, streams=8, mode=mode, bloom_log2=log2z)
     rng = np.random.default_rng(7)
     nqall = w["queries"].shape[0]
     out = []
@@ -269,7 +269,7 @@ def serving(bang, ix, w, L, mode, capacity_qps, log2z, seconds=2.0):
                     "requests": nreq, "p50_ms": float(np.percentile(lat, 50)),
                     "p99_ms": float(np.percentile(lat, 99))})
     srv.stop()
-    return {"what": "Poisson arrivals of 1..1024-query requests, k=10, L=%d, 4 streams, "
+    return {"what": "Poisson arrivals of 1..1024-query requests, k=10, L=%d, 8 streams, "
                     "max 1024 queries per launch" % L, "points": out}
 
 
