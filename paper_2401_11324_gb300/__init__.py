@@ -335,7 +335,7 @@ class Server:
     submit() copies host queries and returns a ticket; wait() returns the
     request's ids, distances (nq x k_max) and latency in milliseconds."""
 
-    def __init__(self, index, k_max, L_max, max_batch=1024, streams=4, mode=0, bloom_log2=0):
+    def __init__(self, index, k_max, L_max, max_batch=1024, streams=8, mode=0, bloom_log2=0):
         self.index = index
         self.k_max = k_max
         cfg = bang_server_config(k_max, L_max, max_batch, streams, mode, bloom_log2)
