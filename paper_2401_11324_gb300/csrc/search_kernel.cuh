@@ -721,6 +721,38 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     Nk[j] = make_key(pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
                                                         a.M, a.Mpad), id);
                 }
+            } else if (DT != 2 && DCH == 1 && (d & 15u) == 0 && a.vecb_ok) {
+                // integer data sums exactly in any order, so one lane takes
+                // one new neighbour (its whole row) and all of them are
+                // requested at once; query words come by shuffle
+                const uint32_t nw = d / 4u;  // 32-bit words per row, <= 32
+                for (uint32_t j0 = 0; j0 < nn; j0 += kWarp) {
+                    const uint32_t j = j0 + static_cast<uint32_t>(lane);
+                    const bool act = j < nn;
+                    const uint32_t id = act ? Nid[j] : 0u;
+                    const uint4 *row = reinterpret_cast<const uint4 *>(static_cast<const E *>(a.base) +
+                                                                       static_cast<uint64_t>(id) * d);
+                    uint4 xv[8];
+#pragma unroll
+                    for (int c = 0; c < 8; ++c)
+                        xv[c] = (act && 4u * c < nw) ? __ldg(row + c) : make_uint4(0u, 0u, 0u, 0u);
+                    uint32_t acc = 0;
+#pragma unroll
+                    for (int c = 0; c < 8; ++c) {
+                        const uint32_t xw[4] = {xv[c].x, xv[c].y, xv[c].z, xv[c].w};
+#pragma unroll
+                        for (int i = 0; i < 4; ++i) {
+                            const uint32_t w = 4u * c + i;
+                            const uint32_t qw = __shfl_sync(0xFFFFFFFFu, qs.w[0], static_cast<int>(w));
+                            const uint32_t x = DT == 1 ? xw[i] ^ 0x80808080u : xw[i];
+                            if (w < nw) {
+                                const uint32_t df = __vabsdiffu4(qw, x);
+                                acc = __dp4a(df, df, acc);
+                            }
+                        }
+                    }
+                    if (act) Nk[j] = make_key(acc, id);
+                }
             } else {
                 for (uint32_t j0 = 0; j0 < nn; j0 += 4) {
                     VecShare<DT, DCH> xs[4];

@@ -332,6 +332,16 @@ def test_exact_mode_bit_exact(u8small, cfg1, placement):
         assert_parity(g, o, trace_cap=400)
 
 
+def test_exact_mode_int8_rows_of_16_byte_multiples():
+    # d = 96 int8: the one-lane-per-neighbour integer path, bias included
+    w = cases.clustered(n=8_000, nq=40, ncomp=4, dtype="i8", d=96, M=24, R=40,
+                        centre="uniform100")
+    Q = w["queries"]
+    for placement in (0, 3):
+        g = gpu_search(w, Q, 10, 40, trace_cap=200, mode=bang.BANG_MODE_EXACT, placement=placement)
+        assert_parity(g, oracle_search(w, Q, 10, 40, trace_cap=200, exact=True), trace_cap=200)
+
+
 def test_exact_mode_int8():
     w = cases.clustered(n=8_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40,
                         centre="uniform100")
