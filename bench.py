@@ -72,6 +72,9 @@ def parse():
                     help="build the PQ codes and the clustered graph with the library's GPU "
                          "builder instead of the host generator (data and ground truth stay on "
                          "the host)")
+    ap.add_argument("--gpu-truth", action="store_true",
+                    help="with --gpu-build: exact k-NN by bang_ground_truth on the GPU, checked "
+                         "against the oracle's brute force on sampled queries")
     ap.add_argument("--packed", action="store_true",
                     help="fixed forms read packed graph rows (BANG_GRAPH_PACKED)")
     ap.add_argument("--config", type=int, default=2, choices=(2, 3),
@@ -114,8 +117,22 @@ def gpu_built_workload(args, kw, device):
     the clustered graph from bang_build_pq / bang_build_cluster_graph."""
     import workload
     import paper_2401_11324_gb300 as bang
+    if args.gpu_truth:
+        kw = dict(kw, k=0)
     w = workload.clustered_data(args.config, verbose=True, **kw)
     c = w["params"]
+    if args.gpu_truth:
+        import oracle
+        t0 = time.perf_counter()
+        w["gt_ids"], w["gt_dist"] = bang.bang_ground_truth(w["base"], w["queries"], max(100, K),
+                                                           device=device)
+        t_gt = time.perf_counter() - t0
+        sel = np.linspace(0, w["queries"].shape[0] - 1, 16).astype(np.int64)
+        ids_o, dist_o = oracle.bruteforce_knn(w["base"], w["queries"][sel], max(100, K))
+        if not ((ids_o == w["gt_ids"][sel]).all() and (dist_o == w["gt_dist"][sel]).all()):
+            raise RuntimeError("GPU ground truth differs from the oracle's brute force")
+        w["truth"] = ("GPU (bang_ground_truth) in %.1f s; 16 sampled queries equal to the oracle's "
+                      "brute force" % t_gt)
     t0 = time.perf_counter()
     cb, codes = bang.bang_build_pq(w["base"], c["M"], w["pq_sample"],
                                    w["pq_init"].reshape(c["M"], 256), 10, device=device)
@@ -564,7 +581,8 @@ def main():
                    "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "l2": "512 MB flush written between timed steps",
                    "n": int(w["base"].shape[0]), "nq": nq,
-                   "index_build": w.get("index_build", "host generator (workload/)")},
+                   "index_build": w.get("index_build", "host generator (workload/)"),
+                   "ground_truth": w.get("truth", "host generator (workload/), exact")},
         "plain_form": brief(res["fp32"]),
         "forms": {f: brief(r) for f, r in list(res.items()) + list(variants.items())},
         # the binding roofline of this path is the host link (neighbour rows

@@ -309,6 +309,18 @@ int bang_build_pq(int device, const void *base, bang_dtype dtype, uint64_t n, ui
                   const uint64_t *sample, uint64_t ns, const uint64_t *init, uint32_t iters,
                   float *codebook, uint8_t *codes, void *stream);
 
+/* Exact k nearest neighbours of nq queries among n points on the GPU: the
+ * ground truth of k-recall@k (§6.3).  Squared L2; integer data exact; f32 in
+ * FP64, summed in ascending dimension order with each difference, product and
+ * sum rounded; sorted by (distance, id), padded with 0xFFFFFFFF / +inf when
+ * n < k.  base (n*d) and queries (nq*d) host or device, of dtype; out_ids and
+ * out_dist (nq*k) both host or both device.  k <= 256, d <= 4096.  Allocates
+ * device scratch (about nq*k*24*ceil(n/262144) bytes plus copies of host
+ * inputs) and blocks until done. */
+int bang_ground_truth(int device, const void *base, const void *queries, bang_dtype dtype, uint64_t n,
+                      uint32_t nq, uint32_t d, uint32_t k, uint32_t *out_ids, double *out_dist,
+                      void *stream);
+
 /* ---- Autotuner (not in the paper).  Picks, for this GPU and index, the
  * settings that change speed but not the method: the PQ table's precision
  * (bang_mode; bit m of `modes` admits mode m), whether mode 1's tables come

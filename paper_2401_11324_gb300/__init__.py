@@ -110,6 +110,7 @@ def _load():
     L.bang_server_stop.argtypes = [vp]
     L.bang_build_cluster_graph.argtypes = [i32, vp, i32, u64, u32, vp, vp, u32, vp, u32,
                                            ctypes.c_float, u32, vp, u32, vp, vp, vp]
+    L.bang_ground_truth.argtypes = [i32, vp, vp, i32, u64, u32, u32, u32, vp, vp, vp]
     L.bang_build_pq.argtypes = [i32, vp, i32, u64, u32, u32, vp, u64, vp, u32, vp, vp, vp]
     L.bang_autotune.argtypes = [vp, vp, u32, u32, u32, vp, ctypes.POINTER(bang_autotune_opts),
                                 ctypes.POINTER(bang_autotune_result), vp]
@@ -120,7 +121,7 @@ def _load():
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
               "bang_search_batched_noalloc", "bang_index_info", "bang_server_start", "bang_pq_tables",
               "bang_server_submit", "bang_server_wait", "bang_server_stop", "bang_autotune",
-              "bang_build_cluster_graph", "bang_build_pq"):
+              "bang_build_cluster_graph", "bang_build_pq", "bang_ground_truth"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -268,6 +269,19 @@ def bang_build_pq(base, M, sample, init, iters=10, device=0, stream=None):
     _check(lib().bang_build_pq(device, _ptr(base), dt, n, d, M, _ptr(sample), len(sample),
                                _ptr(init), iters, _ptr(cb), _ptr(codes), s))
     return cb, codes
+
+
+def bang_ground_truth(base, queries, k, device=0, stream=None):
+    """Exact k-NN on the GPU: (ids uint32 nq x k, distances float64 nq x k)."""
+    n, d = base.shape
+    nq = queries.shape[0]
+    dt = _DTYPES[np.dtype(str(base.dtype).replace("torch.", ""))]
+    ids = np.zeros((nq, k), np.uint32)
+    dist = np.zeros((nq, k), np.float64)
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    _check(lib().bang_ground_truth(device, _ptr(base), _ptr(queries), dt, n, nq, d, k, _ptr(ids),
+                                   _ptr(dist), s))
+    return ids, dist
 
 
 def bang_set_placement(ix, flags):

@@ -114,3 +114,29 @@ def test_pq_build_rejects_bad_ids():
         bang.bang_build_pq(X, 2, np.array([0, 1], np.uint64), init + 300)
     with pytest.raises(bang.BangError):
         bang.bang_build_pq(np.zeros((300, 40), np.uint8), 2, np.array([0], np.uint64), init)   # 20-wide
+
+
+@pytest.mark.parametrize("dt,n,d,k,nq", [
+    ("u8", 20_000, 128, 10, 50),           # rows held in registers
+    ("i8", 20_000, 100, 100, 30),          # 32-bit words, int8 offset
+    ("i8", 5_000, 99, 7, 20),              # bytes
+    ("f32", 20_000, 96, 10, 40),           # FP64 in the oracle's order
+    ("u8", 300_000, 32, 16, 20),           # more points than the threshold sample
+    ("u8", 5, 16, 10, 4),                  # fewer points than k: padding
+])
+def test_ground_truth_bit_exact(dt, n, d, k, nq):
+    rng = np.random.default_rng(n + d + k)
+    if dt == "f32":
+        X = rng.normal(size=(n, d)).astype(np.float32)
+        Q = rng.normal(size=(nq, d)).astype(np.float32)
+    elif dt == "i8":
+        X = rng.integers(-128, 128, size=(n, d)).astype(np.int8)
+        Q = rng.integers(-128, 128, size=(nq, d)).astype(np.int8)
+    else:
+        X = rng.integers(0, 8, size=(n, d)).astype(np.uint8)          # many distance ties
+        Q = rng.integers(0, 8, size=(nq, d)).astype(np.uint8)
+    ids_o, dist_o = oracle.bruteforce_knn(X, Q, k)
+    ids, dist = bang.bang_ground_truth(X, Q, k)
+    assert (ids == ids_o).all(), np.argwhere(ids != ids_o)[:5]
+    fin = np.isfinite(dist_o)
+    assert (np.isfinite(dist) == fin).all() and (dist[fin] == dist_o[fin]).all()

@@ -295,7 +295,10 @@ def clustered_data(cfg=2, n=None, nq=None, ncomp=None, k=100, train_n=256_000, v
     gi = graph_inputs(cfg, w["base"], w["labels"], ncomp, c["nx"], c["nh"])
     _, _, gmed = medoids_of_groups(w["base"], np.zeros(n, np.uint32), 1)
     t1 = time.time()
-    gt_ids, gt_dist = ground_truth(w["base"], w["queries"], k)
+    if k > 0:
+        gt_ids, gt_dist = ground_truth(w["base"], w["queries"], k)
+    else:                                       # the caller computes the ground truth
+        gt_ids, gt_dist = np.zeros((nq, 0), np.uint32), np.zeros((nq, 0))
     t2 = time.time()
     if verbose:
         print("data cfg%d n=%d: data %.1fs gt %.1fs (threads %d)" % (
