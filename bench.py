@@ -43,6 +43,9 @@ L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024)
 TARGET_RECALL = 0.9
 K = 10                      # k of the search and of recall@k (--k)
 def workload_name(args):
+    if args.config == 4:
+        return ("batched form: n=%d int8 d=100, 4096 components, %d queries, PQ M=%d, R=64, k=%d"
+                % (args.n or 100_000_000, args.nq or 10_000, args.M or 50, K))
     if args.config == 3:
         return ("precision form: n=%d f32 d=96 unit-normalised, 1024 components, %d queries, "
                 "PQ M=%d, R=68 (64 in-cluster + 4 medoid links), k=%d" % (
@@ -77,8 +80,9 @@ def parse():
                          "against the oracle's brute force on sampled queries")
     ap.add_argument("--packed", action="store_true",
                     help="fixed forms read packed graph rows (BANG_GRAPH_PACKED)")
-    ap.add_argument("--config", type=int, default=2, choices=(2, 3),
-                    help="2: mid-scale u8 (the headline); 3: the precision form (f32 d=96)")
+    ap.add_argument("--config", type=int, default=2, choices=(2, 3, 4),
+                    help="2: mid-scale u8 (the headline); 3: the precision form (f32 d=96); "
+                         "4: the batched form (100M int8, d=100; needs --gpu-build)")
     args = ap.parse_args()
     global K
     K = args.k
@@ -137,9 +141,10 @@ def gpu_built_workload(args, kw, device):
     cb, codes = bang.bang_build_pq(w["base"], c["M"], w["pq_sample"],
                                    w["pq_init"].reshape(c["M"], 256), 10, device=device)
     t1 = time.perf_counter()
-    adj = bang.bang_build_cluster_graph(w["base"], w["members"], w["gstart"], w["medoids"], c["R"],
-                                        c["alpha"], c["nx"], w["xclu"], w["hclu"].shape[1],
-                                        w["hclu"], device=device)
+    adj = workload.aligned_empty((w["base"].shape[0], c["R"]), np.uint32)   # read in place later
+    bang.bang_build_cluster_graph(w["base"], w["members"], w["gstart"], w["medoids"], c["R"],
+                                  c["alpha"], c["nx"], w["xclu"], w["hclu"].shape[1], w["hclu"],
+                                  adj=adj, device=device)
     t2 = time.perf_counter()
     w.update(codebook=cb, codes=codes, adj=adj,
              index_build={"pq_s": round(t1 - t0, 2), "graph_s": round(t2 - t1, 2),

@@ -15,6 +15,7 @@
 // rerun with room for the longest list.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <cstring>
 #include <string>
@@ -28,7 +29,7 @@ namespace {
 constexpr uint32_t kNo = 0xFFFFFFFFu;
 constexpr int kW = 32;
 constexpr int kKPL = 8;                  // top-k entries per lane in pass 1: k <= 256
-constexpr uint32_t kTileQ = 32;          // queries per CTA in pass 2
+constexpr uint32_t kTileQ = 128;         // at most this many queries per CTA in pass 2
 constexpr uint32_t kSample = 262144;
 
 struct GtArgs {
@@ -44,6 +45,7 @@ struct GtArgs {
     uint64_t cap;
     uint32_t *out_ids;
     double *out_dist;
+    uint32_t tileq;              // queries per CTA in pass 2 (48 KB of rows at most)
     uint32_t words;              // integer rows readable as 32-bit words (d % 4 == 0, aligned)
     uint32_t regrow;             // integer rows of 16..128 bytes in 16-byte steps, 16-byte aligned
 };
@@ -174,8 +176,8 @@ __global__ void sample_threshold(const GtArgs g, uint64_t S)
 __global__ void collect(const GtArgs g)
 {
     extern __shared__ __align__(16) unsigned char qs[];
-    const uint32_t q0 = blockIdx.y * kTileQ;
-    const uint32_t nt = g.nq - q0 < kTileQ ? g.nq - q0 : kTileQ;
+    const uint32_t q0 = blockIdx.y * g.tileq;
+    const uint32_t nt = g.nq - q0 < g.tileq ? g.nq - q0 : g.tileq;
     const size_t rowb = static_cast<size_t>(g.d) * (g.dtype == 2 ? 4 : 1);
     for (size_t i = threadIdx.x; i < nt * rowb; i += blockDim.x)
         qs[i] = static_cast<const unsigned char *>(query_row(g, q0))[i];
@@ -311,7 +313,8 @@ extern "C" int bang_ground_truth(int device, const void *base, const void *queri
         return gtfail(BANG_EINVAL, "bang_ground_truth: need 0 < n < 2^32 - 1, 0 < d <= 4096, 1 <= k <= 256");
     if (nq == 0) return BANG_OK;
     const size_t esz = dtype == BANG_F32 ? 4 : 1;
-    if (kTileQ * d * esz > 48u * 1024u) return gtfail(BANG_EINVAL, "bang_ground_truth: rows too long");
+    const uint32_t tileq = static_cast<uint32_t>(std::min<size_t>(kTileQ, (48u * 1024u) / (d * esz)));
+    if (tileq == 0) return gtfail(BANG_EINVAL, "bang_ground_truth: rows too long");
     int prev = -1;
     cudaGetDevice(&prev);
     if (cudaSetDevice(device) != cudaSuccess) {
@@ -350,6 +353,7 @@ extern "C" int bang_ground_truth(int device, const void *base, const void *queri
     g.thr_out = thr.p;
     g.thr = thr.p;
     g.cnt = cnt.p;
+    g.tileq = tileq;
     {
         const uintptr_t ab = reinterpret_cast<uintptr_t>(B), aq = reinterpret_cast<uintptr_t>(Q);
         g.words = dtype != BANG_F32 && d % 4 == 0 && ab % 4 == 0 && aq % 4 == 0;
@@ -361,7 +365,7 @@ extern "C" int bang_ground_truth(int device, const void *base, const void *queri
     uint64_t cap = 2ull * k * ((n + S - 1) / S) + 256;
     int sms = 0;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-    const uint32_t tiles = (nq + kTileQ - 1) / kTileQ;
+    const uint32_t tiles = (nq + tileq - 1) / tileq;
     const uint32_t gx = static_cast<uint32_t>((static_cast<uint64_t>(sms) * 8 + tiles - 1) / tiles) + 1;
     for (int attempt = 0; attempt < 2; ++attempt) {
         GT_TRY(cd.alloc(cap * nq));
@@ -370,7 +374,7 @@ extern "C" int bang_ground_truth(int device, const void *base, const void *queri
         g.cd = cd.p;
         g.ci = ci.p;
         g.cap = cap;
-        collect<<<dim3(gx, tiles), 256, kTileQ * d * esz, st>>>(g);
+        collect<<<dim3(gx, tiles), 256, tileq * d * esz, st>>>(g);
         GT_TRY(cudaGetLastError());
         std::vector<uint32_t> c(nq);
         GT_TRY(cudaMemcpyAsync(c.data(), cnt.p, nq * 4, cudaMemcpyDeviceToHost, st));

@@ -19,6 +19,9 @@ Configurations (the recipe of each is in ``CONFIGS``):
   3  n=10,000,000 f32 d=96, 1,024 components, centres ~N(0, I) scaled to unit
      length, x = normalise(c + 0.1 z); 10,000 queries; PQ M=48; clustered
      graph with 64 in-cluster neighbours and 4 medoid links (R=68).
+  4  n=100,000,000 int8 d=100, 4,096 components, centres ~U[-100,100]^d,
+     sigma 16, clipped to -128..127; 10,000 queries; PQ M=50; clustered graph
+     R=64 (built on the GPU: the host cores would take days).
 Seeds: data 1000+cfg, queries 2000+cfg, PQ 3000+cfg, graph 4000+cfg.
 """
 import ctypes
@@ -45,6 +48,10 @@ CONFIGS = {
     3: dict(n=10_000_000, nq=10_000, d=96, dtype="f32", ncomp=1024, centre="unitnormal",
             centre_scale=None, sigma=0.1, normalise=True, M=48, R=68, alpha=1.2, nx=4, nh=32,
             k=10, L=128),
+    # batched form: int8 mixture clipped to -128..127; 60 in-cluster neighbours
+    # plus 4 medoid links (R = 64)
+    4: dict(n=100_000_000, nq=10_000, d=100, dtype="i8", ncomp=4096, centre="uniform100",
+            centre_scale=None, sigma=16.0, M=50, R=64, alpha=1.2, nx=4, nh=32, k=10, L=128),
 }
 
 _DTN = {"u8": np.uint8, "i8": np.int8, "f32": np.float32}
@@ -307,9 +314,10 @@ def clustered_data(cfg=2, n=None, nq=None, ncomp=None, k=100, train_n=256_000, v
                gt_dist=gt_dist, pq_sample=sample, pq_init=sample[init.astype(np.int64)],
                members=gi["members"], gstart=gi["gstart"], medoids=gi["medoids"], xclu=gi["xclu"],
                hclu=gi["hclu"], medoid=np.int64(gmed[0]))
-    tmp = path + ".tmp.npz"
-    np.savez(tmp, **out)
-    os.replace(tmp, path)
+    if w["base"].nbytes <= (2 << 30):          # larger datasets are regenerated, not cached
+        tmp = path + ".tmp.npz"
+        np.savez(tmp, **out)
+        os.replace(tmp, path)
     out["medoid"] = int(gmed[0])
     out["params"] = dict(c, n=n, nq=nq, ncomp=ncomp)
     return out
