@@ -45,7 +45,7 @@ struct GtArgs {
     uint64_t cap;
     uint32_t *out_ids;
     double *out_dist;
-    uint32_t tileq;              // queries per CTA in pass 2 (48 KB of rows at most)
+    uint32_t tileq;              // queries per CTA in pass 2 (46 KB of rows at most)
     uint32_t words;              // integer rows readable as 32-bit words (d % 4 == 0, aligned)
     uint32_t regrow;             // integer rows of 16..128 bytes in 16-byte steps, 16-byte aligned
 };
@@ -313,7 +313,8 @@ extern "C" int bang_ground_truth(int device, const void *base, const void *queri
         return gtfail(BANG_EINVAL, "bang_ground_truth: need 0 < n < 2^32 - 1, 0 < d <= 4096, 1 <= k <= 256");
     if (nq == 0) return BANG_OK;
     const size_t esz = dtype == BANG_F32 ? 4 : 1;
-    const uint32_t tileq = static_cast<uint32_t>(std::min<size_t>(kTileQ, (48u * 1024u) / (d * esz)));
+    // query rows in dynamic shared memory; with the thresholds (static) under 48 KB
+    const uint32_t tileq = static_cast<uint32_t>(std::min<size_t>(kTileQ, (46u * 1024u) / (d * esz)));
     if (tileq == 0) return gtfail(BANG_EINVAL, "bang_ground_truth: rows too long");
     int prev = -1;
     cudaGetDevice(&prev);
