@@ -20,8 +20,9 @@ Configurations (the recipe of each is in ``CONFIGS``):
      length, x = normalise(c + 0.1 z); 10,000 queries; PQ M=48; clustered
      graph with 64 in-cluster neighbours and 4 medoid links (R=68).
   4  n=100,000,000 int8 d=100, 4,096 components, centres ~U[-100,100]^d,
-     sigma 16, clipped to -128..127; 10,000 queries; PQ M=50; clustered graph
-     R=64 (built on the GPU: the host cores would take days).
+     low-rank components as in 2 (A: d x 12 with N(0, 16^2/12) entries, noise
+     4), rounded and clipped to -128..127; 10,000 queries; PQ M=50; clustered
+     graph R=64 (built on the GPU: the host cores would take days).
 Seeds: data 1000+cfg, queries 2000+cfg, PQ 3000+cfg, graph 4000+cfg.
 """
 import ctypes
@@ -51,7 +52,8 @@ CONFIGS = {
     # batched form: int8 mixture clipped to -128..127; 60 in-cluster neighbours
     # plus 4 medoid links (R = 64)
     4: dict(n=100_000_000, nq=10_000, d=100, dtype="i8", ncomp=4096, centre="uniform100",
-            centre_scale=None, sigma=16.0, M=50, R=64, alpha=1.2, nx=4, nh=32, k=10, L=128),
+            centre_scale=None, sigma=16.0, rank=12, noise=4.0, M=50, R=64, alpha=1.2, nx=4,
+            nh=32, k=10, L=128),
 }
 
 _DTN = {"u8": np.uint8, "i8": np.int8, "f32": np.float32}
