@@ -268,6 +268,47 @@ __device__ __forceinline__ uint32_t pq_dist_bits(const void *T, const uint8_t *r
     return pq_dist_bits_g<MODE>(T, [row16](uint32_t c16) { return __ldg(row16 + c16); }, M, Mpad);
 }
 
+// Part of an 8-bit-table PQ distance: the 8-byte chunks c = part, part + P,
+// ... of the code row (rows are padded to 16 bytes).  P lanes together give
+// the exact integer sum of the whole row.
+template <uint32_t P>
+__device__ __forceinline__ uint32_t adc_q8_part(const uint8_t *__restrict__ T, const uint8_t *row, uint32_t M,
+                                                uint32_t Mpad, uint32_t part)
+{
+    uint32_t p[4] = {0u, 0u, 0u, 0u};
+    const uint2 *row8 = reinterpret_cast<const uint2 *>(row);
+    for (uint32_t c = part; c < Mpad / 8u; c += P) {
+        const uint2 v = __ldg(row8 + c);
+        const uint32_t w[2] = {v.x, v.y};
+        const uint8_t *tc = T + c * 8u * 256u;
+        if (c * 8u + 8u <= M) {
+#pragma unroll
+            for (int b = 0; b < 8; ++b) p[b & 3] += tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)];
+        } else {
+#pragma unroll
+            for (int b = 0; b < 8; ++b)
+                if (c * 8u + b < M) p[b & 3] += tc[b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)];
+        }
+    }
+    return (p[0] + p[1]) + (p[2] + p[3]);
+}
+
+// 8-bit-table PQ distances of up to 32 / P new neighbours, P lanes each:
+// neighbour j = lane / P, its key left in lane P*j (kv set there only).
+template <uint32_t P>
+__device__ __forceinline__ void pq_q8_split(const SearchArgs &a, const uint8_t *T, const uint32_t *Nid,
+                                            uint32_t nn, int lane, uint64_t &kk, bool &kv)
+{
+    const uint32_t j = static_cast<uint32_t>(lane) / P, part = static_cast<uint32_t>(lane) % P;
+    const bool act = j < nn;
+    const uint32_t id = act ? Nid[j] : 0u;
+    uint32_t s = act ? adc_q8_part<P>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad, a.M, a.Mpad, part) : 0u;
+#pragma unroll
+    for (uint32_t h = 1; h < P; h <<= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, static_cast<int>(h));
+    kv = act && part == 0u;
+    kk = kv ? make_key(s, id) : ~0ull;
+}
+
 template <int DT, int DCH> struct VecShare {
     float f[DT == 2 ? 4 * DCH : 1];
     uint32_t w[DT == 2 ? 1 : DCH];
@@ -510,18 +551,17 @@ __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv
     }
 }
 
-struct PhaseClock {
-    bool on;
-    unsigned long long t, acc[kPhases];
-    __device__ __forceinline__ explicit PhaseClock(bool enabled) : on(enabled), t(0)
+template <bool ON> struct PhaseClock {
+    unsigned long long t, acc[ON ? kPhases : 1];
+    __device__ __forceinline__ PhaseClock() : t(0)
     {
 #pragma unroll
-        for (int i = 0; i < kPhases; ++i) acc[i] = 0;
-        if (on) t = clock64();
+        for (int i = 0; i < (ON ? kPhases : 1); ++i) acc[i] = 0;
+        if constexpr (ON) t = clock64();
     }
     __device__ __forceinline__ void mark(int ph)
     {
-        if (on) {
+        if constexpr (ON) {
             const unsigned long long now = clock64();
             acc[ph] += now - t;
             t = now;
@@ -529,7 +569,7 @@ struct PhaseClock {
     }
 };
 
-template <int DT, int RPL, int DCH, int MODE, bool NC>
+template <int DT, int RPL, int DCH, int MODE, bool NC, bool PH>
 __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 {
     using E = typename Elem<DT>::T;
@@ -582,7 +622,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             continue;
         }
         const uint32_t iter_cap = a.iter_cap ? a.iter_cap : 8u * L + 64u;
-        PhaseClock clk(a.phase_cycles != nullptr);
+        PhaseClock<PH> clk;
         const unsigned long long t_start = clk.t;
         // ---- query: FP32 copy in shared memory, this lane's share in registers
         const E *qp = static_cast<const E *>(a.queries) + static_cast<uint64_t>(q) * d;
@@ -707,6 +747,16 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             // ---- distances of the new neighbours: PQ (§4.4), one lane per
             // neighbour; or exact (§5.2), the warp per neighbour, four
             // neighbours' vectors requested at a time
+            // Keys of the new neighbours: in registers where one lane computed
+            // them (kk[t], valid where kv[t]), otherwise in Nk[0..nn).
+            uint64_t kk[RPL];
+            bool kv[RPL];
+#pragma unroll
+            for (int t = 0; t < RPL; ++t) {
+                kk[t] = ~0ull;
+                kv[t] = false;
+            }
+            bool in_regs = false;
             if constexpr (NC) {              // code rows arrived with the node: the lane that holds them
 #pragma unroll
                 for (int r = 0; r < RPL; ++r) {
@@ -716,10 +766,22 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                                                                 a.M, a.Mpad), nd.nb[r]);
                 }
             } else if (kPQ) {
-                for (uint32_t j = lane; j < nn; j += kWarp) {
-                    const uint32_t id = Nid[j];
-                    Nk[j] = make_key(pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
-                                                        a.M, a.Mpad), id);
+                in_regs = true;
+                if (MODE == kModeQ8 && nn <= 8u) {           // exact integer sums: split each row
+                    pq_q8_split<4>(a, static_cast<const uint8_t *>(T), Nid, nn, lane, kk[0], kv[0]);
+                } else if (MODE == kModeQ8 && nn <= 16u) {
+                    pq_q8_split<2>(a, static_cast<const uint8_t *>(T), Nid, nn, lane, kk[0], kv[0]);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < RPL; ++t) {
+                        const uint32_t j = lane + kWarp * t;
+                        if (j < nn) {
+                            const uint32_t id = Nid[j];
+                            kk[t] = make_key(pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
+                                                                a.M, a.Mpad), id);
+                            kv[t] = true;
+                        }
+                    }
                 }
             } else if (DT != 2 && DCH == 1 && (d & 15u) == 0 && a.vecb_ok) {
                 // integer data sums exactly in any order, so one lane takes
@@ -775,18 +837,45 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             }
             ndist += nn;
             __syncwarp();
+            if (!in_regs) {
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    const uint32_t j = lane + kWarp * t;
+                    kv[t] = j < nn;
+                    kk[t] = kv[t] ? Nk[j] : ~0ull;
+                }
+                __syncwarp();
+            }
+            // New keys behind the last entry of a full worklist land at L or
+            // later, and so does every larger key: drop them here, so that
+            // only keys that enter the list are merged (§4.6-§4.7); the rest
+            // are compacted into Nk[0..nm).
+            uint32_t nm = 0;
+            uint64_t bestn = ~0ull;
+            {
+                const uint64_t last = nl == L ? Lk[L - 1] >> 1 : ~0ull;
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    const bool keep = kv[t] && (kk[t] >> 1) < last;
+                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+                    if (keep) {
+                        Nk[nm + __popc(bal & ((1u << lane) - 1u))] = kk[t];
+                        bestn = kk[t] < bestn ? kk[t] : bestn;
+                    }
+                    nm += __popc(bal);
+                }
+            }
+            __syncwarp();
             clk.mark(kPhDistance);
 
             // ---- eager next node, §4.5: the best of the new neighbours and
-            // the first unvisited worklist entry after u*; prefetch its lists
+            // the first unvisited worklist entry after u*; prefetch its lists.
+            // A dropped key is never the best: the first unvisited entry, if
+            // any, precedes it, and otherwise the search ends in the merge.
             uint64_t best = ~0ull;
             {
-                for (uint32_t j = lane; j < nn; j += kWarp) best = Nk[j] < best ? Nk[j] : best;
-                best = lkey < best ? lkey : best;
+                best = lkey < bestn ? lkey : bestn;
                 best = warp_min_key(best);
-                // the best new neighbour can still fall off the end of a full
-                // worklist of expanded entries; whether a next node exists is
-                // settled by the merge below
                 if (kPQ) xu = nd.x;              // wait for the vector only here
                 if (best != ~0ull) {
                     cur = key_id(best);
@@ -832,44 +921,23 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 
             // ---- merge the new neighbours into the worklist, §4.6-§4.7.
             // Output position = own index + rank in the other list (keys are
-            // unique).  A new key's rank in the worklist comes from a binary
-            // search, its rank among the new keys from a count; the insertion
-            // points, stored in the order of the new keys, are nondecreasing,
-            // so a worklist entry's shift is one more binary search among
-            // them.  Entries move right only: groups of up to 8 chunks are
-            // read, then written, from the end of the list down to the first
-            // insertion point.
+            // unique: a new neighbour was never seen, so its id is not in the
+            // list).  A new key's rank in the worklist comes from a 4-ary
+            // search, its rank among the new keys from a count; its output
+            // position is marked in a bit mask.  Every other output position
+            // p takes worklist entry p - (new keys before p): entries move
+            // right only, so groups of up to 8 chunks are read, then written,
+            // from the end of the list down to the first insertion point.
             uint32_t npos = 0;               // new position of `best`, plus one
-            // New keys behind the last entry of a full worklist land at L or
-            // later, and so does every larger key: drop them first, so that
-            // only keys that enter the list are ranked (they are the
-            // smallest, so their ranks among the new keys do not change).
-            uint32_t nm = nn;
-            if (nn > 0 && nl == L) {
-                const uint64_t last = Lk[L - 1] >> 1;
-                uint64_t kk[RPL];
-                bool keep[RPL];
-#pragma unroll
-                for (int t = 0; t < RPL; ++t) {
-                    const uint32_t j = lane + kWarp * t;
-                    kk[t] = j < nn ? Nk[j] : 0ull;
-                    keep[t] = j < nn && (kk[t] >> 1) < last;
-                }
-                __syncwarp();
-                nm = 0;
-#pragma unroll
-                for (int t = 0; t < RPL; ++t) {
-                    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep[t]);
-                    if (keep[t]) Nk[nm + __popc(bal & ((1u << lane) - 1u))] = kk[t];
-                    nm += __popc(bal);
-                }
-                __syncwarp();
-            }
             if (nm > 0) {
-                uint32_t *ins = Nid;         // ids are in the keys now; reuse
+                uint32_t *obits = Nid;       // ids are in the keys now: output-position bits (L <= 1024)
+                const uint32_t nl2 = nl + nm < L ? nl + nm : L;
+                const uint32_t nw = (nl2 + 31u) >> 5;
+                if (static_cast<uint32_t>(lane) < nw) obits[lane] = 0u;
                 uint64_t xk[RPL];
                 uint32_t xpos[RPL];
                 uint32_t rmin = 0xFFFFFFFFu;
+                const uint32_t b4 = 1u << ((31 - __clz(nl)) & ~1);     // largest power of 4 <= nl
 #pragma unroll
                 for (int t = 0; t < RPL; ++t) {
                     const uint32_t j = lane + kWarp * t;
@@ -877,17 +945,18 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     xpos[t] = 0xFFFFFFFFu;
                     if (j < nm) {
                         const uint64_t x = Nk[j];
-                        uint32_t lo = 0, hi = nl;
-                        while (lo < hi) {
-                            const uint32_t mid = (lo + hi) >> 1;
-                            if ((Lk[mid] >> 1) < (x >> 1)) lo = mid + 1;
-                            else hi = mid;
+                        uint32_t lo = 0;     // #{worklist keys < x}
+                        for (uint32_t b = b4; b != 0u; b >>= 2) {
+                            const uint32_t c1 = lo + b, c2 = c1 + b, c3 = c2 + b;
+                            const uint32_t m = static_cast<uint32_t>(c1 <= nl && Lk[c1 - 1u] < x) +
+                                               static_cast<uint32_t>(c2 <= nl && Lk[c2 - 1u] < x) +
+                                               static_cast<uint32_t>(c3 <= nl && Lk[c3 - 1u] < x);
+                            lo += b * m;
                         }
                         uint32_t rn = 0, tt = 0;
                         for (; tt + 4 <= nm; tt += 4)
                             rn += (Nk[tt] < x) + (Nk[tt + 1] < x) + (Nk[tt + 2] < x) + (Nk[tt + 3] < x);
                         for (; tt < nm; ++tt) rn += Nk[tt] < x;
-                        ins[rn] = lo;
                         xk[t] = x;
                         xpos[t] = lo + rn;
                         rmin = lo < rmin ? lo : rmin;
@@ -895,33 +964,45 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 }
                 rmin = __reduce_min_sync(0xFFFFFFFFu, rmin);
                 __syncwarp();
+#pragma unroll
+                for (int t = 0; t < RPL; ++t)
+                    if (xpos[t] < L) atomicOr(&obits[xpos[t] >> 5], 1u << (xpos[t] & 31u));
+                __syncwarp();
+                // lane c: the new keys' positions in chunk c, and how many lie below it
+                const uint32_t wbits = static_cast<uint32_t>(lane) < nw ? obits[lane] : 0u;
+                uint32_t pre = __popc(wbits);
+#pragma unroll
+                for (int h = 1; h < kWarp; h <<= 1) {
+                    const uint32_t v = __shfl_up_sync(0xFFFFFFFFu, pre, h);
+                    if (lane >= h) pre += v;
+                }
+                pre -= __popc(wbits);
                 clk.mark(kPhMergeRank);
                 const int32_t cmin = static_cast<int32_t>(rmin >> 5);
-                for (int32_t gtop = static_cast<int32_t>((nl - 1) >> 5); gtop >= cmin; gtop -= 8) {
+                const uint32_t lt = (1u << lane) - 1u;
+                for (int32_t ctop = static_cast<int32_t>(nw) - 1; ctop >= cmin; ctop -= 8) {
                     uint64_t key[8];
-                    uint32_t pos[8];
+                    uint32_t dst[8];
 #pragma unroll
                     for (int g = 0; g < 8; ++g) {
-                        const int32_t c = gtop - g;
-                        const uint32_t i = static_cast<uint32_t>(c) * 32u + lane;
+                        const int32_t c = ctop - g;
                         key[g] = 0;
-                        pos[g] = 0xFFFFFFFFu;
-                        if (c >= cmin && i < nl && i >= rmin) {
-                            key[g] = Lk[i];
-                            uint32_t lo = 0, hi = nm;    // #{new: insertion point <= i}
-                            while (lo < hi) {
-                                const uint32_t mid = (lo + hi) >> 1;
-                                if (ins[mid] <= i) lo = mid + 1;
-                                else hi = mid;
+                        dst[g] = 0xFFFFFFFFu;
+                        if (c >= cmin) {
+                            const uint32_t w = __shfl_sync(0xFFFFFFFFu, wbits, c);
+                            const uint32_t below = __shfl_sync(0xFFFFFFFFu, pre, c) + __popc(w & lt);
+                            const uint32_t p = static_cast<uint32_t>(c) * 32u + lane;
+                            if (p < nl2 && p >= rmin && !((w >> lane) & 1u)) {
+                                key[g] = Lk[p - below];
+                                dst[g] = p;
+                                if (key[g] == best) npos = p + 1;
                             }
-                            pos[g] = i + lo;
-                            if (key[g] == best && pos[g] < L) npos = pos[g] + 1;
                         }
                     }
                     __syncwarp();
 #pragma unroll
                     for (int g = 0; g < 8; ++g)
-                        if (pos[g] < L) Lk[pos[g]] = key[g];
+                        if (dst[g] != 0xFFFFFFFFu) Lk[dst[g]] = key[g];
                     __syncwarp();
                 }
                 clk.mark(kPhMergeShift);
@@ -933,7 +1014,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     }
                 }
                 __syncwarp();
-                nl = nl + nm < L ? nl + nm : L;
+                nl = nl2;
                 npos = __reduce_max_sync(0xFFFFFFFFu, npos);
                 if (npos == 0 && lnext >= 0 && best == lkey)      // in the untouched prefix
                     npos = static_cast<uint32_t>(lnext) + 1;
@@ -986,11 +1067,13 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 }
             }
         }
-        if (clk.on && lane == 0) {
-            clk.acc[kPhTotal] = clock64() - t_start;
+        if constexpr (PH) {
+            if (lane == 0) {
+                clk.acc[kPhTotal] = clock64() - t_start;
 #pragma unroll
-            for (int i = 0; i < kPhases; ++i)
-                a.phase_cycles[static_cast<uint64_t>(q) * kPhases + i] = clk.acc[i];
+                for (int i = 0; i < kPhases; ++i)
+                    a.phase_cycles[static_cast<uint64_t>(q) * kPhases + i] = clk.acc[i];
+            }
         }
         if (lane == 0) {
             if (a.out_iters) a.out_iters[q] = iters;
@@ -1003,10 +1086,10 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 
 // Launch for one mode: dispatch on element type, neighbours per lane
 // (R <= 64 or <= 128) and 128-dimension chunks per lane (d <= 128 or <= 512).
-template <int DT, int RPL, int DCH, int MODE, bool NC = false>
+template <int DT, int RPL, int DCH, int MODE, bool NC, bool PH>
 cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, NC>,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, NC, PH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     uint32_t grid = a.nq;
@@ -1014,15 +1097,24 @@ cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE, NC>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE, NC, PH>,
                                                                32, smem)) != cudaSuccess)
             return e;
         const uint64_t want = static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1) *
                               (a.grid_mult ? a.grid_mult : 1u);
         grid = static_cast<uint32_t>(want < a.nq ? want : a.nq);
     }
-    search_kernel<DT, RPL, DCH, MODE, NC><<<grid, 32, smem, st>>>(a);
+    search_kernel<DT, RPL, DCH, MODE, NC, PH><<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
+}
+
+// The per-phase clock (SearchArgs::phase_cycles) is a separate instantiation,
+// so the timed kernel carries none of its registers or branches.
+template <int DT, int RPL, int DCH, int MODE, bool NC = false>
+cudaError_t launch_ph(const SearchArgs &a, size_t smem, cudaStream_t st)
+{
+    return a.phase_cycles ? launch_one<DT, RPL, DCH, MODE, NC, true>(a, smem, st)
+                          : launch_one<DT, RPL, DCH, MODE, NC, false>(a, smem, st);
 }
 
 template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st)
@@ -1030,14 +1122,14 @@ template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size
     const bool narrow = a.d <= 128, wide_r = a.R > 64;
     if constexpr (MODE != kModeExact) {
         if (a.ncodes) {                // neighbour-code layout: R <= 64, d <= 128, checked by the caller
-            if (dtype == 0) return launch_one<0, 2, 1, MODE, true>(a, smem, st);
-            if (dtype == 1) return launch_one<1, 2, 1, MODE, true>(a, smem, st);
-            return launch_one<2, 2, 1, MODE, true>(a, smem, st);
+            if (dtype == 0) return launch_ph<0, 2, 1, MODE, true>(a, smem, st);
+            if (dtype == 1) return launch_ph<1, 2, 1, MODE, true>(a, smem, st);
+            return launch_ph<2, 2, 1, MODE, true>(a, smem, st);
         }
     }
 #define BANG_DISPATCH(DT)                                                                    \
-    return wide_r ? (narrow ? launch_one<DT, 4, 1, MODE>(a, smem, st) : launch_one<DT, 4, 4, MODE>(a, smem, st)) \
-                  : (narrow ? launch_one<DT, 2, 1, MODE>(a, smem, st) : launch_one<DT, 2, 4, MODE>(a, smem, st))
+    return wide_r ? (narrow ? launch_ph<DT, 4, 1, MODE>(a, smem, st) : launch_ph<DT, 4, 4, MODE>(a, smem, st)) \
+                  : (narrow ? launch_ph<DT, 2, 1, MODE>(a, smem, st) : launch_ph<DT, 2, 4, MODE>(a, smem, st))
     if (dtype == 0) { BANG_DISPATCH(0); }
     if (dtype == 1) { BANG_DISPATCH(1); }
     BANG_DISPATCH(2);
