@@ -431,8 +431,9 @@ __device__ __forceinline__ void unpack_ids(const SearchArgs &a, int lane, uint32
         const uint32_t r = static_cast<uint32_t>(lane + kWarp * t);
         const uint32_t bit = r * b, wi = bit >> 5, o = bit & 31u;
         uint32_t lo = 0, hi = 0;
+        // ids r < 32(t + 1) of at most 32 bits lie in words below 32(t + 1)
 #pragma unroll
-        for (int s = 0; s < RPL; ++s) {
+        for (int s = 0; s <= t; ++s) {
             const uint32_t v0 = __shfl_sync(0xFFFFFFFFu, w[s], static_cast<int>(wi & 31u));
             const uint32_t v1 = __shfl_sync(0xFFFFFFFFu, w[s], static_cast<int>((wi + 1u) & 31u));
             if (static_cast<uint32_t>(s) == (wi >> 5)) lo = v0;
@@ -723,8 +724,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 if (id != kNone) {
                     p1[r] = fnv1a32_id(id) & zmask;
                     p2[r] = fnv1a64_id_folded(id) & zmask;
-                    const bool hit = ((bloom[p1[r] >> 5] >> (p1[r] & 31u)) & 1u) &&
-                                     ((bloom[p2[r] >> 5] >> (p2[r] & 31u)) & 1u);
+                    const uint32_t w1 = bloom[p1[r] >> 5], w2 = bloom[p2[r] >> 5];   // both loads at once
+                    const bool hit = (w1 >> (p1[r] & 31u)) & (w2 >> (p2[r] & 31u)) & 1u;
                     fresh[r] = !hit;
                 }
             }
