@@ -18,7 +18,7 @@ RTOL = 1e-5
 
 
 def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
-               placement=0, prefetch_depth=0):
+               placement=0, prefetch_depth=0, phases=False):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     if placement:
@@ -35,14 +35,17 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     status = torch.empty(nq, dtype=torch.int32, device=dev)
     ndist = torch.empty(nq, dtype=torch.int32, device=dev)
     trace = torch.zeros((nq, max(trace_cap, 1)), dtype=torch.int32, device=dev)
+    ph = torch.zeros((nq, len(bang.PHASES)), dtype=torch.int64, device=dev) if phases else None
     p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
                          out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
-                         mode=mode, prefetch_depth=prefetch_depth)
+                         mode=mode, prefetch_depth=prefetch_depth, out_phase_cycles=ph)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
                iters=iters.cpu().numpy().view(np.uint32), status=status.cpu().numpy(),
                ndist=ndist.cpu().numpy().view(np.uint32), trace=trace.cpu().numpy().view(np.uint32))
+    if phases:
+        out["phases"] = ph.cpu().numpy()
     ix.close()
     return out
 
@@ -290,6 +293,22 @@ def test_speculative_prefetch_gives_identical_results(u8small, cfg1, mode, flags
         g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags, prefetch_depth=2)
         for f in ("ids", "dist", "iters", "ndist", "trace"):
             assert (g[f] == ref[f]).all(), (mode, flags, f)
+
+
+@pytest.mark.parametrize("mode,flags", [(0, 0), (1, 0), (2, 3), (3, 4)])
+def test_phase_clock_instantiation_gives_identical_results(u8small, mode, flags):
+    # out_phase_cycles selects a separate instantiation of the kernel with
+    # the per-phase clock; visits and results are those of the plain one, and
+    # the phases (table and loop) add up to at most the whole query's cycles
+    Q = u8small["queries"][:100]
+    ref = gpu_search(u8small, Q, 10, 64, trace_cap=300, mode=mode, placement=flags)
+    g = gpu_search(u8small, Q, 10, 64, trace_cap=300, mode=mode, placement=flags, phases=True)
+    for f in ("ids", "dist", "iters", "ndist", "trace"):
+        assert (g[f] == ref[f]).all(), (mode, flags, f)
+    ph = g["phases"]
+    assert (ph >= 0).all()
+    assert (ph[:, -1] > 0).all()
+    assert (ph[:, :-1].sum(1) <= ph[:, -1]).all()
 
 
 def test_packed_graph_rows_wide_rows():

@@ -50,11 +50,11 @@ CONFIGS = {
             centre_scale=None, sigma=0.1, normalise=True, M=48, R=68, alpha=1.2, nx=4, nh=32,
             k=10, L=128),
     # batched form: int8 mixture clipped to -128..127; 60 in-cluster neighbours
-    # plus 4 links to the medoids of nearby clusters (R = 64): with 4,096
-    # clusters, links to random clusters leave the search too few routes
+    # plus 4 links to other clusters' medoids (R = 64), half to nearby
+    # clusters and half to random ones
     4: dict(n=100_000_000, nq=10_000, d=100, dtype="i8", ncomp=4096, centre="uniform100",
             centre_scale=None, sigma=16.0, rank=12, noise=4.0, M=50, R=64, alpha=1.2, nx=4,
-            nh=32, k=10, L=128, links="nearest"),
+            nh=32, k=10, L=128, links="mixed"),
 }
 
 _DTN = {"u8": np.uint8, "i8": np.int8, "f32": np.float32}
@@ -219,19 +219,33 @@ def graph_inputs(cfg, base, labels, ng, nx, nh):
     order, gstart, meds = medoids_of_groups(base, labels, ng)
     rng = np.random.default_rng(4000 + cfg)
     own = labels.astype(np.int64)
-    if CONFIGS.get(cfg, {}).get("links") == "nearest":
-        # links to clusters whose medoids are near this cluster's: each point
-        # to nx of the 2*nx nearest, each medoid to the nh nearest.  Squared
-        # distances between integer medoids are exact in FP64 (integers
-        # below 2^53), so the order is the same on every machine.
+    if CONFIGS.get(cfg, {}).get("links") == "mixed":
+        # half of the links go to clusters whose medoids are near this
+        # cluster's (each point: nx/2 of the nx nearest; each medoid: its
+        # nh/2 nearest), half to random other clusters, so that greedy routing
+        # has both long jumps and local steps.  Squared distances between
+        # integer medoids are exact in FP64 (integers below 2^53), so the
+        # order is the same on every machine.
         mv = base[meds.astype(np.int64)].astype(np.float64)
         g = mv @ mv.T
         sq = np.diag(g).copy()
         dm = sq[:, None] + sq[None, :] - 2.0 * g
         np.fill_diagonal(dm, np.inf)
         near = np.argsort(dm, axis=1, kind="stable")
-        xclu = near[own[:, None], rng.integers(0, min(2 * nx, ng - 1), size=(n, nx))]
-        hclu = near[:, :min(nh, ng - 1)] if nh else np.zeros((ng, 0), np.int64)
+        xn = nx // 2
+        xclu = np.concatenate([
+            near[own[:, None], rng.integers(0, min(nx, ng - 1), size=(n, xn))],
+            (own[:, None] + 1 + rng.integers(0, ng - 1, size=(n, nx - xn))) % ng], axis=1)
+        if nh:
+            hn = min(nh // 2, ng - 1)
+            rows = []
+            for c in range(ng):
+                others = np.setdiff1d(np.arange(ng), np.concatenate([[c], near[c, :hn]]))
+                k = min(nh - hn, len(others))
+                rows.append(np.concatenate([near[c, :hn], rng.choice(others, size=k, replace=False)]))
+            hclu = np.stack(rows)
+        else:
+            hclu = np.zeros((ng, 0), np.int64)
     else:
         xclu = (own[:, None] + 1 + rng.integers(0, ng - 1, size=(n, nx))) % ng
         hclu = np.stack([(g + 1 + rng.choice(ng - 1, size=min(nh, ng - 1), replace=False)) % ng
