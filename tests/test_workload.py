@@ -57,3 +57,29 @@ def test_deterministic_across_thread_counts(tmp_path):
                    PYTHONPATH=os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
         out.append(subprocess.check_output([sys.executable, "-c", code], env=env, text=True))
     assert out[0] == out[1]
+
+
+def test_mixed_cluster_links_of_configuration_4():
+    # configuration 4's links between clusters: per point, half to clusters
+    # among its cluster's nearest (by medoid distance) and half to random
+    # other clusters; per medoid, its nh/2 nearest and nh/2 distinct random
+    # ones; never its own cluster
+    ng, nx, nh = 64, 4, 32
+    w = workload.make_data(4, n=20_000, nq=4, ncomp=ng)
+    gi = workload.graph_inputs(4, w["base"], w["labels"], ng, nx, nh)
+    own = w["labels"].astype(np.int64)
+    xclu, hclu, meds = gi["xclu"].astype(np.int64), gi["hclu"].astype(np.int64), gi["medoids"]
+    assert xclu.shape == (20_000, nx) and hclu.shape == (ng, nh)
+    assert (xclu != own[:, None]).all() and (xclu < ng).all()
+    mv = w["base"][meds.astype(np.int64)].astype(np.int64)
+    dm = ((mv[:, None, :] - mv[None, :, :]) ** 2).sum(-1)        # exact integers
+    np.fill_diagonal(dm, np.iinfo(np.int64).max)
+    near = np.argsort(dm, axis=1, kind="stable")
+    for c in range(ng):
+        assert c not in hclu[c] and len(set(hclu[c].tolist())) == nh
+        assert (hclu[c, :nh // 2] == near[c, :nh // 2]).all()
+    for p in range(0, 20_000, 97):
+        assert set(xclu[p, :nx // 2].tolist()) <= set(near[own[p], :nx].tolist())
+    # deterministic: the same inputs twice
+    gi2 = workload.graph_inputs(4, w["base"], w["labels"], ng, nx, nh)
+    assert (gi2["xclu"] == gi["xclu"]).all() and (gi2["hclu"] == gi["hclu"]).all()
