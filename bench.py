@@ -13,8 +13,9 @@ Forms timed: the plain method (FP32 table), the reduced-precision tables
 (BF16 per warp or on the tensor cores, 8-bit), and the settings bang_autotune
 picks for recall@k >= 0.9 (table precision and source, Bloom filter size,
 L); the fastest form reaching the target is the headline.  The In-memory and
-Exact-distance variants (§5.1, §5.2) are timed beside them.  With `--L` the
-sweep and the autotuner are skipped.
+Exact-distance variants (§5.1, §5.2) are timed beside them, and the autotuned
+settings with only the full vectors in HBM (the graph rows still read from
+host memory).  With `--L` the sweep and the autotuner are skipped.
 
 Timed: `--steps` searches of the device-resident batch, each bracketed by CUDA
 events on the launching stream, an L2 flush (a 512 MB write) between them.
@@ -478,8 +479,11 @@ def main():
                                                    if tune["graph_packed"] else "") +
                                                   (", neighbours' codes side by side in HBM"
                                                    if tune["neighbor_codes"] else "")))
-            if flags & (bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
+            if flags & bang.BANG_GRAPH_IN_HBM:
                 what = "In-memory variant (§5.1), graph and vectors in HBM, with the " + what
+            elif flags & bang.BANG_VECTORS_IN_HBM:
+                what = ("vectors in HBM, graph rows read in place from host memory (between the "
+                        "base method and the In-memory variant, §5.1), with the " + what)
             place(flags)
         search(L, mode, with_stats=True, tsrc=tsrc, lz=lz)
         stream.synchronize()
@@ -522,6 +526,8 @@ def main():
     if tune is not None and "failed" not in tune:
         variants["in_memory_autotuned"] = measure("in_memory_autotuned", max(5, args.steps // 5),
                                                   dict(tune, placement=3))
+        variants["hbm_vectors_autotuned"] = measure("hbm_vectors_autotuned", max(5, args.steps // 5),
+                                                    dict(tune, placement=bang.BANG_VECTORS_IN_HBM))
     place(head["placement"])
     depth[0] = head["depth"]
     L, mode, tsrc, lz = head["L"], head["mode"], head["tsrc"], head["lz"]

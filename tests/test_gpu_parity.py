@@ -210,10 +210,11 @@ def test_empty_batch(u8small):
 # ---------------------------------------------------------------- other forms
 
 def test_in_memory_placement_matches_host_placement(u8small):
-    # §5.1: graph (and vectors) read from HBM instead of host memory
+    # §5.1: graph and/or vectors read from HBM instead of host memory
     Q = u8small["queries"][:100]
     ref = gpu_search(u8small, Q, 10, 64, trace_cap=300)
-    for flags in (bang.BANG_GRAPH_IN_HBM, bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
+    for flags in (bang.BANG_GRAPH_IN_HBM, bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM,
+                  bang.BANG_VECTORS_IN_HBM, bang.BANG_VECTORS_IN_HBM | bang.BANG_GRAPH_PACKED):
         g = gpu_search(u8small, Q, 10, 64, trace_cap=300, placement=flags)
         for f in ("ids", "dist", "iters", "ndist", "trace"):
             assert (g[f] == ref[f]).all()
