@@ -472,13 +472,17 @@ def main():
                                         tune["L"], [])
             flags = (tune.get("placement", 0) | (bang.BANG_GRAPH_PACKED if tune["graph_packed"] else 0)
                      | (bang.BANG_NEIGHBOR_CODES if tune["neighbor_codes"] else 0))
+            if tune.get("node_records") and not tune.get("placement", 0):   # host memory only
+                flags |= bang.BANG_NODE_RECORDS
             what = ("autotuned (bang_autotune): %s table%s, Bloom filter 2^%d bits, smallest L "
                     "reaching recall@%d 0.9%s" % ({0: "FP32", 1: "BF16", 3: "8-bit"}[mode],
                                                   " from the tensor cores" if tsrc else "", lz, K,
                                                   (", graph rows packed to %d-bit ids" % tune["adj_bits"]
                                                    if tune["graph_packed"] else "") +
                                                   (", neighbours' codes side by side in HBM"
-                                                   if tune["neighbor_codes"] else "")))
+                                                   if tune["neighbor_codes"] else "") +
+                                                  (", each node's row and vector side by side"
+                                                   if flags & bang.BANG_NODE_RECORDS else "")))
             if flags & bang.BANG_GRAPH_IN_HBM:
                 what = "In-memory variant (§5.1), graph and vectors in HBM, with the " + what
             elif flags & bang.BANG_VECTORS_IN_HBM:
@@ -512,7 +516,7 @@ def main():
                 tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
                                    target_recall=TARGET_RECALL, bloom_min=14, bloom_max=19,
                                    try_packed_graph=1, try_neighbor_codes=1, try_prefetch_depth=1,
-                                   stream=sptr)
+                                   try_node_records=1, stream=sptr)
                 tune["adj_bits"] = int(np.ceil(np.log2(w["base"].shape[0] + 1)))
             except bang.BangError as e:        # no setting reaches the target within L <= 1024
                 tune = {"failed": str(e)}
@@ -610,7 +614,9 @@ def main():
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
 
-    link = bang.bang_probe_host_link(local, 1 << 30, row_bytes)    # the head's own row size
+    records = bool(head["placement"] & bang.BANG_NODE_RECORDS)   # row and vector in one record
+    gather = (row_bytes + d * esz + 31) // 32 * 32 if records else row_bytes
+    link = bang.bang_probe_host_link(local, 1 << 30, gather)      # the head's own request size
     peaks = measured_peaks()
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
     hbm_gbs = hbm_bytes / launch_s / 1e9
@@ -649,8 +655,8 @@ def main():
                      "peak_source": "measured in this run: random %d-byte row gathers in place "
                                     "from mapped host memory over NVLink-C2C" % link["gather_row_bytes"],
                      "algorithmic_bytes_per_launch": host_bytes,
-                     "per_unit": "%d B per expansion (neighbour row %d B + vector %d B)" % (
-                         row_bytes + d * esz, row_bytes, d * esz),
+                     "per_unit": "%d B per expansion (%sneighbour row %d B + vector %d B)" % (
+                         row_bytes + d * esz, "one record: " if records else "", row_bytes, d * esz),
                      "units_per_launch": int(it.sum())},
         "hbm_roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                          "frac": hbm_gbs / hbm_peak,

@@ -106,7 +106,8 @@ typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,
                BANG_MODE_PQ_Q8 = 3 } bang_mode;
 
 /* Placement flags for bang_set_placement. */
-enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2, BANG_GRAPH_PACKED = 4, BANG_NEIGHBOR_CODES = 8 };
+enum { BANG_GRAPH_IN_HBM = 1, BANG_VECTORS_IN_HBM = 2, BANG_GRAPH_PACKED = 4, BANG_NEIGHBOR_CODES = 8,
+       BANG_NODE_RECORDS = 16 };
 
 /* Create an empty index bound to CUDA device `device`.  *out receives an
  * opaque handle owned by the library; free it with bang_destroy. */
@@ -233,6 +234,13 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
  * R = 64), so that the codes of the next node's neighbours are requested
  * together with its row instead of after it; needs R <= 64, d <= 128 and
  * M <= 32; results are unchanged.
+ * BANG_NODE_RECORDS (not in the paper) makes the search read a page-locked
+ * copy, owned by the index, in which each node's neighbour row (packed when
+ * BANG_GRAPH_PACKED is also set) and its full vector lie side by side, the
+ * record padded to 32 bytes: one expansion then reads one contiguous record
+ * (288 bytes at n = 1M, R = 64, d = 128 u8 with packed rows) instead of a row
+ * and a vector at two places.  Not with BANG_GRAPH_IN_HBM or
+ * BANG_VECTORS_IN_HBM (BANG_EINVAL); results are unchanged.
  * Blocks until the copies are done.  BANG_ENOMEM if the device or the host
  * memory is full. */
 int bang_set_placement(bang_index *ix, uint32_t flags);
@@ -358,6 +366,7 @@ typedef struct bang_autotune_opts {
     uint32_t try_packed_graph;   /* also try BANG_GRAPH_PACKED rows */
     uint32_t try_neighbor_codes; /* also try BANG_NEIGHBOR_CODES (where the index allows it) */
     uint32_t try_prefetch_depth; /* also time the winner with prefetch_depth 2 */
+    uint32_t try_node_records;   /* also time the winner with BANG_NODE_RECORDS (host placement only) */
 } bang_autotune_opts;
 
 typedef struct bang_autotune_result {
@@ -369,6 +378,7 @@ typedef struct bang_autotune_result {
     uint32_t graph_packed;       /* 1: the choice reads packed rows (set the flag) */
     uint32_t neighbor_codes;     /* 1: the choice uses the neighbour-code layout (set the flag) */
     uint32_t prefetch_depth;     /* 1 or 2 (bang_search_params.prefetch_depth) */
+    uint32_t node_records;       /* 1: the choice reads node records (set BANG_NODE_RECORDS) */
 } bang_autotune_result;
 
 int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,

@@ -153,7 +153,7 @@ std::string cache_key(bang_index *ix, uint32_t nq, uint32_t k, uint32_t L, const
       << "|tol=" << o.recall_tolerance << "|modes=" << o.modes << "|bloom=" << o.bloom_min << "-"
       << o.bloom_max << "|tc=" << o.try_tensor_tables << "|batched=" << o.batched
       << "|packed=" << o.try_packed_graph << "|ncodes=" << o.try_neighbor_codes
-      << "|depth=" << o.try_prefetch_depth
+      << "|depth=" << o.try_prefetch_depth << "|records=" << o.try_node_records
       << "|truth=" << (truth ? 1 : 0);
     std::string r = s.str();
     for (char &c : r)
@@ -180,11 +180,11 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     while (std::getline(f, line))
         if (line.compare(0, kpat.size(), kpat) == 0) hit = line;    // the last entry wins
     if (hit.empty()) return false;
-    double v[13];
-    const char *names[13] = {"mode", "bloom_log2", "table_source", "grid_mult", "L", "ms", "recall",
+    double v[14];
+    const char *names[14] = {"mode", "bloom_log2", "table_source", "grid_mult", "L", "ms", "recall",
                              "ref_ms", "ref_recall", "candidates", "graph_packed", "neighbor_codes",
-                             "prefetch_depth"};
-    for (int i = 0; i < 13; ++i)
+                             "prefetch_depth", "node_records"};
+    for (int i = 0; i < 14; ++i)
         if (!field(hit, names[i], &v[i])) return false;
     out->mode = static_cast<uint32_t>(v[0]);
     out->bloom_log2 = static_cast<uint32_t>(v[1]);
@@ -199,6 +199,7 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     out->graph_packed = static_cast<uint32_t>(v[10]);
     out->neighbor_codes = static_cast<uint32_t>(v[11]);
     out->prefetch_depth = static_cast<uint32_t>(v[12]);
+    out->node_records = static_cast<uint32_t>(v[13]);
     out->from_cache = 1;
     return true;
 }
@@ -213,9 +214,10 @@ void store(const char *path, const std::string &key, const bang_autotune_result 
                   "\"mode\": %u, \"bloom_log2\": %u, \"table_source\": %u, \"grid_mult\": %u, "
                   "\"L\": %u, \"ms\": %.6g, \"recall\": %.6g, \"ref_ms\": %.6g, \"ref_recall\": %.6g, "
                   "\"candidates\": %u, \"graph_packed\": %u, \"neighbor_codes\": %u, "
-                  "\"prefetch_depth\": %u}",
+                  "\"prefetch_depth\": %u, \"node_records\": %u}",
                   r.mode, r.bloom_log2, r.table_source, r.grid_mult, r.L, r.ms, r.recall, r.ref_ms,
-                  r.ref_recall, r.candidates, r.graph_packed, r.neighbor_codes, r.prefetch_depth);
+                  r.ref_recall, r.candidates, r.graph_packed, r.neighbor_codes, r.prefetch_depth,
+                  r.node_records);
     f << "{\"key\": \"" << key << "\", " << buf << "\n";
 }
 
@@ -382,11 +384,25 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
     out->ref_recall = ref_acc;
     out->candidates = tried;
     if (!found) return tfail(BANG_EINVAL, "bang_autotune: no candidate reached the target recall");
-    if (o.try_prefetch_depth) {       // the winner with the speculative request too (same results)
-        if (best_c.layout != cur_lay) {
-            if ((rc = bang_set_placement(ix, (place0 & ~kLay) | best_c.layout))) return rc;
-            cur_lay = best_c.layout;
+    out->node_records = 0;
+    if (best_c.layout != cur_lay) {
+        if ((rc = bang_set_placement(ix, (place0 & ~kLay) | best_c.layout))) return rc;
+        cur_lay = best_c.layout;
+    }
+    if (o.try_node_records && !(place0 & (BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM | BANG_NODE_RECORDS))) {
+        // the winner with each node's row and vector side by side (same results)
+        if ((rc = bang_set_placement(ix, (place0 & ~kLay) | best_c.layout | BANG_NODE_RECORDS))) return rc;
+        float msr = 0.f;
+        if ((rc = run.time(best_c, o.reps, &msr))) return rc;
+        ++out->candidates;
+        if (msr < out->ms) {
+            out->ms = msr;
+            out->node_records = 1;
+        } else if ((rc = bang_set_placement(ix, (place0 & ~kLay) | best_c.layout))) {
+            return rc;
         }
+    }
+    if (o.try_prefetch_depth) {       // the winner with the speculative request too (same results)
         Cfg c2 = best_c;
         c2.depth = 2;
         float ms2 = 0.f;

@@ -210,6 +210,12 @@ struct bang_index {
     // adj_row_words words, page-locked and owned by the index.
     HostView adj_packed;
     uint32_t adj_bits = 0, adj_row_words = 0;
+    // Node records (BANG_NODE_RECORDS): each node's row (packed or not) and
+    // full vector side by side, rec_words words per node (a multiple of 8),
+    // page-locked and owned by the index.
+    HostView records;
+    uint32_t rec_words = 0, rec_row_words = 0;
+    bool rec_packed = false;
     bool have_pq = false, have_graph = false, have_vectors = false;
     DevBuf staging;
     // In-memory placement (§5.1): device copies of the graph and/or vectors.
@@ -423,14 +429,79 @@ __global__ void gather_neighbor_codes(const uint32_t *adj, uint64_t n, uint32_t 
 }
 
 // Where and how the kernel reads the graph rows.
+// Builds the node records: row i (packed when `packed`) then vector i, the
+// record rounded up to 32 bytes so that every record starts on a sector.
+int build_records(bang_index *ix, bool packed)
+{
+    if (ix->records.host && ix->rec_packed == packed) return BANG_OK;
+    ix->records.release();
+    if (packed) {
+        const int rc = build_packed_rows(ix);
+        if (rc) return rc;
+    }
+    const uint32_t rw = packed ? ix->adj_row_words : ix->R;
+    const size_t vb = (size_t)ix->d * elem_size(ix->dtype);
+    const uint32_t words = (uint32_t)((((size_t)rw * 4u + vb + 31u) / 32u) * 8u);
+    const size_t bytes = (size_t)ix->n * words * 4u;
+    void *h = nullptr;
+    cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BANG_ENOMEM, "node records: %zu bytes of page-locked memory: %s", bytes,
+                    cudaGetErrorString(e));
+    }
+    const unsigned char *rows = static_cast<const unsigned char *>(packed ? ix->adj_packed.host : ix->adj.host);
+    const unsigned char *vec = static_cast<const unsigned char *>(ix->base.host);
+    const uint64_t n = ix->n;
+    const size_t rb = (size_t)rw * 4u, recb = (size_t)words * 4u;
+    unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    std::vector<std::thread> th;
+    for (unsigned t = 0; t < nt; ++t)
+        th.emplace_back([=]() {
+            for (uint64_t i = n * t / nt; i < n * (t + 1) / nt; ++i) {
+                unsigned char *out = static_cast<unsigned char *>(h) + i * recb;
+                std::memcpy(out, rows + i * rb, rb);
+                std::memcpy(out + rb, vec + i * vb, vb);
+                std::memset(out + rb + vb, 0, recb - rb - vb);
+            }
+        });
+    for (auto &x : th) x.join();
+    void *dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, h, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        cudaFreeHost(h);
+        return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
+    }
+    ix->records.host = h;
+    ix->records.dev = dp;
+    ix->records.copied = true;
+    ix->rec_words = words;
+    ix->rec_row_words = rw;
+    ix->rec_packed = packed;
+    return BANG_OK;
+}
+
+// Where the search reads rows and vectors, and their strides.
 void set_graph_args(const bang_index *ix, bang::SearchArgs &a)
 {
     a.ncodes = (ix->placement & BANG_NEIGHBOR_CODES) ? static_cast<const uint8_t *>(ix->ncodes.p) : nullptr;
     const bool pk = (ix->placement & BANG_GRAPH_PACKED) != 0;
-    if (ix->placement & BANG_GRAPH_IN_HBM) a.adj = static_cast<const uint32_t *>(ix->adj_hbm.p);
-    else a.adj = static_cast<const uint32_t *>(pk ? ix->adj_packed.dev : ix->adj.dev);
     a.adj_bits = pk ? ix->adj_bits : 0u;
     a.adj_row_words = pk ? ix->adj_row_words : ix->R;
+    if (ix->placement & BANG_NODE_RECORDS) {
+        const uint32_t *rec = static_cast<const uint32_t *>(ix->records.dev);
+        a.adj = rec;
+        a.adj_stride = ix->rec_words;
+        a.base = rec + ix->rec_row_words;
+        a.vstride = ix->rec_words * 4u / (uint32_t)elem_size(ix->dtype);
+        return;
+    }
+    if (ix->placement & BANG_GRAPH_IN_HBM) a.adj = static_cast<const uint32_t *>(ix->adj_hbm.p);
+    else a.adj = static_cast<const uint32_t *>(pk ? ix->adj_packed.dev : ix->adj.dev);
+    a.adj_stride = a.adj_row_words;
+    a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
+    a.vstride = ix->d;
 }
 
 }  // namespace
@@ -472,7 +543,8 @@ int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
     ix->codebook = nullptr; ix->off = nullptr; ix->codes = nullptr;
     ix->ncodes.release();
     ix->ncodes_ok = false;
-    ix->placement &= ~(uint32_t)BANG_NEIGHBOR_CODES;
+    ix->records.release();
+    ix->placement &= ~(uint32_t)(BANG_NEIGHBOR_CODES | BANG_NODE_RECORDS);
     ix->adj.release();
     ix->base.release();
     ix->have_pq = ix->have_graph = ix->have_vectors = false;
@@ -525,9 +597,10 @@ int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_
     ix->adj_hbm.release();
     ix->adj_packed.release();
     ix->adj_bits = ix->adj_row_words = 0;
+    ix->records.release();
     ix->ncodes.release();
     ix->ncodes_ok = false;
-    ix->placement &= ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES);
+    ix->placement &= ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES | BANG_NODE_RECORDS);
     ix->have_graph = false;
     int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->adj);
     if (rc) return rc;
@@ -547,7 +620,8 @@ int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype)
     if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
     ix->base.release();
     ix->base_hbm.release();
-    ix->placement &= ~(uint32_t)BANG_VECTORS_IN_HBM;
+    ix->records.release();
+    ix->placement &= ~(uint32_t)(BANG_VECTORS_IN_HBM | BANG_NODE_RECORDS);
     ix->have_vectors = false;
     int rc = map_host(base, (size_t)ix->n * ix->d * elem_size(dtype), ix->base);
     if (rc) return rc;
@@ -686,7 +760,6 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.off = ix->off;
     a.codes = ix->codes;
     set_graph_args(ix, a);
-    a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
     a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
     a.medoid = ix->medoid;
     a.nq = nq; a.k = k; a.L = L; a.log2z = log2z; a.iter_cap = p.iter_cap;
@@ -799,8 +872,14 @@ int bang_index_info(const bang_index *ix, uint64_t *n, uint32_t *d, uint32_t *M,
 int bang_set_placement(bang_index *ix, uint32_t flags)
 {
     if (!ix) return fail(BANG_EINVAL, "bang_set_placement: index is NULL");
-    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES))
+    if (flags & ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES |
+                            BANG_NODE_RECORDS))
         return fail(BANG_EINVAL, "bang_set_placement: unknown flags 0x%x", flags);
+    if ((flags & BANG_NODE_RECORDS) && (flags & (BANG_GRAPH_IN_HBM | BANG_VECTORS_IN_HBM)))
+        return fail(BANG_EINVAL, "bang_set_placement: node records are host memory; not with "
+                    "BANG_GRAPH_IN_HBM or BANG_VECTORS_IN_HBM");
+    if ((flags & BANG_NODE_RECORDS) && !(ix->have_graph && ix->have_vectors))
+        return fail(BANG_ESTATE, "bang_set_placement: register the graph and the vectors first");
     if ((flags & BANG_NEIGHBOR_CODES) && (ix->R > 64 || ix->d > 128 || ix->Mpad > 32))
         return fail(BANG_EINVAL, "bang_set_placement: the neighbour-code layout needs R <= 64, d <= 128 "
                     "and M <= 32");
@@ -843,6 +922,12 @@ int bang_set_placement(bang_index *ix, uint32_t flags)
     } else {
         ix->base_hbm.release();
     }
+    if (flags & BANG_NODE_RECORDS) {
+        const int rc = build_records(ix, (flags & BANG_GRAPH_PACKED) != 0);
+        if (rc) return rc;
+    } else {
+        ix->records.release();
+    }
     ix->placement = flags;
     return BANG_OK;
 }
@@ -857,6 +942,7 @@ int bang_destroy(bang_index *ix)
         if (ix->codes) cudaFree(ix->codes);
         ix->adj.release();
         ix->adj_packed.release();
+        ix->records.release();
         ix->ncodes.release();
         ix->base.release();
         ix->staging.release();
@@ -1017,7 +1103,6 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.off = ix->off;
     a.codes = ix->codes;
     set_graph_args(ix, a);
-    a.base = (ix->placement & BANG_VECTORS_IN_HBM) ? ix->base_hbm.p : ix->base.dev;
     a.n = (uint32_t)ix->n; a.d = ix->d; a.M = ix->M; a.Mpad = ix->Mpad; a.R = ix->R;
     a.medoid = ix->medoid;
     a.nq = nq; a.k = k_max; a.L = L_max; a.log2z = log2z; a.iter_cap = p.iter_cap;

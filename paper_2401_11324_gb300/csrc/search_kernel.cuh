@@ -61,9 +61,11 @@ struct SearchArgs {
     const uint32_t *adj;      // device-accessible (mapped host), n rows of adj_row_words words
     uint32_t adj_bits;        // 0: rows of R ids; else ids packed to adj_bits bits, all ones = none
     uint32_t adj_row_words;   // 32-bit words per row (R when not packed)
+    uint32_t adj_stride;      // 32-bit words from one row to the next (>= the row's words)
     const uint8_t *ncodes;    // device or null: for every node, its R neighbours' code rows, 32 bytes each
     uint32_t spec;            // also request the first unvisited worklist entry after u* at once
-    const void *base;         // device-accessible (mapped host), n*d
+    const void *base;         // device-accessible (mapped host), n vectors of d elements
+    uint32_t vstride;         // elements from one vector to the next (>= d)
     uint32_t n, d, M, Mpad, R, medoid;
     uint32_t nq, k, L, log2z, iter_cap;
     uint32_t vec_ok;          // rows of `queries` allow 4-element vector loads
@@ -393,14 +395,14 @@ __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int l
 {
     using E = typename Elem<DT>::T;
     const uint32_t W = a.adj_bits ? a.adj_row_words : a.R;     // words per row
-    const uint32_t *row = a.adj + static_cast<uint64_t>(u) * W;
+    const uint32_t *row = a.adj + static_cast<uint64_t>(u) * a.adj_stride;
 #pragma unroll
     for (int r = 0; r < RPL; ++r) {
         uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
         nd.nb[r] = i < W ? row[i] : kNone;
     }
     if (WITH_VECTOR) {
-        const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.d;
+        const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.vstride;
         load_share<DT, DCH>(x, a.d, a.vecb_ok != 0, lane, nd.x);
     }
     if constexpr (NC) {
@@ -651,7 +653,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         uint32_t dm_bits = 0;
         if (!kPQ) {
             VecShare<DT, DCH> xs;
-            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(a.medoid) * d, d,
+            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(a.medoid) * a.vstride, d,
                                 a.vecb_ok != 0, lane, xs);
             dm_bits = exact_distance_bits<DT, DCH>(qs, xs);
         }
@@ -794,7 +796,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     const bool act = j < nn;
                     const uint32_t id = act ? Nid[j] : 0u;
                     const uint4 *row = reinterpret_cast<const uint4 *>(static_cast<const E *>(a.base) +
-                                                                       static_cast<uint64_t>(id) * d);
+                                                                       static_cast<uint64_t>(id) * a.vstride);
                     uint4 xv[8];
 #pragma unroll
                     for (int c = 0; c < 8; ++c)
@@ -824,7 +826,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                     for (int t = 0; t < 4; ++t) {
                         ids[t] = j0 + t < nn ? Nid[j0 + t] : 0u;
                         if (j0 + t < nn)
-                            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(ids[t]) * d,
+                            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(ids[t]) * a.vstride,
                                                 d, a.vecb_ok != 0, lane, xs[t]);
                     }
 #pragma unroll

@@ -85,6 +85,23 @@ def test_packed_rows_as_a_candidate(setup):
     assert abs(_recall_with(ix, q, w, r) - r["recall"]) < 1e-6
 
 
+def test_node_records_timed_on_the_winner(setup):
+    w, ix, q = setup
+    truth = np.ascontiguousarray(w["gt_ids"][:, :10])
+    r = ix.autotune(q, 10, 64, truth=truth, modes=(1 << 3), bloom_min=15, bloom_max=15,
+                    try_packed_graph=1, try_node_records=1)
+    # two layouts, then the winner once more with its rows and vectors as records
+    assert r["node_records"] in (0, 1) and r["candidates"] == 3
+    assert abs(_recall_with(ix, q, w, r) - r["recall"]) < 1e-6
+    flags = (bang.BANG_GRAPH_PACKED if r["graph_packed"] else 0) | (
+        bang.BANG_NODE_RECORDS if r["node_records"] else 0)
+    ix.set_placement(flags)
+    try:
+        assert abs(_recall_with(ix, q, w, r) - r["recall"]) < 1e-6
+    finally:
+        ix.set_placement(0)
+
+
 def test_rejects_bad_options(setup):
     w, ix, q = setup
     for kw in (dict(target_recall=1.5), dict(bloom_min=17, bloom_max=14), dict(modes=1 << 7)):

@@ -263,7 +263,8 @@ def test_placement_transitions_and_reregistration(u8small):
     ref = run()
     P, H, V, N = (bang.BANG_GRAPH_PACKED, bang.BANG_GRAPH_IN_HBM, bang.BANG_VECTORS_IN_HBM,
                   bang.BANG_NEIGHBOR_CODES)
-    for flags in (P, P | H, H, N | H | V, N | P, 0, N, P | N | H | V, 0):
+    D = bang.BANG_NODE_RECORDS
+    for flags in (P, P | H, H, N | H | V, N | P, 0, N, P | N | H | V, D | P, D, D | N, P, 0):
         ix.set_placement(flags)
         got = run()
         assert (got[0] == ref[0]).all() and (got[1] == ref[1]).all(), flags
@@ -272,7 +273,7 @@ def test_placement_transitions_and_reregistration(u8small):
     got = run()
     assert (got[0] == ref[0]).all()
     with pytest.raises(bang.BangError):
-        ix.set_placement(16)                                     # unknown flag
+        ix.set_placement(32)                                     # unknown flag
     ix.close()
 
 
@@ -310,6 +311,39 @@ def test_phase_clock_instantiation_gives_identical_results(u8small, mode, flags)
     assert (ph >= 0).all()
     assert (ph[:, -1] > 0).all()
     assert (ph[:, :-1].sum(1) <= ph[:, -1]).all()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_node_records_give_identical_results(u8small, cfg1, mode):
+    # BANG_NODE_RECORDS: each node's row and vector in one host record
+    R, P, N = bang.BANG_NODE_RECORDS, bang.BANG_GRAPH_PACKED, bang.BANG_NEIGHBOR_CODES
+    for w, Q in ((u8small, u8small["queries"][:120]), (cfg1, cfg1["queries"])):
+        ref = gpu_search(w, Q, 10, 64, trace_cap=400, mode=mode)
+        for flags in (R, R | P, R | N, R | P | N):
+            if (flags & N) and mode == 2:
+                continue
+            g = gpu_search(w, Q, 10, 64, trace_cap=400, mode=mode, placement=flags)
+            for f in ("ids", "dist", "iters", "ndist", "trace"):
+                assert (g[f] == ref[f]).all(), (mode, flags, f)
+
+
+def test_node_records_f32_wide_rows_and_limits():
+    # R = 68 f32 rows (272-byte rows before each vector) and d = 200 vectors
+    for kw in (dict(dtype="f32", d=96, M=48, R=68), dict(dtype="f32", d=200, M=50, R=32)):
+        w = cases.clustered(n=6_000, nq=40, ncomp=4, centre="uniform255", **kw)
+        Q = w["queries"]
+        for mode in (0, 2):
+            ref = gpu_search(w, Q, 10, 48, trace_cap=200, mode=mode, M=kw["M"])
+            for flags in (bang.BANG_NODE_RECORDS, bang.BANG_NODE_RECORDS | bang.BANG_GRAPH_PACKED):
+                g = gpu_search(w, Q, 10, 48, trace_cap=200, mode=mode, M=kw["M"], placement=flags)
+                for f in ("ids", "dist", "iters", "ndist", "trace"):
+                    assert (g[f] == ref[f]).all(), (kw, mode, flags, f)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    for bad in (bang.BANG_NODE_RECORDS | bang.BANG_GRAPH_IN_HBM,
+                bang.BANG_NODE_RECORDS | bang.BANG_VECTORS_IN_HBM):
+        with pytest.raises(bang.BangError):
+            ix.set_placement(bad)
+    ix.close()
 
 
 def test_packed_graph_rows_wide_rows():
