@@ -81,6 +81,9 @@ def parse():
                          "against the oracle's brute force on sampled queries")
     ap.add_argument("--packed", action="store_true",
                     help="fixed forms read packed graph rows (BANG_GRAPH_PACKED)")
+    ap.add_argument("--records", action="store_true",
+                    help="fixed host forms read each node's row and vector as one record "
+                         "(BANG_NODE_RECORDS)")
     ap.add_argument("--config", type=int, default=2, choices=(2, 3, 4),
                     help="2: mid-scale u8 (the headline); 3: the precision form (f32 d=96); "
                          "4: the batched form (100M int8, d=100; needs --gpu-build)")
@@ -465,6 +468,9 @@ def main():
             if args.packed and not flags:
                 flags = bang.BANG_GRAPH_PACKED
                 what += "; graph rows packed"
+            if args.records and not flags & (bang.BANG_GRAPH_IN_HBM | bang.BANG_VECTORS_IN_HBM):
+                flags |= bang.BANG_NODE_RECORDS
+                what += "; each node's row and vector as one host record"
             place(flags)
             L, sweep = operating_point(mode, tsrc)
         else:                       # settings chosen by bang_autotune
