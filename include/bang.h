@@ -15,7 +15,9 @@
  *    other value, bang_last_error() returns a message for the calling thread
  *    (valid until that thread's next call into the library).
  *  - Pointers are plain host or device addresses.  Arguments documented as
- *    "host or device" are detected with cudaPointerGetAttributes.
+ *    "host or device" are detected with cudaPointerGetAttributes; device
+ *    memory must belong to the GPU the call works on (the index's, or the
+ *    `device` argument), otherwise the call returns BANG_EINVAL.
  *  - Outputs are allocated by the caller.
  *  - A bang_index is not thread-safe: serialise calls on one index.
  *  - Ids are uint32; 0xFFFFFFFF marks an absent id.  n < 2^31.
@@ -206,7 +208,12 @@ int bang_search_batched(bang_index *ix, const void *queries, uint32_t nq, const 
  *     device array of about 270 KB that every GPU loading the library keeps
  *     until exit; nq above 65536 (its capacity) returns BANG_EINVAL.
  *   - The first call on a device looks up that array's device address; make
- *     it before any stream capture.
+ *     it before any stream capture.  The address is kept for the life of the
+ *     process: it does not survive cudaDeviceReset on that device (the
+ *     reset destroys the context the array lives in), so a process that
+ *     resets a device must not call this entry point on it afterwards.
+ *   - Every pointer must be device memory of the index's GPU (or managed
+ *     memory); device memory of another GPU returns BANG_EINVAL.
  *   - All calls share the array: calls that overlap on the GPU (on different
  *     streams, or different indexes at once) race and must not be issued.
  *     Each call clears the counter it needs and rewrites the order.

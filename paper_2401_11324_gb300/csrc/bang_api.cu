@@ -94,7 +94,7 @@ void parallel_copy(void *dst, const void *src, size_t bytes)
     for (auto &t : th) t.join();
 }
 
-int map_host(const void *p, size_t bytes, HostView &out)
+int map_host(const void *p, size_t bytes, int device, HostView &out)
 {
     cudaPointerAttributes at;
     cudaError_t e = cudaPointerGetAttributes(&at, p);
@@ -104,6 +104,9 @@ int map_host(const void *p, size_t bytes, HostView &out)
     }
     out.host = p;
     out.registered_here = out.copied = false;
+    if (at.type == cudaMemoryTypeDevice && at.device != device)
+        return fail(BANG_EINVAL, "the array is device memory of GPU %d, not of the index's GPU %d",
+                    at.device, device);
     if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) {
         out.dev = p;
         return BANG_OK;
@@ -156,16 +159,26 @@ int map_host(const void *p, size_t bytes, HostView &out)
     return BANG_OK;
 }
 
-bool is_device_accessible(const void *p)
+// Where a caller's pointer lives: host memory (pageable or page-locked),
+// device memory of `device` (or managed memory, reachable from every GPU),
+// or device memory of another GPU, which the index's kernels must not be
+// given: without peer access that is a fault on that GPU.
+enum PtrKind { kPtrHost = 0, kPtrDevice = 1, kPtrOtherDevice = 2 };
+
+PtrKind pointer_kind(const void *p, int device)
 {
-    if (!p) return false;
+    if (!p) return kPtrHost;
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
-        return false;
+        return kPtrHost;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return kPtrDevice;
+    if (at.type == cudaMemoryTypeDevice) return at.device == device ? kPtrDevice : kPtrOtherDevice;
+    return kPtrHost;
 }
+
+bool is_device_accessible(const void *p, int device) { return pointer_kind(p, device) == kPtrDevice; }
 
 size_t elem_size(int dt) { return dt == BANG_F32 ? 4 : 1; }
 
@@ -195,6 +208,7 @@ struct DevBuf {
 
 namespace bang {
 void set_error(const std::string &msg) { g_err = msg; }
+int pointer_kind(const void *p, int device) { return ::pointer_kind(p, device); }
 }  // namespace bang
 
 struct bang_index {
@@ -602,7 +616,7 @@ int bang_register_graph(bang_index *ix, const uint32_t *adj, uint32_t R, uint32_
     ix->ncodes_ok = false;
     ix->placement &= ~(uint32_t)(BANG_GRAPH_IN_HBM | BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES | BANG_NODE_RECORDS);
     ix->have_graph = false;
-    int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->adj);
+    int rc = map_host(adj, (size_t)ix->n * R * sizeof(uint32_t), ix->device, ix->adj);
     if (rc) return rc;
     ix->R = R;
     ix->medoid = medoid;
@@ -623,7 +637,7 @@ int bang_register_vectors(bang_index *ix, const void *base, bang_dtype dtype)
     ix->records.release();
     ix->placement &= ~(uint32_t)(BANG_VECTORS_IN_HBM | BANG_NODE_RECORDS);
     ix->have_vectors = false;
-    int rc = map_host(base, (size_t)ix->n * ix->d * elem_size(dtype), ix->base);
+    int rc = map_host(base, (size_t)ix->n * ix->d * elem_size(dtype), ix->device, ix->base);
     if (rc) return rc;
     ix->dtype = dtype;
     ix->have_vectors = true;
@@ -687,7 +701,11 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     for (int i = 0; i < 10; ++i) {
         Slot &s = slots[i];
         if (!s.user) continue;
-        s.dev = is_device_accessible(s.user);
+        const PtrKind kind = pointer_kind(s.user, ix->device);
+        if (kind == kPtrOtherDevice)
+            return fail(BANG_EINVAL, "bang_search: a buffer is device memory of another GPU than "
+                        "the index's device %d", ix->device);
+        s.dev = kind == kPtrDevice;
         if (!s.dev) {
             s.off = need;
             need += (s.bytes + 255) & ~size_t(255);
@@ -831,8 +849,9 @@ int bang_pq_tables(bang_index *ix, const void *queries, uint32_t nq, void *out, 
     if (!ix->have_pq) return fail(BANG_ESTATE, "bang_pq_tables: load the PQ data first");
     if (ix->dtype < 0) return fail(BANG_ESTATE, "bang_pq_tables: register the vectors first (element type)");
     if (!ix->tc_ok) return fail(BANG_EINVAL, "bang_pq_tables: unavailable for this PQ layout");
-    if (!is_device_accessible(queries) || !is_device_accessible(out))
-        return fail(BANG_EINVAL, "bang_pq_tables: queries and out must be device memory");
+    if (!is_device_accessible(queries, ix->device) || !is_device_accessible(out, ix->device))
+        return fail(BANG_EINVAL, "bang_pq_tables: queries and out must be device memory of the "
+                    "index's device %d", ix->device);
     if (nq == 0) return BANG_OK;
     DeviceGuard g(ix->device);
     if (!g.ok) return fail(BANG_ECUDA, "cannot select device %d", ix->device);
@@ -1061,10 +1080,13 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
                             p.out_ndist, p.trace, p.out_phase_cycles};
     for (int i = 0; i < 10; ++i) {
         if (i < 5 && !ptrs[i]) return fail(BANG_EINVAL, "bang_search_batched_noalloc: NULL buffer");
-        if (ptrs[i] && !is_device_accessible(ptrs[i]))
+        if (ptrs[i] && !is_device_accessible(ptrs[i], ix->device))
             return fail(BANG_EINVAL, "bang_search_batched_noalloc: every buffer must be device memory "
-                        "(host buffers would need staging allocations)");
+                        "of the index's device %d (host buffers would need staging allocations)",
+                        ix->device);
     }
+    if (p.table_source != 0)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0 (tables need scratch)");
     bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: %u bytes of shared memory per query "
@@ -1120,8 +1142,6 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.queue = scratch;
     a.grid_mult = p.grid_mult;
     a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
-    if (p.table_source != 0)
-        return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0 (tables need scratch)");
     const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
     const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
     a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;

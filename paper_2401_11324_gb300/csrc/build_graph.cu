@@ -540,6 +540,8 @@ extern "C" int bang_build_cluster_graph(int device, const void *base, bang_dtype
     const uint32_t row_bytes = d * esz, stride_bytes = (row_bytes + 15u) & ~15u;
     if (stride_bytes > kMaxRow) return gfail(BANG_EINVAL, "bang_build_cluster_graph: rows above 2048 bytes");
     if (!(alpha > 0.f)) return gfail(BANG_EINVAL, "bang_build_cluster_graph: alpha must be positive");
+    if (bang::pointer_kind(base, device) == 2 || bang::pointer_kind(adj, device) == 2)
+        return gfail(BANG_EINVAL, "bang_build_cluster_graph: base or adj is memory of another GPU");
     if (is_dev(members) || is_dev(gstart) || is_dev(medoids) || (nx && is_dev(xclu)) ||
         (nh && is_dev(hclu)))
         return gfail(BANG_EINVAL, "bang_build_cluster_graph: members, gstart, medoids, xclu and hclu "

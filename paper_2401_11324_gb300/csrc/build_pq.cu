@@ -176,6 +176,9 @@ extern "C" int bang_build_pq(int device, const void *base, bang_dtype dtype, uin
     if (n == 0 || d == 0 || M == 0 || M > d || ns == 0 || iters > 1000)
         return pfail(BANG_EINVAL, "bang_build_pq: need n, d, ns > 0, 1 <= M <= d, iters <= 1000");
     if ((d + M - 1) / M > kMaxDsub) return pfail(BANG_EINVAL, "bang_build_pq: subspaces wider than 16 dimensions");
+    if (bang::pointer_kind(base, device) == 2 || bang::pointer_kind(codebook, device) == 2 ||
+        bang::pointer_kind(codes, device) == 2)
+        return pfail(BANG_EINVAL, "bang_build_pq: base, codebook or codes is memory of another GPU");
     if (is_dev(sample) || is_dev(init)) return pfail(BANG_EINVAL, "bang_build_pq: sample and init must be host memory");
     for (uint64_t i = 0; i < ns; ++i)
         if (sample[i] >= n) return pfail(BANG_EINVAL, "bang_build_pq: sample id >= n");

@@ -311,6 +311,9 @@ extern "C" int bang_ground_truth(int device, const void *base, const void *queri
         return gtfail(BANG_EINVAL, "bang_ground_truth: unknown dtype");
     if (n == 0 || n >= (1ull << 32) - 1 || d == 0 || d > 4096 || k == 0 || k > kKPL * kW)
         return gtfail(BANG_EINVAL, "bang_ground_truth: need 0 < n < 2^32 - 1, 0 < d <= 4096, 1 <= k <= 256");
+    if (bang::pointer_kind(base, device) == 2 || bang::pointer_kind(queries, device) == 2 ||
+        bang::pointer_kind(out_ids, device) == 2 || bang::pointer_kind(out_dist, device) == 2)
+        return gtfail(BANG_EINVAL, "bang_ground_truth: a buffer is memory of another GPU");
     if (nq == 0) return BANG_OK;
     const size_t esz = dtype == BANG_F32 ? 4 : 1;
     // query rows in dynamic shared memory; with the thresholds (static) under 48 KB

@@ -8,8 +8,10 @@
 // pending requests as fit into one bang_search_batched launch on that slot's
 // stream (H2D copy, search, D2H copy, event).  Launches on different slots
 // overlap on the GPU, so requests that arrive while others are being searched
-// start as soon as a slot frees, not when the whole GPU is idle.  Completion
-// is found by polling the slots' events; results are scattered to the
+// start as soon as a slot frees, not when the whole GPU is idle.  A host
+// function enqueued behind each launch's result copies wakes the dispatcher
+// when the launch is done (it sleeps otherwise; its events are checked again
+// every 2 ms in case a wake-up is missed); results are scattered to the
 // requests and their latency (submit to results in host memory) recorded.
 #include <cuda_runtime.h>
 
@@ -55,6 +57,7 @@ struct Slot {
     float *d_dist = nullptr;
     std::vector<std::shared_ptr<Request>> batch;
     bool busy = false;
+    bang_server *srv = nullptr;     // for the completion host function
 };
 
 }  // namespace
@@ -97,6 +100,15 @@ void release_slots(bang_server *s)
     s->slots.clear();
 }
 
+// Runs on a CUDA-owned thread once a slot's launch and result copies are
+// done: wake the dispatcher (no CUDA calls are allowed here).
+void CUDART_CB slot_done(void *arg)
+{
+    bang_server *s = static_cast<Slot *>(arg)->srv;
+    { std::lock_guard<std::mutex> lk(s->mu); }
+    s->cv_work.notify_one();
+}
+
 // Launch the packed batch of a slot (called by the dispatcher, lock not held).
 int launch_slot(bang_server *s, Slot &sl)
 {
@@ -122,6 +134,7 @@ int launch_slot(bang_server *s, Slot &sl)
     cudaMemcpyAsync(sl.h_ids, sl.d_ids, rb, cudaMemcpyDeviceToHost, sl.stream);
     cudaMemcpyAsync(sl.h_dist, sl.d_dist, rb, cudaMemcpyDeviceToHost, sl.stream);
     cudaEventRecord(sl.done, sl.stream);
+    cudaLaunchHostFunc(sl.stream, slot_done, &sl);
     return cudaGetLastError() == cudaSuccess ? BANG_OK : BANG_ECUDA;
 }
 
@@ -177,10 +190,7 @@ void dispatch_loop(bang_server *s)
         bool any_busy = false;
         for (Slot &sl : s->slots) any_busy |= sl.busy;
         if (s->stopping && !any_busy && s->pending.empty()) break;
-        if (!progressed) {
-            if (any_busy) s->cv_work.wait_for(lk, std::chrono::microseconds(20));
-            else s->cv_work.wait_for(lk, std::chrono::milliseconds(5));
-        }
+        if (!progressed) s->cv_work.wait_for(lk, std::chrono::milliseconds(any_busy ? 2 : 5));
     }
 }
 
@@ -211,6 +221,7 @@ int bang_server_start(bang_index *ix, const bang_server_config *cfg, bang_server
     s->slots.resize(cfg->streams);
     const size_t nb = cfg->max_batch, km = cfg->k_max;
     for (Slot &sl : s->slots) {
+        sl.srv = s.get();
         bool ok = cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess &&
                   cudaEventCreateWithFlags(&sl.done, cudaEventDisableTiming) == cudaSuccess &&
                   cudaHostAlloc((void **)&sl.h_q, nb * d * s->esz, 0) == cudaSuccess &&

@@ -74,3 +74,34 @@ def test_server_rejects_oversized_requests(index):
     ids, _, _ = srv.wait(t)
     assert (ids != bang.BANG_NONE).any()
     srv.stop()
+
+
+def test_requests_wait_for_a_busy_slot(index):
+    """One slot and more work than it holds: requests submitted at once queue
+    behind the running launch (a zero-timeout wait on the last one reports
+    BANG_ETIMEOUT and keeps its ticket), then every request completes with
+    the result it has alone."""
+    w, ix = index
+    kmax, Lmax = 10, 128
+    srv = bang.Server(ix, kmax, Lmax, max_batch=64, streams=1)
+    rng = np.random.default_rng(21)
+    reqs = []
+    for _ in range(24):
+        sel = rng.choice(w["queries"].shape[0], 64, replace=False)
+        k = np.full(64, 10, np.uint32)
+        L = np.full(64, 128, np.uint32)
+        reqs.append((w["queries"][sel], k, L))
+    tickets = [srv.submit(*r) for r in reqs]
+    with pytest.raises(bang.BangError) as e:
+        srv.wait(tickets[-1], timeout_ms=0)
+    assert e.value.code == bang.BANG_ETIMEOUT
+    lat = []
+    for i, (Q, k, L) in enumerate(reqs):
+        ids, dist, ms = srv.wait(tickets[i], timeout_ms=60_000)
+        ids_a, dist_a = _alone(ix, Q, k, L, kmax, Lmax)
+        assert (ids == ids_a).all(), i
+        assert (dist == dist_a).all(), i
+        lat.append(ms)
+    # queued behind the single slot: later requests waited longer
+    assert lat[-1] > lat[0]
+    srv.stop()

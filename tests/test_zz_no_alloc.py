@@ -61,6 +61,103 @@ def test_noalloc_matches_allocating_batched_search_twice():
     ix.close()
 
 
+def _run(fn, ix, q, kd, Ld, n, kmax, Lmax, s):
+    ids = torch.full((n, kmax), -7, dtype=torch.int32, device="cuda")
+    dist = torch.full((n, kmax), -7.0, dtype=torch.float32, device="cuda")
+    iters = torch.zeros(n, dtype=torch.int32, device="cuda")
+    status = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    p = bang.make_params(out_iters=iters, out_status=status)
+    fn(ix.h, q, n, kd, Ld, kmax, Lmax, p, ids, dist, stream=s.cuda_stream)
+    s.synchronize()
+    return [t.cpu().numpy() for t in (ids, dist, iters, status)]
+
+
+def test_noalloc_large_batch_with_out_of_range_rows():
+    """A batch of 3,000 queries (more than the order kernel's 1,024 threads,
+    so its strided loops run) in which some rows have L = 0, L > L_max or
+    k > k_max: those rows are padded with status -1, and every other row
+    equals bang_search_batched's."""
+    w = cases.clustered(n=20_000, nq=300, ncomp=8)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    s = torch.cuda.Stream()
+    n, kmax, Lmax = 3000, 16, 64
+    rng = np.random.default_rng(11)
+    Q = np.ascontiguousarray(w["queries"][rng.integers(0, w["queries"].shape[0], n)])
+    k = rng.choice([1, 5, 10, 16], size=n).astype(np.uint32)
+    L = np.maximum(rng.choice([16, 32, 48, 64], size=n), k).astype(np.uint32)
+    bad = rng.choice(n, 60, replace=False)
+    L[bad[:20]] = 0                  # out of range: bucket 0 of the order
+    L[bad[20:40]] = Lmax + 1 + rng.integers(0, 500, 20)
+    k[bad[40:]] = kmax + 1
+    q, kd, Ld = _dev(Q), _dev(k, np.int32), _dev(L, np.int32)
+    r = _run(bang.bang_search_batched, ix, q, kd, Ld, n, kmax, Lmax, s)
+    z = _run(bang.bang_search_batched_noalloc, ix, q, kd, Ld, n, kmax, Lmax, s)
+    assert (z[3][bad] == -1).all() and (z[0][bad] == -1).all() and np.isinf(z[1][bad]).all()
+    assert (z[2][bad] == 0).all()
+    good = np.setdiff1d(np.arange(n), bad)
+    assert (z[3][good] == 0).all()
+    for a, b in zip(z, r):
+        assert (a == b).all()
+    ix.close()
+
+
+def test_noalloc_at_its_capacity():
+    """nq = 65,536, the static scratch's capacity: every result equals the
+    allocating entry point's."""
+    w = cases.clustered(n=20_000, nq=300, ncomp=8)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    s = torch.cuda.Stream()
+    n = 65536
+    rng = np.random.default_rng(12)
+    Q = np.ascontiguousarray(w["queries"][rng.integers(0, w["queries"].shape[0], n)])
+    k = np.full(n, 10, np.uint32)
+    L = rng.choice([16, 32], size=n).astype(np.uint32)
+    q, kd, Ld = _dev(Q), _dev(k, np.int32), _dev(L, np.int32)
+    r = _run(bang.bang_search_batched, ix, q, kd, Ld, n, 10, 32, s)
+    z = _run(bang.bang_search_batched_noalloc, ix, q, kd, Ld, n, 10, 32, s)
+    for a, b in zip(z, r):
+        assert (a == b).all()
+    assert (z[3] == 0).all()
+    ix.close()
+
+
+def test_noalloc_replayed_from_a_cuda_graph():
+    """After one ordinary call (which looks up the scratch address), the
+    entry point is recorded under stream capture and the graph replayed
+    twice; each replay gives the allocating entry point's results."""
+    w = cases.clustered(n=20_000, nq=300, ncomp=8)
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
+    Q, k, L = _batch(w, 250, 5)
+    n, kmax, Lmax = 250, int(k.max()), int(L.max())
+    q, kd, Ld = _dev(Q), _dev(k, np.int32), _dev(L, np.int32)
+    s = torch.cuda.Stream()
+    r = _run(bang.bang_search_batched, ix, q, kd, Ld, n, kmax, Lmax, s)
+    ids = torch.full((n, kmax), -7, dtype=torch.int32, device="cuda")
+    dist = torch.full((n, kmax), -7.0, dtype=torch.float32, device="cuda")
+    iters = torch.zeros(n, dtype=torch.int32, device="cuda")
+    status = torch.full((n,), 9, dtype=torch.int32, device="cuda")
+    p = bang.make_params(out_iters=iters, out_status=status)
+    bang.bang_search_batched_noalloc(ix.h, q, n, kd, Ld, kmax, Lmax, p, ids, dist,
+                                     stream=s.cuda_stream)
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        bang.bang_search_batched_noalloc(ix.h, q, n, kd, Ld, kmax, Lmax, p, ids, dist,
+                                         stream=s.cuda_stream)
+    for _ in range(2):
+        ids.fill_(-7)
+        dist.fill_(-7.0)
+        iters.zero_()
+        status.fill_(9)
+        g.replay()
+        torch.cuda.synchronize()
+        z = [t.cpu().numpy() for t in (ids, dist, iters, status)]
+        for a, b in zip(z, r):
+            assert (a == b).all()
+    del g
+    ix.close()
+
+
 def test_noalloc_rejects_what_it_cannot_serve():
     w = cases.clustered(n=20_000, nq=300, ncomp=8)
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["M"])
