@@ -22,9 +22,11 @@
  *   orc_pq_encode            §4 (a point is the list of its per-subspace cluster ids)
  *   orc_medoid               §6.3 (the search starts from the medoid)
  *   orc_robust_prune         §2.2 (Vamana RobustPrune with the pruning parameter)
- *   orc_vamana_build         §2.2, §6.3 (R, L, pruning parameter); parity unpinned
- *                            beyond invariants: the paper takes the graph from
- *                            DiskANN and does not state its construction
+ *   orc_vamana_build         §2.2, §6.3 (R, L, pruning parameter): two passes
+ *                            (parameter 1, then alpha) of GreedySearch +
+ *                            RobustPrune + reverse edges; pinned by hand-worked
+ *                            builds (a chain, a reverse-edge overflow, an edge
+ *                            the second pass restores) and invariants
  *   orc_cluster_graph        the clustered construction of the large synthetic
  *                            indexes (per-cluster candidates, RobustPrune of §2.2,
  *                            reverse edges, medoid links); not from the paper

@@ -44,6 +44,16 @@ MUTANTS = [
     ("bf16_truncates", "u += 0x7FFFu + keep_lsb;", "u += 0u * keep_lsb;", 0),
     ("bf16_ties_up", "u += 0x7FFFu + keep_lsb;", "u += 0x8000u + 0u * keep_lsb;", 0),
     ("bf16_mode_uses_f32", "if (mode == 3) orc_adc_table_bf16(T, M, T);", "", 0),
+    ("vamana_one_pass", "for (pass = 0; pass < 2; pass++)", "for (pass = 0; pass < 1; pass++)", 0),
+    ("vamana_alpha_in_pass1", "float a = pass == 0 ? 1.0f : alpha;", "float a = alpha;", 0),
+    ("vamana_no_reverse_edges", "if (has) continue;\n                if (deg < R)",
+     "if (has || 1) continue;\n                if (deg < R)", 0),
+    ("vamana_overflow_skips",
+     "nk = orc_robust_prune(X, d, j, c2, k2, a, R, kept);\n                    for (r = 0; r < R; r++) lj[r] = r < nk ? kept[r] : ORC_NONE;",
+     "nk = 0 * k2 + 0 * kept[0];", 0),
+    ("vamana_overflow_replaces_last",
+     "nk = orc_robust_prune(X, d, j, c2, k2, a, R, kept);\n                    for (r = 0; r < R; r++) lj[r] = r < nk ? kept[r] : ORC_NONE;",
+     "nk = 0 * k2 + 0 * kept[0];\n                    lj[R - 1] = p;", 0),
     ("exact_mode_keeps_rerank", "if (mode == 1) {                    /* Alg. 1",
      "if (mode == 7) {                    /* Alg. 1", 0),
 ]

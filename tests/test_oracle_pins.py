@@ -788,3 +788,57 @@ def test_vamana_invariants():
                     nxt.append(int(v))
         frontier = nxt
     assert len(seen) / n >= 0.99
+
+
+# ---------------------------------------------------------------- Vamana build, hand-worked
+#
+# Each expected graph below was derived by hand from the two-pass build
+# (pass 1 with pruning parameter 1, pass 2 with alpha; per point: GreedySearch
+# from the medoid, RobustPrune of visited U current list, then each new
+# neighbour j gets the point appended, or, when j's list is full, j's list
+# plus the point is pruned again to R).  Squared distances; ties by id.
+
+def _vamana_empty(X, R, Lb, alpha, med, order):
+    n = X.shape[0]
+    init = np.full((n, R), NONE, np.uint32)
+    return oracle.vamana_build(np.asarray(X, np.float32), R, Lb, alpha, med, init,
+                               np.asarray(order, np.uint32))
+
+
+def test_vamana_collinear_alpha1_gives_the_chain():
+    # x = 0..4, R = 2, alpha = 1, medoid 2, empty start, order 0..4.
+    # Pass 1 ends with rows 0:[2,1] 1:[0,2] 2:[1,3] 3:[2,4] 4:[3]; pass 2
+    # prunes every point's candidates (all five points are visited) to its
+    # nearest neighbour on each side, nearer first (ties: smaller id).
+    X = np.arange(5, dtype=np.float32).reshape(5, 1)
+    adj = _vamana_empty(X, 2, 8, 1.0, 2, range(5))
+    want = [[1, NONE], [0, 2], [1, 3], [2, 4], [3, NONE]]
+    assert adj.tolist() == want
+
+
+def test_vamana_reverse_edge_overflow_is_pruned():
+    # x = 0, 2, 3, 7 (ids 0..3), R = 1, alpha = 1, medoid 1, order 0..3.
+    # Pass 1: 0 -> 1 and 1 gets 0; 1 -> 0; 2 -> 1, and 1's full list {0}
+    # plus 2 is pruned to its nearer member 2 (d 1 < 4); 3 -> 2 (visited 1,
+    # 2), and 2's full list {1} plus 3 is pruned to 1 (d 1 < 16).  Pass 2
+    # repeats the same choices: 1's list {2} plus 0 keeps 2, 2's list {1}
+    # plus 3 keeps 1.
+    X = np.array([[0], [2], [3], [7]], np.float32)
+    adj = _vamana_empty(X, 1, 8, 1.0, 1, range(4))
+    assert adj.tolist() == [[1], [2], [1], [2]]
+
+
+def test_vamana_second_pass_keeps_what_the_first_pruned():
+    # Points 0:(8,10) 1:(6,10) 2:(8,9) 3:(5,0); squared distances d01 = 4,
+    # d02 = 1, d03 = 109, d12 = 5, d13 = 101, d23 = 90.  R = 2, alpha = 1.2,
+    # medoid 0, order 1, 2, 3, 0.
+    # Pass 1 (parameter 1): 1 -> [0]; 2 -> [0] (1 pruned: d01 = 4 <= d21 = 5);
+    # 3 -> [2]; 0 -> [2, 1]; reverse edges make 0:[1,2] then [2,1], 2:[0,3].
+    # Pass 2 (alpha^2 = 1.44): 1 -> [0, 3] (1.44 * 109 > 101 keeps 3) and 3
+    # gets 1; 2 -> [0, 1] (1.44 * 4 = 5.76 > 5 now keeps 1, the edge pass 1
+    # pruned), and 1's full list [0, 3] plus 2 is pruned back to [0, 3];
+    # 3 -> [2], and 2's full list [0, 1] plus 3 is pruned to [0, 1]
+    # (1.44 * 109 > 90 would keep 3, but R = 2 is reached first); 0 -> [2, 1].
+    X = np.array([[8, 10], [6, 10], [8, 9], [5, 0]], np.float32)
+    adj = _vamana_empty(X, 2, 8, 1.2, 0, [1, 2, 3, 0])
+    assert adj.tolist() == [[2, 1], [0, 3], [0, 1], [2, NONE]]
