@@ -308,6 +308,51 @@ int bang_build_cluster_graph(int device, const void *base, bang_dtype dtype, uin
                              const uint32_t *xclu, uint32_t nh, const uint32_t *hclu,
                              uint32_t *adj, void *stream);
 
+/* Overlapping-shard graph (§2.2: the paper's Vamana index is built by
+ * splitting the dataset into smaller overlapping clusters, building a
+ * directed subgraph on each with GreedySearch and RobustPrune, and merging
+ * the subgraphs' edges), in a batched form whose result does not depend on
+ * thread scheduling:
+ *   1. point i joins the shards of its ell nearest centres (FP32 squared
+ *      distance over ascending dimensions, each difference, product and sum
+ *      rounded; ties to the smaller centre index);
+ *   2. shard g lists its members in ascending id; its entry is the member
+ *      nearest its centre (same distance; ties to the smaller id); it
+ *      inserts the entry first, then the other members in ascending id
+ *      (callers whose ids follow the data's structure shuffle the rows);
+ *   3. two passes, pruning parameter 1 then alpha; a pass cuts every shard's
+ *      insertion order into batches (pass 1: 1, 1, 2, 4, ... up to
+ *      cap = max(1, floor(batch_frac * m)), pass 2: cap each) and batch r of
+ *      every shard forms round r.  In a round, against the graph as it stood
+ *      at the round's start, every member runs GreedySearch from its shard's
+ *      entry (Alg. 1 with exact distances as in BANG_MODE_EXACT, worklist Lb,
+ *      a 2^log2z-bit Bloom seen set, at most iter_cap expansions); its list
+ *      becomes RobustPrune(member, expanded nodes U its current list); then
+ *      every node named by a new list takes the members that named it: the
+ *      union sorted by distance when it fits in R, else RobustPrune'd;
+ *   4. point i's row is the union of its shard lists, sorted when it fits
+ *      in R, else RobustPrune'd with alpha.
+ * Distances are the exact squared L2 of the search's Exact-distance mode
+ * rounded to FP32; lists are sorted by (distance, id) without repeats or the
+ * owner.  RobustPrune keeps, in that order, each live candidate (at most R)
+ * and removes every later candidate c with a^2 * d(kept, c) <= d(owner, c),
+ * a^2 and the product in FP32.  Rows are written sorted, 0xFFFFFFFF padding.
+ *   base      n*d elements of dtype, host or device; n*ell < 2^31 - 1.
+ *   centres   host, S*d floats; ell in 1..min(4, S).
+ *   R         multiple of 4 in 4..128, ell*R <= 512.  Lb 1..1024; log2z
+ *             10..20; iter_cap 0 selects 2*Lb + 64, and iter_cap + R <= 512;
+ *             alpha >= 1; 0 < batch_frac <= 1.
+ *   adj       n*R output, host or device.  shard_of: host, n*ell, may be NULL
+ *             (each point's shards, nearest centre first).
+ * Device memory: about n*ell*(R*4 + d*elem rounded to 16, then to 32 bytes
+ * per record) plus per-round scratch (about 40*R bytes per member of the
+ * largest round).  Blocks until done.  BANG_EINVAL also when a node gains
+ * more than 16,384 reverse candidates in one round (lower batch_frac). */
+int bang_build_shard_graph(int device, const void *base, bang_dtype dtype, uint64_t n, uint32_t d,
+                           const float *centres, uint32_t S, uint32_t ell, uint32_t R, uint32_t Lb,
+                           float alpha, float batch_frac, uint32_t log2z, uint32_t iter_cap,
+                           uint32_t *adj, uint32_t *shard_of, void *stream);
+
 /* PQ codebook and codes on the GPU (§4): M contiguous subspaces, the first
  * d mod M one dimension wider (§6.3); 256 centroids per subspace by k-means:
  * centroids start at the points init[s*256 + c]; each of `iters` Lloyd

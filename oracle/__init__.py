@@ -80,6 +80,9 @@ def lib():
         L.orc_cluster_graph.argtypes = [vp, i32, u32, u64, vp, vp, u32, vp, u32, f32, u32, vp,
                                         u32, vp, vp]
         L.orc_cluster_graph.restype = i32
+        L.orc_shard_graph.argtypes = [vp, i32, u64, u32, vp, u32, u32, u32, u32, f32, f32, u32,
+                                      u32, vp, vp, i32]
+        L.orc_shard_graph.restype = i32
         L.orc_adc_table_f32.argtypes = [vp, u32, vp, vp, vp]
         L.orc_adc_dist_f32.argtypes = [vp, u32, vp]
         L.orc_adc_dist_f32.restype = f32
@@ -174,6 +177,23 @@ def vamana_build(X, R, Lb, alpha, medoid_id, init_adj, order):
                                 _p(adj))
     assert rc == 0
     return adj
+
+
+def shard_graph(X, centres, ell, R, Lb, alpha, batch_frac=0.02, log2z=16, iter_cap=0,
+                nthreads=0):
+    """Overlapping-shard graph (orc_shard_graph, §2.2): n x R adjacency and
+    the n x ell shard assignment (nearest centre first)."""
+    X = np.ascontiguousarray(X)
+    n, d = X.shape
+    centres = _c(centres, np.float32).reshape(-1, d)
+    S = centres.shape[0]
+    adj = np.zeros((n, R), np.uint32)
+    sh = np.zeros((n, ell), np.uint32)
+    rc = lib().orc_shard_graph(_p(X), _DT[X.dtype], n, d, _p(centres), S, ell, R, Lb,
+                               ctypes.c_float(alpha), ctypes.c_float(batch_frac), log2z,
+                               iter_cap or (2 * Lb + 64), _p(adj), _p(sh), nthreads)
+    assert rc == 0, rc
+    return adj, sh
 
 
 def cluster_graph(X, members, gstart, medoids, R, alpha, nx=0, xclu=None, nh=0, hclu=None):

@@ -929,6 +929,316 @@ int orc_max_threads(void)
 }
 
 /* ---------------------------------------------------------------------- */
+/* Overlapping-shard graph (§2.2): the paper's Vamana index is built by     */
+/* splitting the dataset into smaller overlapping clusters, building a      */
+/* directed subgraph on each with GreedySearch and RobustPrune, and merging */
+/* the subgraphs' edges.  Restated in a batched form a GPU can also run:    */
+/*  1. assignment: point i joins the shards of its ell nearest centres      */
+/*     (FP32 squared distance over ascending dimensions, each difference,   */
+/*     product and sum rounded; ties to the smaller centre index);          */
+/*  2. shard g lists its members in ascending point id; its entry e_g is    */
+/*     the member nearest its centre (same distance, ties to the smaller    */
+/*     id); it inserts e_g first, then the other members in ascending id;   */
+/*  3. two passes, pruning parameter 1 then alpha.  A pass cuts each        */
+/*     shard's insertion order into batches (pass 1: 1, 1, 2, 4, ... up to  */
+/*     cap_g = max(1, floor(batch_frac * m_g)); pass 2: cap_g each); batch  */
+/*     r of every shard forms round r.  In a round, against the graph as it */
+/*     stood at the round's start, each member p runs GreedySearch from e_g */
+/*     (Alg. 1 with exact distances, worklist Lb, a Bloom seen set of       */
+/*     2^log2z bits, at most iter_cap expansions): V_p = its expanded       */
+/*     nodes.  Then p's list becomes RobustPrune(p, V_p U N(p)).  Then each */
+/*     q named by a new list takes the members that named it: N(q) U In(q) */
+/*     sorted when it fits in R, else RobustPrune(q, N(q) U In(q));         */
+/*  4. merge: point i's row is the union of its shard lists (as point ids), */
+/*     sorted when it fits in R, else RobustPrune(i, union) with alpha.     */
+/* Distances are orc_exact_dist rounded to FP32; candidate lists are sorted */
+/* by (distance, id) with repeats and the point itself removed; every row   */
+/* is kept in that order.  RobustPrune: in that order, a live candidate is  */
+/* kept (at most R) and removes each later candidate c with                 */
+/* a^2 * d(kept, c) <= d(p, c), a^2 and the product rounded to FP32.        */
+/* ---------------------------------------------------------------------- */
+
+typedef struct { float dist; uint32_t id; } sg_cand;
+
+static int sg_cmp(const void *pa, const void *pb)
+{
+    const sg_cand *a = (const sg_cand *)pa, *b = (const sg_cand *)pb;
+    if (a->dist < b->dist) return -1;
+    if (a->dist > b->dist) return 1;
+    return (a->id < b->id) ? -1 : (a->id > b->id);
+}
+
+static float sg_dist(const void *V, int dtype, uint32_t d, uint64_t a, uint64_t b)
+{
+    size_t esz = dtype == ORC_F32 ? 4 : 1;
+    return (float)orc_exact_dist((const unsigned char *)V + a * d * esz,
+                                 (const unsigned char *)V + b * d * esz, dtype, d);
+}
+
+/* FP32 squared distance of point i to centre c (step 1). */
+static float sg_centre_dist(const void *X, int dtype, uint32_t d, uint64_t i, const float *c)
+{
+    float acc = 0.0f;
+    uint32_t j;
+    for (j = 0; j < d; j++) {
+        float t = elem_f(X, dtype, i * d + j) - c[j];
+        float sq = t * t;
+        acc = acc + sq;
+    }
+    return acc;
+}
+
+/* The list of p from nc candidate ids (any order, repeats allowed): drop p
+ * and NONE, sort by (distance to p, id), drop repeats, then keep all (at
+ * most R) or RobustPrune.  V holds the vectors the ids index.  Returns the
+ * row length; out has R slots, padded with NONE. */
+static uint32_t sg_list(const void *V, int dtype, uint32_t d, uint32_t p, const uint32_t *ids,
+                        uint32_t nc, float alpha, uint32_t R, int always_prune, uint32_t *out)
+{
+    sg_cand *c = (sg_cand *)malloc(sizeof(sg_cand) * (nc ? nc : 1));
+    unsigned char *dead = (unsigned char *)calloc(nc ? nc : 1, 1);
+    uint32_t m = 0, u = 0, i, j, nout = 0;
+    float a2 = alpha * alpha;
+    for (i = 0; i < nc; i++) {
+        if (ids[i] == p || ids[i] == ORC_NONE) continue;
+        c[m].id = ids[i];
+        c[m].dist = sg_dist(V, dtype, d, p, ids[i]);
+        m++;
+    }
+    qsort(c, m, sizeof(sg_cand), sg_cmp);
+    for (i = 0; i < m; i++)
+        if (u == 0 || c[i].id != c[u - 1].id) c[u++] = c[i];
+    if (u <= R && !always_prune) {
+        for (i = 0; i < u; i++) out[nout++] = c[i].id;
+    } else {
+        for (i = 0; i < u && nout < R; i++) {
+            if (dead[i]) continue;
+            out[nout++] = c[i].id;
+            for (j = i + 1; j < u; j++) {
+                float lhs;
+                if (dead[j]) continue;
+                lhs = a2 * sg_dist(V, dtype, d, c[i].id, c[j].id);
+                if (lhs <= c[j].dist) dead[j] = 1;
+            }
+        }
+    }
+    for (i = nout; i < R; i++) out[i] = ORC_NONE;
+    free(c); free(dead);
+    return nout;
+}
+
+typedef struct { uint32_t q, p; } sg_pair;
+
+static int sg_pair_cmp(const void *pa, const void *pb)
+{
+    const sg_pair *a = (const sg_pair *)pa, *b = (const sg_pair *)pb;
+    if (a->q != b->q) return a->q < b->q ? -1 : 1;
+    return (a->p < b->p) ? -1 : (a->p > b->p);
+}
+
+int orc_shard_graph(const void *X, int dtype, uint64_t n, uint32_t d, const float *centres,
+                    uint32_t S, uint32_t ell, uint32_t R, uint32_t Lb, float alpha,
+                    float batch_frac, uint32_t log2z, uint32_t iter_cap, uint32_t *adj,
+                    uint32_t *shard_of, int nthreads)
+{
+    size_t esz = dtype == ORC_F32 ? 4 : 1;
+    uint64_t nv = n * ell, i, v;
+    uint32_t g, t, pass;
+    uint32_t *sh, *cnt, *vpt, *vadj, *entry, *epos, *cap, *vid;
+    uint64_t *gstart, *cur;
+    unsigned char *vbase;
+    int rc = 0;
+    if (n == 0 || d == 0 || S == 0 || ell == 0 || ell > S || R == 0 || Lb == 0 || iter_cap == 0 ||
+        log2z < 5 || log2z > 24 || nv >= ORC_NONE || !(batch_frac > 0.0f))
+        return -1;
+#ifdef _OPENMP
+    if (nthreads <= 0) nthreads = omp_get_max_threads();
+#else
+    (void)nthreads;
+#endif
+    sh = (uint32_t *)malloc(sizeof(uint32_t) * nv);
+    vid = (uint32_t *)malloc(sizeof(uint32_t) * nv);
+    cnt = (uint32_t *)calloc(S, sizeof(uint32_t));
+    gstart = (uint64_t *)calloc(S + 1, sizeof(uint64_t));
+    cur = (uint64_t *)calloc(S, sizeof(uint64_t));
+    vpt = (uint32_t *)malloc(sizeof(uint32_t) * nv);
+    vadj = (uint32_t *)malloc(sizeof(uint32_t) * nv * R);
+    entry = (uint32_t *)malloc(sizeof(uint32_t) * S);
+    epos = (uint32_t *)malloc(sizeof(uint32_t) * S);
+    cap = (uint32_t *)malloc(sizeof(uint32_t) * S);
+    vbase = (unsigned char *)malloc(nv * d * esz);
+    if (!sh || !vid || !cnt || !gstart || !cur || !vpt || !vadj || !entry || !epos || !cap || !vbase) {
+        rc = -2;
+        goto done;
+    }
+    /* 1. assignment */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(nthreads)
+#endif
+    for (int64_t ii = 0; ii < (int64_t)n; ii++) {
+        sg_cand *best = (sg_cand *)malloc(sizeof(sg_cand) * S);
+        uint32_t gg;
+        for (gg = 0; gg < S; gg++) {
+            best[gg].dist = sg_centre_dist(X, dtype, d, (uint64_t)ii, centres + (uint64_t)gg * d);
+            best[gg].id = gg;
+        }
+        qsort(best, S, sizeof(sg_cand), sg_cmp);
+        for (gg = 0; gg < ell; gg++) sh[(uint64_t)ii * ell + gg] = best[gg].id;
+        free(best);
+    }
+    /* 2. members in ascending point id, entries, virtual vectors */
+    for (i = 0; i < nv; i++) cnt[sh[i]]++;
+    for (g = 0; g < S; g++) gstart[g + 1] = gstart[g] + cnt[g];
+    for (g = 0; g < S; g++) cur[g] = gstart[g];
+    for (i = 0; i < n; i++)
+        for (t = 0; t < ell; t++) {
+            g = sh[i * ell + t];
+            vid[i * ell + t] = (uint32_t)cur[g];
+            vpt[cur[g]++] = (uint32_t)i;
+        }
+    for (g = 0; g < S; g++) {
+        float bd = INFINITY;
+        entry[g] = ORC_NONE;
+        epos[g] = 0;
+        for (v = gstart[g]; v < gstart[g + 1]; v++) {
+            float dd = sg_centre_dist(X, dtype, d, vpt[v], centres + (uint64_t)g * d);
+            if (entry[g] == ORC_NONE || dd < bd) { bd = dd; entry[g] = (uint32_t)v; }
+        }
+        if (entry[g] != ORC_NONE) epos[g] = (uint32_t)(entry[g] - gstart[g]);
+        cap[g] = (uint32_t)(batch_frac * (float)cnt[g]);
+        if (cap[g] < 1) cap[g] = 1;
+    }
+    for (v = 0; v < nv; v++)
+        memcpy(vbase + v * d * esz, (const unsigned char *)X + (uint64_t)vpt[v] * d * esz, d * esz);
+    for (i = 0; i < nv * R; i++) vadj[i] = ORC_NONE;
+
+    /* 3. two passes of batched insertion */
+    for (pass = 0; pass < 2; pass++) {
+        float a = pass == 0 ? 1.0f : alpha;
+        uint32_t *start = (uint32_t *)calloc(S, sizeof(uint32_t));   /* next position per shard */
+        uint32_t round;
+        for (round = 0;; round++) {
+            uint64_t nb = 0, b, npairs = 0, q0;
+            uint32_t *mem, *V, *nvis;
+            sg_pair *pairs;
+            for (g = 0; g < S; g++) {
+                uint32_t size = pass == 0 ? (round == 0 ? 1u : (round - 1 < 31 ? 1u << (round - 1) : cap[g])) : cap[g];
+                if (size > cap[g]) size = cap[g];
+                if (start[g] < cnt[g]) nb += (cnt[g] - start[g] < size) ? cnt[g] - start[g] : size;
+            }
+            if (nb == 0) { free(start); break; }
+            mem = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+            V = (uint32_t *)malloc(sizeof(uint32_t) * nb * iter_cap);
+            nvis = (uint32_t *)malloc(sizeof(uint32_t) * nb);
+            pairs = (sg_pair *)malloc(sizeof(sg_pair) * nb * R);
+            nb = 0;
+            for (g = 0; g < S; g++) {
+                uint32_t size = pass == 0 ? (round == 0 ? 1u : (round - 1 < 31 ? 1u << (round - 1) : cap[g])) : cap[g];
+                uint32_t e;
+                if (size > cap[g]) size = cap[g];
+                for (e = 0; e < size && start[g] < cnt[g]; e++, start[g]++) {
+                    uint32_t pos = start[g];       /* insertion position -> member index */
+                    uint32_t idx = pos == 0 ? epos[g] : (pos - 1 < epos[g] ? pos - 1 : pos);
+                    mem[nb++] = (uint32_t)(gstart[g] + idx);
+                }
+            }
+            /* GreedySearch of every member against the round's starting graph */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+            for (int64_t bb = 0; bb < (int64_t)nb; bb++) {
+                uint32_t p = mem[bb], gg = sh[0], k1;
+                float d1;
+                int32_t st;
+                uint64_t nd;
+                orc_index ix;
+                uint32_t lo = 0, hi = S;
+                while (hi - lo > 1) {              /* shard of virtual node p */
+                    uint32_t mid = (lo + hi) / 2;
+                    if (gstart[mid] <= p) lo = mid; else hi = mid;
+                }
+                while (lo + 1 < S && gstart[lo + 1] <= p) lo++;
+                gg = lo;
+                memset(&ix, 0, sizeof ix);
+                ix.d = d; ix.M = 1; ix.R = R; ix.medoid = entry[gg]; ix.n = nv; ix.dtype = dtype;
+                ix.adj = vadj; ix.base = vbase;
+                search_one(&ix, vbase + (uint64_t)p * d * esz, 1, 1, Lb, log2z, iter_cap, &k1, &d1,
+                           &nvis[bb], &st, &nd, V + (uint64_t)bb * iter_cap, iter_cap);
+                if (nvis[bb] > iter_cap) nvis[bb] = iter_cap;
+            }
+            /* RobustPrune of every member's visited set and current list */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads)
+#endif
+            for (int64_t bb = 0; bb < (int64_t)nb; bb++) {
+                uint32_t p = mem[bb], r;
+                uint32_t *c = (uint32_t *)malloc(sizeof(uint32_t) * (iter_cap + R));
+                uint32_t nc = 0;
+                for (r = 0; r < nvis[bb]; r++) c[nc++] = V[(uint64_t)bb * iter_cap + r];
+                for (r = 0; r < R; r++) c[nc++] = vadj[(uint64_t)p * R + r];
+                sg_list(vbase, dtype, d, p, c, nc, a, R, 1, vadj + (uint64_t)p * R);
+                free(c);
+            }
+            /* reverse edges */
+            for (b = 0; b < nb; b++) {
+                uint32_t p = mem[b], r;
+                for (r = 0; r < R; r++) {
+                    uint32_t q = vadj[(uint64_t)p * R + r];
+                    if (q == ORC_NONE) break;
+                    pairs[npairs].q = q;
+                    pairs[npairs].p = p;
+                    npairs++;
+                }
+            }
+            qsort(pairs, npairs, sizeof(sg_pair), sg_pair_cmp);
+            {
+                uint64_t *segs = (uint64_t *)malloc(sizeof(uint64_t) * (npairs + 1));
+                uint64_t ns = 0;
+                for (q0 = 0; q0 < npairs; q0++)
+                    if (q0 == 0 || pairs[q0].q != pairs[q0 - 1].q) segs[ns++] = q0;
+                segs[ns] = npairs;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 16) num_threads(nthreads)
+#endif
+                for (int64_t sgi = 0; sgi < (int64_t)ns; sgi++) {
+                    uint64_t lo = segs[sgi], hi = segs[sgi + 1], e;
+                    uint32_t q = pairs[lo].q, r, nc = 0;
+                    uint32_t *c = (uint32_t *)malloc(sizeof(uint32_t) * (R + (hi - lo)));
+                    for (r = 0; r < R; r++) c[nc++] = vadj[(uint64_t)q * R + r];
+                    for (e = lo; e < hi; e++) c[nc++] = pairs[e].p;
+                    sg_list(vbase, dtype, d, q, c, nc, a, R, 0, vadj + (uint64_t)q * R);
+                    free(c);
+                }
+                free(segs);
+            }
+            free(mem); free(V); free(nvis); free(pairs);
+        }
+    }
+    /* 4. merge the shard lists of every point */
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 64) num_threads(nthreads)
+#endif
+    for (int64_t ii = 0; ii < (int64_t)n; ii++) {
+        uint32_t *c = (uint32_t *)malloc(sizeof(uint32_t) * ell * R);
+        uint32_t nc = 0, tt, r;
+        for (tt = 0; tt < ell; tt++) {
+            uint32_t vv = vid[(uint64_t)ii * ell + tt];
+            for (r = 0; r < R; r++) {
+                uint32_t q = vadj[(uint64_t)vv * R + r];
+                if (q != ORC_NONE) c[nc++] = vpt[q];
+            }
+        }
+        sg_list(X, dtype, d, (uint32_t)ii, c, nc, alpha, R, 0, adj + (uint64_t)ii * R);
+        free(c);
+    }
+    if (shard_of) memcpy(shard_of, sh, sizeof(uint32_t) * nv);
+done:
+    free(sh); free(vid); free(cnt); free(gstart); free(cur); free(vpt); free(vadj); free(entry);
+    free(epos); free(cap); free(vbase);
+    return rc;
+}
+
+/* ---------------------------------------------------------------------- */
 /* Brute-force ground truth (§6.3, k-recall@k): exact distances in FP64    */
 /* (exact integers for integer data) to every point, sorted by             */
 /* (distance, id), first k.                                                */

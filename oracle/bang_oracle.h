@@ -45,6 +45,13 @@ int orc_cluster_graph(const void *X, int dtype, uint32_t d, uint64_t n, const ui
                       const uint64_t *gstart, uint32_t ng, const uint32_t *medoids, uint32_t R,
                       float alpha, uint32_t nx, const uint32_t *xclu, uint32_t nh,
                       const uint32_t *hclu, uint32_t *adj);
+/* Overlapping-shard graph (§2.2): see the C file for the steps.  centres is
+ * S*d floats; adj is n*R (rows sorted by (distance, id), NONE padding);
+ * shard_of (n*ell, may be NULL) receives each point's shards, nearest first. */
+int orc_shard_graph(const void *X, int dtype, uint64_t n, uint32_t d, const float *centres,
+                    uint32_t S, uint32_t ell, uint32_t R, uint32_t Lb, float alpha,
+                    float batch_frac, uint32_t log2z, uint32_t iter_cap, uint32_t *adj,
+                    uint32_t *shard_of, int nthreads);
 void orc_adc_table_f32(const float *q, uint32_t M, const uint32_t *off,
                        const float *codebook, float *T);
 float orc_adc_dist_f32(const float *T, uint32_t M, const uint8_t *code);

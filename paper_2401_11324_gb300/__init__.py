@@ -112,6 +112,8 @@ def _load():
     L.bang_build_cluster_graph.argtypes = [i32, vp, i32, u64, u32, vp, vp, u32, vp, u32,
                                            ctypes.c_float, u32, vp, u32, vp, vp, vp]
     L.bang_ground_truth.argtypes = [i32, vp, vp, i32, u64, u32, u32, u32, vp, vp, vp]
+    L.bang_build_shard_graph.argtypes = [i32, vp, i32, u64, u32, vp, u32, u32, u32, u32,
+                                         ctypes.c_float, ctypes.c_float, u32, u32, vp, vp, vp]
     L.bang_build_pq.argtypes = [i32, vp, i32, u64, u32, u32, vp, u64, vp, u32, vp, vp, vp]
     L.bang_autotune.argtypes = [vp, vp, u32, u32, u32, vp, ctypes.POINTER(bang_autotune_opts),
                                 ctypes.POINTER(bang_autotune_result), vp]
@@ -122,7 +124,8 @@ def _load():
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
               "bang_search_batched_noalloc", "bang_index_info", "bang_server_start", "bang_pq_tables",
               "bang_server_submit", "bang_server_wait", "bang_server_stop", "bang_autotune",
-              "bang_build_cluster_graph", "bang_build_pq", "bang_ground_truth"):
+              "bang_build_cluster_graph", "bang_build_pq", "bang_ground_truth",
+              "bang_build_shard_graph"):
         getattr(L, f).restype = i32
     _lib = L
     return L
@@ -257,6 +260,23 @@ def bang_build_cluster_graph(base, members, gstart, medoids, R, alpha, nx=0, xcl
                                           len(medoids), _ptr(medoids), R, alpha, nx, _ptr(xclu), nh,
                                           _ptr(hclu), _ptr(adj), s))
     return adj
+
+
+def bang_build_shard_graph(base, centres, ell, R, Lb, alpha, batch_frac=0.02, log2z=16, iter_cap=0,
+                           adj=None, device=0, stream=None):
+    """Overlapping-shard graph built on the GPU (§2.2); returns (adj n x R
+    uint32, numpy unless a device tensor is passed, shard assignment n x ell)."""
+    n, d = base.shape
+    dt = _DTYPES[np.dtype(str(base.dtype).replace("torch.", ""))]
+    centres = np.ascontiguousarray(centres, np.float32)
+    if adj is None:
+        adj = np.zeros((n, R), np.uint32)
+    sh = np.zeros((n, ell), np.uint32)
+    s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
+    _check(lib().bang_build_shard_graph(device, _ptr(base), dt, n, d, _ptr(centres),
+                                        centres.shape[0], ell, R, Lb, alpha, batch_frac, log2z,
+                                        iter_cap, _ptr(adj), _ptr(sh), s))
+    return adj, sh
 
 
 def bang_build_pq(base, M, sample, init, iters=10, device=0, stream=None):

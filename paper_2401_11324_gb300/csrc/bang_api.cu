@@ -773,6 +773,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     }
 
     bang::SearchArgs a;
+    std::memset(&a, 0, sizeof a);
     a.queries = dptr(0);
     a.codebook = ix->codebook;
     a.off = ix->off;

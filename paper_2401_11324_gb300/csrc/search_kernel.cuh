@@ -88,6 +88,7 @@ struct SearchArgs {
     const uint16_t *tables;   // BF16 mode: nq*M*256 precomputed tables (tensor cores), or null
     const unsigned int *tables_err;  // set when the table kernel gave up
     unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
+    const uint32_t *entry;    // device or null: per-query start node (null: every query starts at medoid)
 };
 
 // Phases timed when SearchArgs::phase_cycles is set.
@@ -650,15 +651,16 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         clk.mark(kPhTable);
 
         // ---- start: worklist = {medoid}, medoid marked seen
+        const uint32_t s0 = a.entry ? a.entry[q] : a.medoid;
         uint32_t dm_bits = 0;
         if (!kPQ) {
             VecShare<DT, DCH> xs;
-            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(a.medoid) * a.vstride, d,
+            load_share<DT, DCH>(static_cast<const E *>(a.base) + static_cast<uint64_t>(s0) * a.vstride, d,
                                 a.vecb_ok != 0, lane, xs);
             dm_bits = exact_distance_bits<DT, DCH>(qs, xs);
         }
         if (lane == 0) {
-            const uint32_t s = a.medoid;
+            const uint32_t s = s0;
             if (kPQ)
                 dm_bits = pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(s) * a.Mpad, a.M, a.Mpad);
             Lk[0] = make_key(dm_bits, s);
@@ -670,7 +672,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         bool have_next = !table_failed;
         int32_t status = table_failed ? 2 : 0;
         uint64_t ck = ~0ull;               // register top-k (k <= kRegK): lane i holds rank i
-        uint32_t cur = a.medoid;
+        uint32_t cur = s0;
         NodeData<DT, RPL, DCH, NC> nd, nd2;   // nd2: the speculative request (a.spec)
         load_node<DT, RPL, DCH, kPQ, NC>(a, cur, lane, nd);
         __syncwarp();
