@@ -14,10 +14,13 @@ Parity status of each function (see the C file for the passage it follows):
   cluster_graph          : pinned by closed forms (a line with alpha = 1 gives
                            the chain; a huge alpha gives the exact nearest
                            lists) and by the generator's independent build
-  vamana_build           : invariants only ("parity unpinned" beyond degree,
-                           self-loop, duplicate, pruning-rule and reachability
-                           checks; the paper takes the graph from DiskANN and
-                           does not state the construction)
+  vamana_build           : pinned by hand-worked builds (the chain at alpha = 1,
+                           a reverse-edge overflow pruned back, an edge the
+                           second pass restores) and invariants
+  shard_graph            : pinned by closed forms (nearest-centre assignment,
+                           complete rows when nothing is pruned, the chain at
+                           alpha = 1), a hand-worked build that separates the
+                           two passes' parameters, and invariants
 """
 import ctypes
 import os

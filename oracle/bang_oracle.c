@@ -27,6 +27,9 @@
  *                            RobustPrune + reverse edges; pinned by hand-worked
  *                            builds (a chain, a reverse-edge overflow, an edge
  *                            the second pass restores) and invariants
+ *   orc_shard_graph          §2.2 (the index is built on overlapping clusters
+ *                            with GreedySearch and RobustPrune and the subgraphs'
+ *                            edges merged), in a batched form
  *   orc_cluster_graph        the clustered construction of the large synthetic
  *                            indexes (per-cluster candidates, RobustPrune of §2.2,
  *                            reverse edges, medoid links); not from the paper

@@ -54,6 +54,17 @@ MUTANTS = [
     ("vamana_overflow_replaces_last",
      "nk = orc_robust_prune(X, d, j, c2, k2, a, R, kept);\n                    for (r = 0; r < R; r++) lj[r] = r < nk ? kept[r] : ORC_NONE;",
      "nk = 0 * k2 + 0 * kept[0];\n                    lj[R - 1] = p;", 0),
+    ("shard_alpha_in_pass1", "float a = pass == 0 ? 1.0f : alpha;\n        uint32_t *start",
+     "float a = alpha;\n        uint32_t *start", 0),
+    ("shard_no_reverse_edges", "sg_list(vbase, dtype, d, q, c, nc, a, R, 0, vadj + (uint64_t)q * R);",
+     "(void)nc;", 0),
+    ("shard_merge_one_shard", "for (tt = 0; tt < ell; tt++) {\n            uint32_t vv",
+     "for (tt = 0; tt < 1; tt++) {\n            uint32_t vv", 0),
+    ("shard_farthest_centres", "best[gg].dist = sg_centre_dist(", "best[gg].dist = -sg_centre_dist(", 0),
+    ("shard_farthest_entry", "if (entry[g] == ORC_NONE || dd < bd)", "if (entry[g] == ORC_NONE || dd > bd)", 0),
+    ("shard_keeps_repeats", "if (u == 0 || c[i].id != c[u - 1].id) c[u++] = c[i];", "c[u++] = c[i];", 0),
+    ("shard_ties_larger_id", "return (a->id < b->id) ? -1 : (a->id > b->id);\n}\n\nstatic float sg_dist",
+     "return (a->id > b->id) ? -1 : (a->id < b->id);\n}\n\nstatic float sg_dist", 0),
     ("exact_mode_keeps_rerank", "if (mode == 1) {                    /* Alg. 1",
      "if (mode == 7) {                    /* Alg. 1", 0),
 ]

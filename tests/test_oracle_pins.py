@@ -842,3 +842,92 @@ def test_vamana_second_pass_keeps_what_the_first_pruned():
     X = np.array([[8, 10], [6, 10], [8, 9], [5, 0]], np.float32)
     adj = _vamana_empty(X, 2, 8, 1.2, 0, [1, 2, 3, 0])
     assert adj.tolist() == [[2, 1], [0, 3], [0, 1], [2, NONE]]
+
+
+# ---------------------------------------------------------------- overlapping-shard graph (§2.2)
+
+def _sorted_others(X, i, pool):
+    """Members of pool other than i, sorted by (exact squared distance, id)."""
+    d = ((X[pool].astype(np.int64) - X[i].astype(np.int64)) ** 2).sum(1)
+    keep = [(int(dd), int(p)) for dd, p in zip(d, pool) if p != i]
+    return [p for _, p in sorted(keep)]
+
+
+def test_shard_assignment_is_the_nearest_centres():
+    rng = np.random.default_rng(41)
+    X = rng.integers(0, 256, size=(500, 6)).astype(np.uint8)
+    cen = rng.integers(0, 256, size=(7, 6)).astype(np.float32)
+    _, sh = oracle.shard_graph(X, cen, 3, 8, 8, 1.2)
+    d = ((X.astype(np.int64)[:, None] - cen.astype(np.int64)[None]) ** 2).sum(-1)
+    want = np.argsort(d, axis=1, kind="stable")[:, :3]        # ties: smaller centre index
+    assert (sh == want).all()
+
+
+def test_shard_graph_without_pruning_is_complete_per_shard():
+    # alpha huge removes nothing and R >= n - 1, Lb >= n: every shard's
+    # subgraph is complete, so a point's row is every other member of its
+    # shards, sorted by (distance, id); with ell < S the shards differ.
+    rng = np.random.default_rng(42)
+    n = 40
+    X = np.unique(rng.integers(0, 256, size=(n + 10, 3)), axis=0)[:n].astype(np.uint8)
+    X = X[rng.permutation(n)]
+    for S, ell in ((1, 1), (2, 2), (3, 2)):
+        cen = X[:S].astype(np.float32)
+        adj, sh = oracle.shard_graph(X, cen, ell, 40, 64, 1e6, 0.1, 16, iter_cap=200)
+        for i in range(n):
+            pool = np.where((sh[:, :, None] == sh[i][None, None, :]).any((1, 2)))[0]
+            want = _sorted_others(X, i, pool)
+            assert adj[i, :len(want)].tolist() == want, (S, ell, i)
+            assert (adj[i, len(want):] == NONE).all()
+
+
+def test_shard_graph_line_alpha1_is_the_chain():
+    # one shard, alpha = 1, R = 2, points on a line with distinct gaps: every
+    # point keeps its nearest neighbour on each side, nearer first.
+    rng = np.random.default_rng(43)
+    n = 30
+    pos = np.cumsum(rng.integers(1, 5, size=n))
+    assert pos.max() < 256
+    ids_by_pos = rng.permutation(n)
+    X = np.zeros((n, 1), np.uint8)
+    X[ids_by_pos, 0] = pos
+    adj, _ = oracle.shard_graph(X, X[[ids_by_pos[n // 2]]].astype(np.float32), 1, 2, 64, 1.0, 0.1, 16,
+                                iter_cap=200)
+    for k in range(n):
+        a = ids_by_pos[k]
+        nb = sorted((int(pos[j] - pos[k]) ** 2, int(ids_by_pos[j])) for j in (k - 1, k + 1) if 0 <= j < n)
+        want = [b for _, b in nb]
+        assert adj[a].tolist() == want + [NONE] * (2 - len(want)), (k, adj[a], want)
+
+
+def test_shard_graph_second_pass_keeps_what_the_first_pruned():
+    # One shard centred on point 0 (its entry), insertion 0, 1, 2, 3 one at a
+    # time (batch cap 1), R = 2, alpha = 1.2.  Points 0:(0,11) 1:(9,11)
+    # 2:(4,1) 3:(6,11); squared distances d01 81, d02 116, d03 36, d12 125,
+    # d13 9, d23 104.  Pass 1 (parameter 1): 1 -> [0], 0 gets 1; 2 -> [0]
+    # (1 removed: d01 81 <= d21 125), 0 -> [1, 2]; 3 searches 0, 1, 2 and
+    # keeps [1, 0]; 1 -> [3, 0]; 0's union {1, 2, 3} is pruned to [3] (3
+    # removes 1: 9 <= 81 and 2: 104 <= 116).  Pass 2 (alpha^2 = 1.44): 0 ->
+    # [3] (1.44 * 9 <= 81); 1 -> [3] (1.44 * 36 <= 81); 2 -> [3]; 3's union
+    # {1, 0, 2} is pruned to [1, 0] (1.44 * 81 > 36 keeps 0, R reached);
+    # 3 -> [1, 0].  With alpha in pass 1, 0 would keep 2 (1.44 * 104 > 116).
+    X = np.array([[0, 11], [9, 11], [4, 1], [6, 11]], np.float32)
+    pos = [oracle.Bloom(16).positions(i) for i in range(4)]
+    assert len({p for pp in pos for p in pp}) == 8            # no Bloom false positive
+    adj, _ = oracle.shard_graph(X, X[[0]], 1, 2, 8, 1.2, 0.01, 16)
+    assert adj.tolist() == [[3, NONE], [3, NONE], [3, NONE], [1, 0]]
+
+
+def test_shard_graph_invariants():
+    rng = np.random.default_rng(44)
+    n = 1200
+    cen0 = rng.integers(30, 220, size=(5, 8))
+    X = np.clip(cen0[rng.integers(0, 5, n)] + rng.normal(0, 20, (n, 8)), 0, 255).astype(np.uint8)
+    adj, sh = oracle.shard_graph(X, X[:4].astype(np.float32), 2, 16, 24, 1.2, 0.05, 14)
+    for i in range(n):
+        row = adj[i]
+        ids = row[row != NONE].astype(np.int64)
+        assert len(ids) >= 1 and (row[len(ids):] == NONE).all()
+        assert i not in ids.tolist() and len(set(ids.tolist())) == len(ids)
+        dd = ((X[ids].astype(np.int64) - X[i].astype(np.int64)) ** 2).sum(1)
+        assert [(int(a), int(b)) for a, b in zip(dd, ids)] == sorted(zip(dd.tolist(), ids.tolist()))
