@@ -334,7 +334,9 @@ int bang_build_cluster_graph(int device, const void *base, bang_dtype dtype, uin
  *      in R, else RobustPrune'd with alpha.
  * Distances are the exact squared L2 of the search's Exact-distance mode
  * rounded to FP32; lists are sorted by (distance, id) without repeats or the
- * owner.  RobustPrune keeps, in that order, each live candidate (at most R)
+ * owner and cut to their 750 nearest (the bound DiskANN puts on the
+ * candidate pool; only reverse edges into hub nodes reach it).  RobustPrune
+ * keeps, in that order, each live candidate (at most R)
  * and removes every later candidate c with a^2 * d(kept, c) <= d(owner, c),
  * a^2 and the product in FP32.  Rows are written sorted, 0xFFFFFFFF padding.
  *   base      n*d elements of dtype, host or device; n*ell < 2^31 - 1.
@@ -346,8 +348,8 @@ int bang_build_cluster_graph(int device, const void *base, bang_dtype dtype, uin
  *             (each point's shards, nearest centre first).
  * Device memory: about n*ell*(R*4 + d*elem rounded to 16, then to 32 bytes
  * per record) plus per-round scratch (about 40*R bytes per member of the
- * largest round).  Blocks until done.  BANG_EINVAL also when a node gains
- * more than 16,384 reverse candidates in one round (lower batch_frac). */
+ * largest round, and 8 bytes per candidate of the longest reverse-edge
+ * lists).  Blocks until done. */
 int bang_build_shard_graph(int device, const void *base, bang_dtype dtype, uint64_t n, uint32_t d,
                            const float *centres, uint32_t S, uint32_t ell, uint32_t R, uint32_t Lb,
                            float alpha, float batch_frac, uint32_t log2z, uint32_t iter_cap,

@@ -955,13 +955,17 @@ int orc_max_threads(void)
 /*  4. merge: point i's row is the union of its shard lists (as point ids), */
 /*     sorted when it fits in R, else RobustPrune(i, union) with alpha.     */
 /* Distances are orc_exact_dist rounded to FP32; candidate lists are sorted */
-/* by (distance, id) with repeats and the point itself removed; every row   */
-/* is kept in that order.  RobustPrune: in that order, a live candidate is  */
-/* kept (at most R) and removes each later candidate c with                 */
-/* a^2 * d(kept, c) <= d(p, c), a^2 and the product rounded to FP32.        */
+/* by (distance, id) with repeats and the point itself removed, and cut to  */
+/* their 750 nearest (DiskANN's bound on the candidate pool; only reverse   */
+/* edges into hubs reach it); every row is kept in that order.  RobustPrune:*/
+/* in that order, a live candidate is kept (at most R) and removes each     */
+/* later candidate c with a^2 * d(kept, c) <= d(p, c), a^2 and the product  */
+/* rounded to FP32.                                                         */
 /* ---------------------------------------------------------------------- */
 
 typedef struct { float dist; uint32_t id; } sg_cand;
+
+#define SG_CAND_CAP 750       /* RobustPrune considers the 750 nearest candidates (DiskANN's bound) */
 
 static int sg_cmp(const void *pa, const void *pb)
 {
@@ -1011,6 +1015,7 @@ static uint32_t sg_list(const void *V, int dtype, uint32_t d, uint32_t p, const 
     qsort(c, m, sizeof(sg_cand), sg_cmp);
     for (i = 0; i < m; i++)
         if (u == 0 || c[i].id != c[u - 1].id) c[u++] = c[i];
+    if (u > SG_CAND_CAP) u = SG_CAND_CAP;
     if (u <= R && !always_prune) {
         for (i = 0; i < u; i++) out[nout++] = c[i].id;
     } else {

@@ -25,7 +25,8 @@
 // data exact; f32 as 32 partial sums of ascending dimensions, lane r owning
 // the dimensions j with (j/4) mod 32 = r, fmaf, then an xor butterfly 16..1).
 // Candidate lists are sorted by (distance, id), repeats and the owner
-// removed.  RobustPrune: in that order a live candidate is kept (at most R)
+// removed, and cut to their 750 nearest (DiskANN's bound on the candidate
+// pool; only reverse edges into hub nodes reach it).  RobustPrune: in that order a live candidate is kept (at most R)
 // and removes every later candidate c with a^2 * d(kept, c) <= d(owner, c),
 // a^2 and the product rounded to FP32.
 //
@@ -54,8 +55,9 @@ constexpr uint32_t kNo = 0xFFFFFFFFu;
 constexpr int kW = 32;
 constexpr int kKPL = 2;                  // candidates per lane per prune block (registers)
 constexpr uint32_t kRegWords = 32;       // integer vectors of at most 128 bytes sit in registers
-constexpr uint32_t kSmallC = 512;        // candidates of a list sorted by the small-job kernel
-constexpr uint32_t kLargeC = 16384;      // candidates of the large-job kernel, at most (powers of 2)
+constexpr uint32_t kSmallC = 512;        // candidates of a list sorted by one warp in shared memory
+constexpr uint32_t kCandCap = 750;       // RobustPrune looks at the nearest 750 candidates at most
+constexpr uint32_t kKeySlots = 768;      // shared key slots: >= kSmallC and >= kCandCap
 constexpr size_t kSmemMax = 227u * 1024u;
 constexpr uint32_t kChunk = 1u << 20;    // searches per launch
 constexpr int kScanT = 1024;
@@ -114,11 +116,8 @@ struct LArgs {
     uint64_t p0;
     const uint32_t *vid, *vpt;
     uint32_t *out_rows;      // merge output, njobs rows of R
-    // large-job deferral
-    uint32_t ccap;           // candidates this launch can sort
-    uint32_t *defer, *ndefer;   // jobs above ccap (small kernel), or the job list (large kernel)
-    const uint32_t *job_list;   // null: job j = j
-    unsigned int *err;       // set when a list exceeds the large kernel's capacity
+    // lists longer than kSmallC, handed to big_list_kernel
+    uint32_t *defer, *ndefer;
 };
 
 __device__ __forceinline__ const uint32_t *vec_ptr(const LArgs &a, uint32_t v)
@@ -197,79 +196,267 @@ __device__ __forceinline__ uint64_t mkkey(float dist, uint32_t id)
 __device__ __forceinline__ uint32_t kid(uint64_t k) { return static_cast<uint32_t>(k); }
 __device__ __forceinline__ float kdist(uint64_t k) { return __uint_as_float(static_cast<uint32_t>(k >> 32)); }
 
-// One warp per list.  Shared memory: candidate ids and keys (ccap each), the
-// owner's vector, the kept vectors (R) and ids.
-template <int DT>
-__global__ void __launch_bounds__(32) list_kernel(const LArgs a)
+// Candidate ids of a job (the owner excluded later): forward = its
+// expansions then its current row; reverse = its current row then the
+// members that named it; merge = its shards' rows as point ids.  Writes
+// ids[i] for i < returned count when the count is at most cap.
+__device__ __forceinline__ uint32_t job_candidates(const LArgs &a, uint32_t job, uint32_t cap, uint32_t *ids,
+                                                   uint32_t &owner, int tid, int nthreads)
 {
-    extern __shared__ __align__(16) unsigned char sm[];
-    const int lane = threadIdx.x;
-    uint64_t *keys = reinterpret_cast<uint64_t *>(sm);
-    uint32_t *ids = reinterpret_cast<uint32_t *>(keys + a.ccap);
-    uint32_t *ovec = ids + a.ccap;
-    uint32_t *kvec = ovec + a.vwords;
-    uint32_t *kept = kvec + a.R * a.vwords;
-    const bool regs = DT != 2 && a.vwords <= kRegWords;
-
-    for (uint32_t jj = blockIdx.x; jj < a.njobs; jj += gridDim.x) {
-        const uint32_t job = a.job_list ? a.job_list[jj] : jj;
-        // ---- owner and candidate ids
-        uint32_t owner, C = 0;
-        const uint32_t *ovp;
-        if (a.kind == kJobFwd) {
-            owner = a.members[job];
-            ovp = vec_ptr(a, owner);
-            const uint32_t ni = min(a.iters[job], a.tcap);
-            C = ni + a.R;
-            if (C <= a.ccap) {
-                for (uint32_t i = lane; i < ni; i += kW) ids[i] = a.trace[static_cast<uint64_t>(job) * a.tcap + i];
-                for (uint32_t i = lane; i < a.R; i += kW) ids[ni + i] = a.rec[static_cast<uint64_t>(owner) * a.rec_words + i];
-            }
-        } else if (a.kind == kJobRev) {
-            owner = a.touched[job];
-            ovp = vec_ptr(a, owner);
-            const uint32_t ni = a.in_cnt[job];
-            C = ni + a.R;
-            if (C <= a.ccap) {
-                for (uint32_t i = lane; i < a.R; i += kW) ids[i] = a.rec[static_cast<uint64_t>(owner) * a.rec_words + i];
-                for (uint32_t i = lane; i < ni; i += kW) ids[a.R + i] = a.in_src[a.in_off[job] + i];
-            }
-        } else {
-            owner = static_cast<uint32_t>(a.p0 + job);
-            ovp = cand_vec(a, owner);
-            C = a.ell * a.R;
-            for (uint32_t i = lane; i < C; i += kW) {
+    uint32_t C;
+    if (a.kind == kJobFwd) {
+        owner = a.members[job];
+        const uint32_t ni = min(a.iters[job], a.tcap);
+        C = ni + a.R;
+        if (C <= cap) {
+            for (uint32_t i = tid; i < ni; i += nthreads) ids[i] = a.trace[static_cast<uint64_t>(job) * a.tcap + i];
+            for (uint32_t i = tid; i < a.R; i += nthreads)
+                ids[ni + i] = a.rec[static_cast<uint64_t>(owner) * a.rec_words + i];
+        }
+    } else if (a.kind == kJobRev) {
+        owner = a.touched[job];
+        const uint32_t ni = a.in_cnt[job];
+        C = ni + a.R;
+        if (C <= cap) {
+            for (uint32_t i = tid; i < a.R; i += nthreads) ids[i] = a.rec[static_cast<uint64_t>(owner) * a.rec_words + i];
+            for (uint32_t i = tid; i < ni; i += nthreads) ids[a.R + i] = a.in_src[a.in_off[job] + i];
+        }
+    } else {
+        owner = static_cast<uint32_t>(a.p0 + job);
+        C = a.ell * a.R;
+        if (C <= cap) {
+            for (uint32_t i = tid; i < C; i += nthreads) {
                 const uint32_t v = a.vid[static_cast<uint64_t>(owner) * a.ell + i / a.R];
                 const uint32_t q = a.rec[static_cast<uint64_t>(v) * a.rec_words + i % a.R];
                 ids[i] = q == kNo ? kNo : a.vpt[q];
             }
         }
-        if (C > a.ccap) {                       // sorted by the large-job kernel (or too large)
-            if (lane == 0) {
-                if (a.defer) a.defer[atomicAdd(a.ndefer, 1u)] = job;
-                else atomicOr(a.err, 1u);
+    }
+    return C;
+}
+
+__device__ __forceinline__ const uint32_t *owner_vec(const LArgs &a, uint32_t owner)
+{
+    return a.kind == kJobMerge ? cand_vec(a, owner) : vec_ptr(a, owner);
+}
+
+__device__ __forceinline__ uint32_t *job_out(const LArgs &a, uint32_t job, uint32_t owner)
+{
+    return a.kind == kJobFwd ? a.staging + static_cast<uint64_t>(job) * a.R
+         : a.kind == kJobRev ? a.recw + static_cast<uint64_t>(owner) * a.rec_words
+                             : a.out_rows + static_cast<uint64_t>(job) * a.R;
+}
+
+// Compact C sorted keys (from `src`, shared or global) into dst without
+// repeats or invalid keys, keeping at most kCandCap; returns the count.  The
+// key before each 32-key chunk is carried in a register, since the
+// compaction may overwrite its slot when src == dst.  One warp.
+__device__ __forceinline__ uint32_t dedupe_keys(const uint64_t *src, uint32_t C, uint64_t *dst, int lane)
+{
+    uint32_t u = 0;
+    uint64_t last = ~0ull;                 // id part 0xFFFFFFFF: no valid id
+    for (uint32_t c0 = 0; c0 < C && u < kCandCap; c0 += kW) {
+        const uint32_t i = c0 + lane;
+        const uint64_t x = i < C ? src[i] : ~0ull;
+        uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, x, 1);
+        if (lane == 0) prev = last;
+        last = __shfl_sync(0xFFFFFFFFu, x, kW - 1);
+        const bool keep = x != ~0ull && kid(prev) != kid(x);
+        __syncwarp();
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
+        const uint32_t pos = u + __popc(bal & ((1u << lane) - 1u));
+        if (keep && pos < kCandCap) dst[pos] = x;
+        u = min(u + __popc(bal), kCandCap);
+        __syncwarp();
+    }
+    return u;
+}
+
+// The list of `owner` from u sorted unique keys (shared memory): the keys
+// themselves when they fit in R and the job does not always prune, else
+// RobustPrune over them, 32 * kKPL candidates at a time.  One warp.
+template <int DT>
+__device__ void finish_list(const LArgs &a, const uint64_t *keys, uint32_t u, const uint32_t *ovec,
+                            uint32_t *kvec, uint32_t *kept, uint32_t *out, int lane)
+{
+    const bool regs = DT != 2 && a.vwords <= kRegWords;
+    if (u <= a.R && !a.always_prune) {
+        for (uint32_t i = lane; i < a.R; i += kW) out[i] = i < u ? kid(keys[i]) : kNo;
+        __syncwarp();
+        return;
+    }
+    uint32_t nout = 0;
+    for (uint32_t b0 = 0; b0 < u && nout < a.R; b0 += kW * kKPL) {
+        uint32_t cid[kKPL];
+        float dp[kKPL];
+        bool alive[kKPL];
+        uint32_t cv[kKPL][kRegWords];
+#pragma unroll
+        for (int s = 0; s < kKPL; ++s) {
+            const uint32_t i = b0 + s * kW + lane;
+            alive[s] = i < u;
+            cid[s] = alive[s] ? kid(keys[i]) : kNo;
+            dp[s] = alive[s] ? kdist(keys[i]) : 0.0f;
+            if (regs) {
+                const uint32_t *src = alive[s] ? cand_vec(a, cid[s]) : ovec;
+#pragma unroll
+                for (uint32_t w = 0; w < kRegWords; ++w) cv[s][w] = w < a.vwords ? src[w] : 0u;
             }
+        }
+        // kept neighbours of earlier blocks
+        for (uint32_t t = 0; t < nout; ++t) {
+            const uint32_t *kv = kvec + t * a.vwords;
+#pragma unroll
+            for (int s = 0; s < kKPL; ++s) {
+                if (!alive[s]) continue;
+                const float dd = regs ? __uint2float_rn(idist_reg<DT>(cv[s], kv, a.vwords))
+                                      : vdist<DT>(a, kv, cand_vec(a, cid[s]));
+                if (__fmul_rn(a.a2, dd) <= dp[s]) alive[s] = false;
+            }
+        }
+        // walk this block in order
+        for (uint32_t pos = 0; pos < kW * kKPL && b0 + pos < u && nout < a.R; ++pos) {
+            const int s = static_cast<int>(pos / kW), l = static_cast<int>(pos % kW);
+            bool mine = false;
+#pragma unroll
+            for (int t = 0; t < kKPL; ++t) if (t == s) mine = alive[t];
+            if (!__shfl_sync(0xFFFFFFFFu, mine ? 1 : 0, l)) continue;
+            uint32_t *kv = kvec + nout * a.vwords;
+            if (lane == l) {
+#pragma unroll
+                for (int t = 0; t < kKPL; ++t) {
+                    if (t != s) continue;
+                    kept[nout] = cid[t];
+                    alive[t] = false;
+                    if (regs) {
+#pragma unroll
+                        for (uint32_t w = 0; w < kRegWords; ++w) if (w < a.vwords) kv[w] = cv[t][w];
+                    }
+                }
+            }
+            if (!regs) {
+                const uint32_t kid_ = __shfl_sync(0xFFFFFFFFu, lane == l ? kept[nout] : 0u, l);
+                const uint32_t *src = cand_vec(a, kid_);
+                for (uint32_t w = lane; w < a.vwords; w += kW) kv[w] = src[w];
+            }
+            __syncwarp();
+#pragma unroll
+            for (int t = 0; t < kKPL; ++t) {
+                if (!alive[t]) continue;
+                const float dd = regs ? __uint2float_rn(idist_reg<DT>(cv[t], kv, a.vwords))
+                                      : vdist<DT>(a, kv, cand_vec(a, cid[t]));
+                if (__fmul_rn(a.a2, dd) <= dp[t]) alive[t] = false;
+            }
+            ++nout;
+        }
+        __syncwarp();
+    }
+    __syncwarp();
+    for (uint32_t i = lane; i < a.R; i += kW) out[i] = i < nout ? kept[i] : kNo;
+    __syncwarp();
+}
+
+// Shared memory of a list (both kernels): kKeySlots keys, kSmallC ids, the
+// owner's vector, the kept vectors (R) and ids.
+struct ListSmem {
+    uint64_t *keys;
+    uint32_t *ids, *ovec, *kvec, *kept;
+    __device__ ListSmem(unsigned char *sm, const LArgs &a)
+    {
+        keys = reinterpret_cast<uint64_t *>(sm);
+        ids = reinterpret_cast<uint32_t *>(keys + kKeySlots);
+        ovec = ids + kSmallC;
+        kvec = ovec + a.vwords;
+        kept = kvec + a.R * a.vwords;
+    }
+};
+
+// One warp per list of at most kSmallC candidates; longer lists are listed
+// in a.defer for big_list_kernel.
+template <int DT>
+__global__ void __launch_bounds__(32) list_kernel(const LArgs a)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int lane = threadIdx.x;
+    const ListSmem m(sm, a);
+    for (uint32_t job = blockIdx.x; job < a.njobs; job += gridDim.x) {
+        uint32_t owner = 0;
+        const uint32_t C = job_candidates(a, job, kSmallC, m.ids, owner, lane, kW);
+        if (C > kSmallC) {
+            if (lane == 0) a.defer[atomicAdd(a.ndefer, 1u)] = job;
             __syncwarp();
             continue;
         }
-        for (uint32_t w = lane; w < a.vwords; w += kW) ovec[w] = ovp[w];
+        const uint32_t *ovp = owner_vec(a, owner);
+        for (uint32_t w = lane; w < a.vwords; w += kW) m.ovec[w] = ovp[w];
         __syncwarp();
-        // ---- keys (distance to the owner, id); invalid entries sort last
+        // keys (distance to the owner, id); invalid entries sort last
         uint32_t P = 32;
         while (P < C) P <<= 1;
         for (uint32_t i = lane; i < P; i += kW) {
             uint64_t k = ~0ull;
             if (i < C) {
-                const uint32_t id = ids[i];
-                if (id != kNo && id != owner) k = mkkey(vdist<DT>(a, ovec, cand_vec(a, id)), id);
+                const uint32_t id = m.ids[i];
+                if (id != kNo && id != owner) k = mkkey(vdist<DT>(a, m.ovec, cand_vec(a, id)), id);
+            }
+            m.keys[i] = k;
+        }
+        __syncwarp();
+        for (uint32_t k = 2; k <= P; k <<= 1)                    // bitonic sort, ascending
+            for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+                for (uint32_t i = lane; i < P; i += kW) {
+                    const uint32_t l = i ^ j;
+                    if (l > i) {
+                        const uint64_t x = m.keys[i], y = m.keys[l];
+                        const bool up = (i & k) == 0;
+                        if ((x > y) == up) { m.keys[i] = y; m.keys[l] = x; }
+                    }
+                }
+                __syncwarp();
+            }
+        const uint32_t u = dedupe_keys(m.keys, C, m.keys, lane);
+        finish_list<DT>(a, m.keys, u, m.ovec, m.kvec, m.kept, job_out(a, job, owner), lane);
+    }
+}
+
+// Lists of more than kSmallC candidates (reverse edges of hub nodes): one
+// 1024-thread CTA per list; the keys are computed and sorted (bitonic) in a
+// global-memory region of the next power of two above the count, then warp 0
+// keeps the kCandCap nearest unique ones and finishes the list.
+template <int DT>
+__global__ void __launch_bounds__(1024) big_list_kernel(const LArgs a, const uint32_t *jobs, uint32_t njobs,
+                                                        const uint64_t *region_off, uint64_t *region)
+{
+    extern __shared__ __align__(16) unsigned char sm[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const ListSmem m(sm, a);
+    for (uint32_t b = blockIdx.x; b < njobs; b += gridDim.x) {
+        const uint32_t job = jobs[b];
+        uint64_t *keys = region + region_off[b];
+        uint32_t owner = 0;
+        const uint32_t C = job_candidates(a, job, 0u, nullptr, owner, tid, blockDim.x);
+        uint32_t P = 32;
+        while (P < C) P <<= 1;
+        const uint32_t *ovp = owner_vec(a, owner);
+        for (uint32_t w = tid; w < a.vwords; w += blockDim.x) m.ovec[w] = ovp[w];
+        __syncthreads();
+        for (uint32_t i = tid; i < P; i += blockDim.x) {
+            uint64_t k = ~0ull;
+            if (i < C) {
+                uint32_t id;
+                if (a.kind == kJobRev)
+                    id = i < a.R ? a.rec[static_cast<uint64_t>(owner) * a.rec_words + i]
+                                 : a.in_src[a.in_off[job] + (i - a.R)];
+                else
+                    id = kNo;                 // only reverse lists exceed kSmallC
+                if (id != kNo && id != owner) k = mkkey(vdist<DT>(a, m.ovec, cand_vec(a, id)), id);
             }
             keys[i] = k;
         }
-        __syncwarp();
-        // ---- bitonic sort, ascending
+        __syncthreads();
         for (uint32_t k = 2; k <= P; k <<= 1)
             for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-                for (uint32_t i = lane; i < P; i += kW) {
+                for (uint32_t i = tid; i < P; i += blockDim.x) {
                     const uint32_t l = i ^ j;
                     if (l > i) {
                         const uint64_t x = keys[i], y = keys[l];
@@ -277,105 +464,26 @@ __global__ void __launch_bounds__(32) list_kernel(const LArgs a)
                         if ((x > y) == up) { keys[i] = y; keys[l] = x; }
                     }
                 }
-                __syncwarp();
+                __syncthreads();
             }
-        // ---- drop repeats (equal ids are adjacent: equal id, equal distance);
-        // the key before each chunk is carried in a register, since the
-        // compaction may already have overwritten its slot
-        uint32_t u = 0;
-        uint64_t last = ~0ull;                 // id part 0xFFFFFFFF: no valid id
-        for (uint32_t c0 = 0; c0 < C; c0 += kW) {
-            const uint32_t i = c0 + lane;
-            const uint64_t x = i < C ? keys[i] : ~0ull;
-            uint64_t prev = __shfl_up_sync(0xFFFFFFFFu, x, 1);
-            if (lane == 0) prev = last;
-            last = __shfl_sync(0xFFFFFFFFu, x, kW - 1);
-            const bool keep = x != ~0ull && kid(prev) != kid(x);
-            __syncwarp();
-            const uint32_t bal = __ballot_sync(0xFFFFFFFFu, keep);
-            if (keep) keys[u + __popc(bal & ((1u << lane) - 1u))] = x;
-            u += __popc(bal);
-            __syncwarp();
+        if (warp == 0) {
+            const uint32_t u = dedupe_keys(keys, C, m.keys, lane);
+            finish_list<DT>(a, m.keys, u, m.ovec, m.kvec, m.kept, job_out(a, job, owner), lane);
         }
-        uint32_t *out = a.kind == kJobFwd ? a.staging + static_cast<uint64_t>(job) * a.R
-                      : a.kind == kJobRev ? a.recw + static_cast<uint64_t>(owner) * a.rec_words
-                                          : a.out_rows + static_cast<uint64_t>(job) * a.R;
-        if (u <= a.R && !a.always_prune) {
-            for (uint32_t i = lane; i < a.R; i += kW) out[i] = i < u ? kid(keys[i]) : kNo;
-            __syncwarp();
-            continue;
-        }
-        // ---- RobustPrune, 32 * kKPL candidates at a time
-        uint32_t nout = 0;
-        for (uint32_t b0 = 0; b0 < u && nout < a.R; b0 += kW * kKPL) {
-            uint32_t cid[kKPL];
-            float dp[kKPL];
-            bool alive[kKPL];
-            uint32_t cv[kKPL][kRegWords];
-#pragma unroll
-            for (int s = 0; s < kKPL; ++s) {
-                const uint32_t i = b0 + s * kW + lane;
-                alive[s] = i < u;
-                cid[s] = alive[s] ? kid(keys[i]) : kNo;
-                dp[s] = alive[s] ? kdist(keys[i]) : 0.0f;
-                if (regs) {
-                    const uint32_t *src = alive[s] ? cand_vec(a, cid[s]) : ovec;
-#pragma unroll
-                    for (uint32_t w = 0; w < kRegWords; ++w) cv[s][w] = w < a.vwords ? src[w] : 0u;
-                }
-            }
-            // kept neighbours of earlier blocks
-            for (uint32_t t = 0; t < nout; ++t) {
-                const uint32_t *kv = kvec + t * a.vwords;
-#pragma unroll
-                for (int s = 0; s < kKPL; ++s) {
-                    if (!alive[s]) continue;
-                    const float dd = regs ? __uint2float_rn(idist_reg<DT>(cv[s], kv, a.vwords))
-                                          : vdist<DT>(a, kv, cand_vec(a, cid[s]));
-                    if (__fmul_rn(a.a2, dd) <= dp[s]) alive[s] = false;
-                }
-            }
-            // walk this block in order
-            for (uint32_t pos = 0; pos < kW * kKPL && b0 + pos < u && nout < a.R; ++pos) {
-                const int s = static_cast<int>(pos / kW), l = static_cast<int>(pos % kW);
-                bool mine = false;
-#pragma unroll
-                for (int t = 0; t < kKPL; ++t) if (t == s) mine = alive[t];
-                if (!__shfl_sync(0xFFFFFFFFu, mine ? 1 : 0, l)) continue;
-                uint32_t *kv = kvec + nout * a.vwords;
-                if (lane == l) {
-#pragma unroll
-                    for (int t = 0; t < kKPL; ++t) {
-                        if (t != s) continue;
-                        kept[nout] = cid[t];
-                        alive[t] = false;
-                        if (regs) {
-#pragma unroll
-                            for (uint32_t w = 0; w < kRegWords; ++w) if (w < a.vwords) kv[w] = cv[t][w];
-                        }
-                    }
-                }
-                if (!regs) {
-                    const uint32_t kid_ = __shfl_sync(0xFFFFFFFFu, lane == l ? kept[nout] : 0u, l);
-                    const uint32_t *src = cand_vec(a, kid_);
-                    for (uint32_t w = lane; w < a.vwords; w += kW) kv[w] = src[w];
-                }
-                __syncwarp();
-#pragma unroll
-                for (int t = 0; t < kKPL; ++t) {
-                    if (!alive[t]) continue;
-                    const float dd = regs ? __uint2float_rn(idist_reg<DT>(cv[t], kv, a.vwords))
-                                          : vdist<DT>(a, kv, cand_vec(a, cid[t]));
-                    if (__fmul_rn(a.a2, dd) <= dp[t]) alive[t] = false;
-                }
-                ++nout;
-            }
-            __syncwarp();
-        }
-        __syncwarp();
-        for (uint32_t i = lane; i < a.R; i += kW) out[i] = i < nout ? kept[i] : kNo;
-        __syncwarp();
+        __syncthreads();
     }
+}
+
+// Region sizes of the big lists: the next power of two above each count.
+__global__ void big_regions(const LArgs a, const uint32_t *jobs, uint32_t njobs, uint64_t *off,
+                            unsigned long long *total)
+{
+    const uint32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= njobs) return;
+    const uint32_t C = a.R + a.in_cnt[jobs[b]];
+    uint32_t P = 32;
+    while (P < C) P <<= 1;
+    off[b] = atomicAdd(total, static_cast<unsigned long long>(P));
 }
 
 // ---- assignment: the ell nearest centres of every point; the shard entries
@@ -593,55 +701,71 @@ cudaError_t scan_counts(const uint32_t *in, uint64_t n, uint64_t *out, DBuf<uint
     return cudaGetLastError();
 }
 
-size_t list_smem(uint32_t ccap, uint32_t vwords, uint32_t R)
+size_t list_smem(uint32_t vwords, uint32_t R)
 {
-    return static_cast<size_t>(ccap) * 12u + 4u * (vwords + static_cast<size_t>(R) * vwords + R) + 16u;
+    return static_cast<size_t>(kKeySlots) * 8u + static_cast<size_t>(kSmallC) * 4u +
+           4u * (vwords + static_cast<size_t>(R) * vwords + R) + 16u;
 }
 
-cudaError_t launch_lists(const LArgs &a, cudaStream_t st)
+template <int DT> cudaError_t launch_small(const LArgs &a, size_t smem, uint32_t grid, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(list_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemMax));
+    if (e != cudaSuccess) return e;
+    list_kernel<DT><<<grid, 32, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <int DT>
+cudaError_t launch_big(const LArgs &a, const uint32_t *jobs, uint32_t nd, const uint64_t *off, uint64_t *region,
+                       size_t smem, cudaStream_t st)
+{
+    cudaError_t e = cudaFuncSetAttribute(big_list_kernel<DT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         static_cast<int>(kSmemMax));
+    if (e != cudaSuccess) return e;
+    big_list_kernel<DT><<<std::min<uint32_t>(nd, 1024u), 1024, smem, st>>>(a, jobs, nd, off, region);
+    return cudaGetLastError();
+}
+
+struct BigScratch {
+    DBuf<uint32_t> defer, ndefer;
+    DBuf<uint64_t> off, region;
+    DBuf<unsigned long long> total;
+};
+
+// Every list of the launch: one warp per list of at most kSmallC candidates,
+// then one CTA per longer list.
+cudaError_t run_lists(LArgs a, BigScratch &bs, cudaStream_t st)
 {
     if (a.njobs == 0) return cudaSuccess;
-    const size_t smem = list_smem(a.ccap, a.vwords, a.R);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e;
+    if ((e = bs.defer.alloc(a.njobs)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bs.ndefer.p, 0, 4, st)) != cudaSuccess) return e;
+    a.defer = bs.defer.p;
+    a.ndefer = bs.ndefer.p;
+    const size_t smem = list_smem(a.vwords, a.R);
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const uint32_t grid = std::min<uint32_t>(a.njobs, static_cast<uint32_t>(sms) * 64u);
-    if (a.dtype == 0) {
-        e = cudaFuncSetAttribute(list_kernel<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e == cudaSuccess) list_kernel<0><<<grid, 32, smem, st>>>(a);
-    } else if (a.dtype == 1) {
-        e = cudaFuncSetAttribute(list_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e == cudaSuccess) list_kernel<1><<<grid, 32, smem, st>>>(a);
-    } else {
-        e = cudaFuncSetAttribute(list_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
-        if (e == cudaSuccess) list_kernel<2><<<grid, 32, smem, st>>>(a);
-    }
-    return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-// Small-job launch, then the deferred (large) lists with a larger sort capacity.
-cudaError_t run_lists(LArgs a, DBuf<uint32_t> &defer, DBuf<uint32_t> &ndefer, cudaStream_t st)
-{
-    if (a.njobs == 0) return cudaSuccess;
-    cudaError_t e = defer.alloc(a.njobs);
+    e = a.dtype == 0 ? launch_small<0>(a, smem, grid, st)
+      : a.dtype == 1 ? launch_small<1>(a, smem, grid, st) : launch_small<2>(a, smem, grid, st);
     if (e != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(ndefer.p, 0, 4, st)) != cudaSuccess) return e;
-    a.ccap = kSmallC;
-    a.defer = defer.p;
-    a.ndefer = ndefer.p;
-    a.job_list = nullptr;
-    if ((e = launch_lists(a, st)) != cudaSuccess) return e;
     uint32_t nd = 0;
-    if ((e = cudaMemcpyAsync(&nd, ndefer.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaMemcpyAsync(&nd, bs.ndefer.p, 4, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
     if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
     if (nd == 0) return cudaSuccess;
-    a.njobs = nd;
-    a.ccap = kLargeC;                    // the largest power of two whose lists fit in shared memory
-    while (a.ccap > kSmallC && list_smem(a.ccap, a.vwords, a.R) > kSmemMax) a.ccap >>= 1;
-    a.defer = nullptr;
-    a.job_list = defer.p;
-    return launch_lists(a, st);
+    if ((e = bs.off.alloc(nd)) != cudaSuccess) return e;
+    if ((e = bs.total.alloc(1)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(bs.total.p, 0, 8, st)) != cudaSuccess) return e;
+    big_regions<<<blocks(nd, 256), 256, 0, st>>>(a, bs.defer.p, nd, bs.off.p, bs.total.p);
+    unsigned long long total = 0;
+    if ((e = cudaMemcpyAsync(&total, bs.total.p, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess) return e;
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+    if ((e = bs.region.alloc(total)) != cudaSuccess) return e;
+    return a.dtype == 0 ? launch_big<0>(a, bs.defer.p, nd, bs.off.p, bs.region.p, smem, st)
+         : a.dtype == 1 ? launch_big<1>(a, bs.defer.p, nd, bs.off.p, bs.region.p, smem, st)
+                        : launch_big<2>(a, bs.defer.p, nd, bs.off.p, bs.region.p, smem, st);
 }
 
 }  // namespace
@@ -670,7 +794,7 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
         return sfail(BANG_EINVAL, "bang_build_shard_graph: iter_cap + R must be at most 512");
     {
         const uint32_t vw = ((d * (dtype == BANG_F32 ? 4u : 1u) + 15u) & ~15u) / 4u;
-        if (list_smem(kSmallC, vw, R) > kSmemMax)
+        if (list_smem(vw, R) > kSmemMax)
             return sfail(BANG_EINVAL, "bang_build_shard_graph: R kept vectors of d dimensions exceed shared memory");
     }
     if (!(alpha >= 1.0f) || !(batch_frac > 0.0f) || !(batch_frac <= 1.0f))
@@ -780,8 +904,8 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
     DBuf<uint32_t> dseq, qbuf, ebuf, tbuf, ibuf, oid, staging, cntv, tpos, touched, tcnt, fill, in_src;
     DBuf<float> odist;
     DBuf<uint64_t> toff, bsum;
-    DBuf<unsigned int> ntouched, err;
-    DBuf<uint32_t> defer, ndefer;
+    DBuf<unsigned int> ntouched;
+    BigScratch bs;
     SG_TRY(dseq.alloc(nv));
     SG_TRY(qbuf.alloc(static_cast<uint64_t>(chunk) * vwords));   // rows of row_bytes <= vwords * 4
     SG_TRY(ebuf.alloc(chunk));
@@ -798,10 +922,8 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
     SG_TRY(toff.alloc(std::min<uint64_t>(nv, static_cast<uint64_t>(max_round) * R)));
     SG_TRY(in_src.alloc(static_cast<uint64_t>(max_round) * R));
     SG_TRY(ntouched.alloc(1));
-    SG_TRY(err.alloc(1));
-    SG_TRY(ndefer.alloc(1));
+    SG_TRY(bs.ndefer.alloc(1));
     SG_TRY(cudaMemsetAsync(cntv.p, 0, sizeof(uint32_t) * nv, st));
-    SG_TRY(cudaMemsetAsync(err.p, 0, 4, st));
 
     bang::SearchArgs sa;
     std::memset(&sa, 0, sizeof sa);
@@ -822,7 +944,6 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
     std::memset(&la, 0, sizeof la);
     la.rec = rec.p; la.recw = rec.p; la.rec_words = rec_words; la.vec_off = R; la.vwords = vwords;
     la.dtype = static_cast<int>(dtype); la.d = d; la.R = R; la.ell = ell;
-    la.err = err.p;
 
     std::vector<uint32_t> seq;
     seq.reserve(nv);
@@ -876,7 +997,7 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
                 la.iters = ibuf.p;
                 la.tcap = iter_cap;
                 la.staging = staging.p + static_cast<uint64_t>(c0) * R;
-                SG_TRY(run_lists(la, defer, ndefer, st));
+                SG_TRY(run_lists(la, bs, st));
             }
             commit_rows<<<blocks(static_cast<uint64_t>(rn) * R, 256), 256, 0, st>>>(mem, rn, staging.p, R, rec.p,
                                                                                  rec_words);
@@ -902,17 +1023,11 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
             la.in_off = toff.p;
             la.in_cnt = tcnt.p;
             la.in_src = in_src.p;
-            SG_TRY(run_lists(la, defer, ndefer, st));
+            SG_TRY(run_lists(la, bs, st));
             rev_reset<<<blocks(nt, 256), 256, 0, st>>>(touched.p, nt, cntv.p);
             SG_TRY(cudaGetLastError());
         }
     }
-    unsigned int herr = 0;
-    SG_TRY(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
-    SG_TRY(cudaStreamSynchronize(st));
-    if (herr)
-        return sfail(BANG_EINVAL, "bang_build_shard_graph: a node gained more reverse edges in one round than "
-                     "its list can sort (up to 16384 candidates); lower batch_frac");
     // free what the merge does not need
     for (auto *b : {&qbuf, &ebuf, &tbuf, &ibuf, &oid, &staging, &cntv, &tpos, &touched, &tcnt, &fill, &in_src, &dseq})
         b->release();
@@ -934,12 +1049,10 @@ extern "C" int bang_build_shard_graph(int device, const void *base, bang_dtype d
         la.p0 = p0;
         la.njobs = static_cast<uint32_t>(pn);
         la.out_rows = adj_dev ? adj + p0 * R : rows.p;
-        SG_TRY(run_lists(la, defer, ndefer, st));
+        SG_TRY(run_lists(la, bs, st));
         if (!adj_dev)
             SG_TRY(cudaMemcpyAsync(adj + p0 * R, rows.p, sizeof(uint32_t) * pn * R, cudaMemcpyDeviceToHost, st));
     }
-    SG_TRY(cudaMemcpyAsync(&herr, err.p, 4, cudaMemcpyDeviceToHost, st));
     SG_TRY(cudaStreamSynchronize(st));
-    if (herr) return sfail(BANG_EINVAL, "bang_build_shard_graph: a merged list exceeded its sort capacity");
     return BANG_OK;
 }

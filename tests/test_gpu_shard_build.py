@@ -38,6 +38,8 @@ CASES = [
     ("f32", 700, 130, 3, 1, 8, 16, 1.0, 0.2, 12),
     ("u8", 997, 20, 1, 1, 16, 32, 1.3, 0.05, 13),
     ("u8", 3000, 16, 2, 2, 128, 32, 1.2, 1.0, 14),     # one pass-2 round of every member
+    ("u8", 6000, 24, 1, 1, 64, 48, 1.2, 1.0, 15),      # hubs with over 750 reverse candidates
+    ("u8", 60000, 128, 16, 2, 64, 64, 1.2, 0.02, 16),  # the large configurations' settings
 ]
 
 

@@ -65,6 +65,7 @@ MUTANTS = [
     ("shard_keeps_repeats", "if (u == 0 || c[i].id != c[u - 1].id) c[u++] = c[i];", "c[u++] = c[i];", 0),
     ("shard_ties_larger_id", "return (a->id < b->id) ? -1 : (a->id > b->id);\n}\n\nstatic float sg_dist",
      "return (a->id > b->id) ? -1 : (a->id < b->id);\n}\n\nstatic float sg_dist", 0),
+    ("shard_no_candidate_cap", "if (u > SG_CAND_CAP) u = SG_CAND_CAP;", "", 0),
     ("exact_mode_keeps_rerank", "if (mode == 1) {                    /* Alg. 1",
      "if (mode == 7) {                    /* Alg. 1", 0),
 ]

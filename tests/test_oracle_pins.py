@@ -931,3 +931,18 @@ def test_shard_graph_invariants():
         assert i not in ids.tolist() and len(set(ids.tolist())) == len(ids)
         dd = ((X[ids].astype(np.int64) - X[i].astype(np.int64)) ** 2).sum(1)
         assert [(int(a), int(b)) for a, b in zip(dd, ids)] == sorted(zip(dd.tolist(), ids.tolist()))
+
+
+def test_shard_graph_candidate_pool_is_cut_to_750():
+    # nothing pruned (alpha huge), R above 750, every point reachable: each
+    # list would hold every other point, but the candidate pool is cut to its
+    # 750 nearest (DiskANN's bound), so every row is exactly those.
+    rng = np.random.default_rng(45)
+    n = 800
+    X = np.unique(rng.integers(0, 256, size=(n + 50, 4)), axis=0)[:n].astype(np.uint8)
+    X = X[rng.permutation(n)]
+    adj, _ = oracle.shard_graph(X, X[:1].astype(np.float32), 1, 790, 1024, 1e6, 0.5, 18,
+                                iter_cap=1000)
+    for i in range(0, n, 37):
+        want = _sorted_others(X, i, np.arange(n))[:750]
+        assert adj[i, :750].tolist() == want and (adj[i, 750:] == NONE).all()

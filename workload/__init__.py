@@ -23,6 +23,12 @@ Configurations (the recipe of each is in ``CONFIGS``):
      low-rank components as in 2 (A: d x 12 with N(0, 16^2/12) entries, noise
      4), rounded and clipped to -128..127; 10,000 queries; PQ M=50; clustered
      graph R=64 (built on the GPU: the host cores would take days).
+  5  n=200,000,000 u8 d=128 (the largest size the GPU machine's host memory holds
+     with room for the index; the configuration names 1B), 16,384 low-rank
+     components as in 2; 10,000 queries; PQ M=32; overlapping-shard graph R=64.
+Configurations 4 and 5 come from the counter-based generator (large_data)
+and take the overlapping-shard graph (32 shards, each point in its 2 nearest,
+GreedySearch worklist 64, alpha 1.2) built on the GPU.
 Seeds: data 1000+cfg, queries 2000+cfg, PQ 3000+cfg, graph 4000+cfg.
 """
 import ctypes
@@ -54,7 +60,14 @@ CONFIGS = {
     # clusters and half to random ones
     4: dict(n=100_000_000, nq=10_000, d=100, dtype="i8", ncomp=4096, centre="uniform100",
             centre_scale=None, sigma=16.0, rank=12, noise=4.0, M=50, R=64, alpha=1.2, nx=4,
-            nh=32, k=10, L=128, links="mixed"),
+            nh=32, k=10, L=128, links="mixed", shards=32, ell=2, Lb=64, batch_frac=0.02,
+            bloom_build=16),
+    # serving at the largest size the GPU machine's host memory holds with room
+    # for the index (200M of the 1B points; SIFT's type and dimension),
+    # overlapping-shard graph (§2.2), built on the GPU
+    5: dict(n=200_000_000, nq=10_000, d=128, dtype="u8", ncomp=16384, centre="uniform255",
+            centre_scale=None, sigma=20.0, rank=12, noise=4.0, M=32, R=64, alpha=1.2, k=10,
+            L=64, shards=32, ell=2, Lb=64, batch_frac=0.02, bloom_build=16),
 }
 
 _DTN = {"u8": np.uint8, "i8": np.int8, "f32": np.float32}
@@ -88,6 +101,8 @@ def lib():
         L.wl_cluster_graph.restype = i32
         L.wl_bruteforce.argtypes = [vp, vp, i32, u64, u32, u32, u32, vp, vp]
         L.wl_max_threads.restype = i32
+        L.wl_mixture.argtypes = [vp, i32, u64, u32, vp, u32, vp, u32, f32, u64, vp]
+        L.wl_mixture.restype = i32
         L.wl_scale_index.argtypes = [i32, u64, u32, u32, u32, u32, u32, u32, u64, vp, vp, vp, vp, vp]
         L.wl_scale_index.restype = i32
         _lib = L
@@ -352,6 +367,51 @@ def clustered_data(cfg=2, n=None, nq=None, ncomp=None, k=100, train_n=256_000, v
     out["medoid"] = int(gmed[0])
     out["params"] = dict(c, n=n, nq=nq, ncomp=ncomp)
     return out
+
+
+def large_data(cfg, n=None, nq=None, ncomp=None, train_n=256_000, verbose=False, **over):
+    """Data of a large configuration (4 or 5) from the counter-based generator
+    (wl_mixture: same bytes for any thread count and on x86 and Arm hosts),
+    with the inputs of its index build: the PQ training sample and initial
+    centroids, the shard centres (seeded data points) and the global medoid.
+    The index itself (PQ codes, overlapping-shard graph) and the ground truth
+    are built by the caller (on the GPU)."""
+    c = dict(CONFIGS[cfg])
+    c.update(over)
+    n = n or c["n"]
+    nq = nq or c["nq"]
+    ncomp = ncomp or c["ncomp"]
+    c.update(n=n, nq=nq, ncomp=ncomp)
+    t0 = time.time()
+    rng = np.random.default_rng(1000 + cfg)
+    cen = np.ascontiguousarray(_centres(rng, c), np.float32)
+    fac = rng.standard_normal((ncomp, c["d"], c["rank"]), dtype=np.float32) * np.float32(
+        c["sigma"] / np.sqrt(c["rank"]))
+    fac = np.ascontiguousarray(fac.transpose(0, 2, 1))         # rank-major per component
+    base = aligned_empty((n, c["d"]), _DTN[c["dtype"]])
+    queries = aligned_empty((nq, c["d"]), _DTN[c["dtype"]])
+    for arr, rows, seed in ((base, n, 1000 + cfg), (queries, nq, 2000 + cfg)):
+        rc = lib().wl_mixture(_p(arr), _DTC[c["dtype"]], rows, c["d"], _p(cen), ncomp, _p(fac),
+                              c["rank"], c["noise"], seed, None)
+        if rc != 0:
+            raise ValueError("wl_mixture rejected its arguments")
+    t1 = time.time()
+    sample, init = pq_random_choices(cfg, n, c["M"], train_n)
+    srng = np.random.default_rng(4000 + cfg)
+    shard_ids = np.sort(srng.choice(n, size=c["shards"], replace=False))
+    out = np.zeros(1, np.uint32)
+    everyone = np.arange(n, dtype=np.uint32)
+    bounds = np.array([0, n], np.uint64)
+    lib().wl_medoids(_p(base), _DTC[c["dtype"]], c["d"], _p(everyone), _p(bounds), 1, _p(out))
+    del everyone
+    t2 = time.time()
+    if verbose:
+        print("data cfg%d n=%d: generator %.1fs, build inputs and medoid %.1fs (threads %d)" % (
+            cfg, n, t1 - t0, t2 - t1, lib().wl_max_threads()), flush=True)
+    return dict(base=base, queries=queries, pq_sample=sample,
+                pq_init=sample[init.astype(np.int64)],
+                shard_centres=np.ascontiguousarray(base[shard_ids], np.float32),
+                medoid=int(out[0]), params=c)
 
 
 def cache_dir():

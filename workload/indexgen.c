@@ -525,6 +525,60 @@ int wl_scale_index(int dt, uint64_t n, uint32_t d, uint32_t M, uint32_t R, uint3
     return 0;
 }
 
+/* ---------------------------------------------------------------------- */
+/* Equal-weight Gaussian mixture with low-rank components, counter-based so */
+/* that any thread count writes the same bytes (the large configurations): */
+/* point i takes component c_i = h(seed, i, 0) mod ncomp and               */
+/*   x = centre[c_i] + A[c_i] z + noise * e,  z ~ N(0, I_rank), e ~ N(0, I_d) */
+/* (A[c] stored rank-major, d values per rank; x_j summed over the rank in  */
+/* ascending order)                                                          */
+/* with every normal drawn as the sum of twelve uniforms minus 6 (Irwin-    */
+/* Hall: mean 0, variance 1; the uniforms are 16-bit pieces of SplitMix64   */
+/* counters, so every sum is exact in FP32 and no libm call is made: x86   */
+/* and Arm hosts write the same bytes); the sum over the rank in ascending  */
+/* order in FP32 (no fused multiply-add); integers rounded half to even and */
+/* clipped to the element range.                                            */
+/* ---------------------------------------------------------------------- */
+
+static inline float wl_normal(uint64_t seed, uint64_t i, uint64_t k)
+{
+    float s = 0.0f;
+    int t, q;
+    for (t = 0; t < 3; t++) {
+        uint64_t h = wl_mix((seed << 48) ^ (i * 0x100000001B3ull + k * 3 + (uint64_t)t + 1));
+        for (q = 0; q < 4; q++) s = s + ((float)((h >> (16 * q)) & 0xFFFFu) + 0.5f) / 65536.0f;
+    }
+    return s - 6.0f;
+}
+
+int wl_mixture(void *X, int dt, uint64_t n, uint32_t d, const float *centres, uint32_t ncomp,
+               const float *factors, uint32_t rank, float noise, uint64_t seed, uint32_t *labels)
+{
+    int64_t i;
+    if (rank > 64 || ncomp == 0 || d > 512) return -1;
+#pragma omp parallel for schedule(static)
+    for (i = 0; i < (int64_t)n; i++) {
+        float z[64], x[512], e[512];
+        uint32_t c = (uint32_t)(wl_mix((seed << 48) ^ ((uint64_t)i * 0x100000001B3ull)) % ncomp), r, j;
+        const float *cen = centres + (uint64_t)c * d, *A = factors + (uint64_t)c * d * rank;
+        for (r = 0; r < rank; r++) z[r] = wl_normal(seed, (uint64_t)i, r);
+        for (j = 0; j < d; j++) e[j] = wl_normal(seed, (uint64_t)i, 64 + j);
+        for (j = 0; j < d; j++) x[j] = cen[j];
+        for (r = 0; r < rank; r++)              /* factors stored rank-major: A[r][j] */
+            for (j = 0; j < d; j++) x[j] = x[j] + A[(uint64_t)r * d + j] * z[r];
+        for (j = 0; j < d; j++) {
+            float v;
+            x[j] = x[j] + noise * e[j];
+            v = rintf(x[j]);
+            if (dt == WL_U8) ((uint8_t *)X)[(uint64_t)i * d + j] = (uint8_t)(v < 0.f ? 0.f : v > 255.f ? 255.f : v);
+            else if (dt == WL_I8) ((int8_t *)X)[(uint64_t)i * d + j] = (int8_t)(v < -128.f ? -128.f : v > 127.f ? 127.f : v);
+            else ((float *)X)[(uint64_t)i * d + j] = x[j];
+        }
+        if (labels) labels[i] = c;
+    }
+    return 0;
+}
+
 int wl_max_threads(void)
 {
 #ifdef _OPENMP
