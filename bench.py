@@ -44,6 +44,10 @@ L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024)
 TARGET_RECALL = 0.9
 K = 10                      # k of the search and of recall@k (--k)
 def workload_name(args):
+    if args.config == 5:
+        return ("serving at the largest size the host holds: n=%d u8 d=128, 16384 low-rank "
+                "components, %d queries, PQ M=32, overlapping-shard Vamana graph R=64, k=%d"
+                % (args.n or 200_000_000, args.nq or 10_000, K))
     if args.config == 4:
         return ("batched form: n=%d int8 d=100, 4096 components, %d queries, PQ M=%d, R=64, k=%d"
                 % (args.n or 100_000_000, args.nq or 10_000, args.M or 50, K))
@@ -84,9 +88,10 @@ def parse():
     ap.add_argument("--records", action="store_true",
                     help="fixed host forms read each node's row and vector as one record "
                          "(BANG_NODE_RECORDS)")
-    ap.add_argument("--config", type=int, default=2, choices=(2, 3, 4),
-                    help="2: mid-scale u8 (the headline); 3: the precision form (f32 d=96); "
-                         "4: the batched form (100M int8, d=100; needs --gpu-build)")
+    ap.add_argument("--config", type=int, default=5, choices=(2, 3, 4, 5),
+                    help="5: serving at the largest size the host holds (200M u8, the headline); "
+                         "2: mid-scale u8 (1M); 3: the precision form (f32 d=96); 4: the batched "
+                         "form (100M int8, d=100)")
     args = ap.parse_args()
     global K
     K = args.k
@@ -318,7 +323,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     import workload  # noqa: F401
-    w = load_workload(args, 0, 1, lambda: None)
+    if args.config in (4, 5):       # the index (input to the timed search) is built on the GPU
+        w = large_workload(args, int(os.environ.get("LOCAL_RANK", "0")))
+    else:
+        w = load_workload(args, 0, 1, lambda: None)
     import oracle
     ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], w["codes"].shape[1])
     nq = w["queries"].shape[0]
@@ -375,10 +383,369 @@ FORMS = {
 }
 
 
+def large_workload(args, device):
+    """Configurations 4 and 5: data from the counter-based generator; PQ
+    codebook and codes, the overlapping-shard graph (§2.2) and the exact
+    100 nearest neighbours of every query built on the GPU; 16 sampled ground
+    truth rows checked against the oracle's brute force."""
+    import workload
+    import paper_2401_11324_gb300 as bang
+    w = workload.large_data(args.config, n=args.n, nq=args.nq, ncomp=args.ncomp, verbose=True)
+    c = w["params"]
+    n = w["base"].shape[0]
+    t0 = time.perf_counter()
+    cb, codes = bang.bang_build_pq(w["base"], c["M"], w["pq_sample"],
+                                   w["pq_init"].reshape(c["M"], 256), 10, device=device)
+    t1 = time.perf_counter()
+    adj = workload.aligned_empty((n, c["R"]), np.uint32)          # read in place later
+    bang.bang_build_shard_graph(w["base"], w["shard_centres"], c["ell"], c["R"], c["Lb"], c["alpha"],
+                                c["batch_frac"], c["bloom_build"], adj=adj, device=device)
+    t2 = time.perf_counter()
+    gt_ids, gt_dist = bang.bang_ground_truth(w["base"], w["queries"], 100, device=device)
+    t3 = time.perf_counter()
+    import oracle
+    sel = np.linspace(0, w["queries"].shape[0] - 1, 16).astype(np.int64)
+    ids_o, dist_o = oracle.bruteforce_knn(w["base"], w["queries"][sel], 100)
+    if not ((ids_o == gt_ids[sel]).all() and (dist_o == gt_dist[sel]).all()):
+        raise RuntimeError("GPU ground truth differs from the oracle's brute force")
+    deg = (adj != 0xFFFFFFFF).sum(1)
+    w.update(codebook=cb, codes=codes, adj=adj, gt_ids=gt_ids, gt_dist=gt_dist,
+             index_build={"where": "GPU: bang_build_pq, bang_build_shard_graph (%d shards, each point "
+                                   "in its %d nearest, GreedySearch worklist %d, alpha %.1f, batch "
+                                   "fraction %.2f), bang_ground_truth" % (
+                                       c["shards"], c["ell"], c["Lb"], c["alpha"], c["batch_frac"]),
+                          "pq_s": round(t1 - t0, 1), "graph_s": round(t2 - t1, 1),
+                          "ground_truth_s": round(t3 - t2, 1),
+                          "mean_degree": round(float(deg.mean()), 2), "max_degree": int(deg.max())},
+             truth="GPU (bang_ground_truth); 16 sampled queries equal to the oracle's brute force")
+    return w
+
+
+# Forms of the large configurations: (name, distance mode, placement, Bloom
+# log2, what).  Results do not depend on the placement (tested), so every
+# operating point is found with graph and vectors in HBM.
+LARGE_FORMS = [
+    ("fp32_hbm", 0, 3, 16, "FP32 PQ table (the paper's precision), graph and vectors in HBM (the "
+                           "In-memory variant, §5.1)"),
+    ("bf16_hbm", 1, 3, 16, "BF16 PQ table (reduced precision) summed in FP32, graph and vectors in HBM"),
+    ("q8_hbm", 3, 3, 15, "8-bit PQ table (reduced precision) summed in integers, graph and vectors "
+                         "in HBM"),
+    ("exact_hbm", 2, 3, 16, "Exact-distance variant (§5.2): exact distances in the loop, no table "
+                            "and no re-rank, graph and vectors in HBM"),
+]
+
+
+def run_large(args):
+    import torch
+    import torch.distributed as dist
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    import paper_2401_11324_gb300 as bang
+    w = large_workload(args, local)
+    barrier()
+    c = w["params"]
+    nq, d = w["queries"].shape
+    n = w["base"].shape[0]
+    M, R = w["codes"].shape[1], w["adj"].shape[1]
+    esz = w["base"].dtype.itemsize
+    ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M, device=local)
+    stream = torch.cuda.Stream(device=dev)
+    sptr = stream.cuda_stream
+    q_dev = torch.from_numpy(w["queries"]).to(dev)
+    ids = torch.empty((nq, K), dtype=torch.int32, device=dev)
+    dout = torch.empty((nq, K), dtype=torch.float32, device=dev)
+    iters = torch.empty(nq, dtype=torch.int32, device=dev)
+    ndist = torch.empty(nq, dtype=torch.int32, device=dev)
+    flush = torch.empty(512 * 1024 * 1024, dtype=torch.uint8, device=dev)
+    placement = [None]
+
+    def place(flags):
+        if placement[0] != flags:
+            ix.set_placement(flags)
+            placement[0] = flags
+
+    def search(L, mode, lz, nsub=None, stats=False):
+        p = bang.make_params(bloom_log2=lz, mode=mode, out_iters=iters if stats else None,
+                             out_ndist=ndist if stats else None)
+        m = nsub or nq
+        ix.search(q_dev[:m], K, L, ids[:m], dout[:m], p, stream=sptr)
+
+    def rec_now(m=None):
+        m = m or nq
+        return recall(ids[:m].cpu().numpy().view(np.uint32), w["gt_ids"][:m])
+
+    def operating_point(mode, lz):
+        sweep = []
+        if args.L is not None:
+            return args.L, sweep
+        for Lc in sweep_values():
+            search(Lc, mode, lz)
+            stream.synchronize()
+            rc = rec_now()
+            sweep.append({"L": Lc, "recall@%d" % K: round(rc, 4)})
+            if rc >= TARGET_RECALL:
+                return Lc, sweep
+        return sweep_values()[-1], sweep
+
+    def timed(L, mode, lz, steps, nsub=None):
+        for _ in range(args.warmup):
+            search(L, mode, lz, nsub)
+        stream.synchronize()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        barrier()
+        torch.cuda.synchronize(dev)
+        t_wall = time.perf_counter()
+        for a_, b_ in evs:
+            with torch.cuda.stream(stream):
+                flush.fill_(3)
+                a_.record(stream)
+            search(L, mode, lz, nsub)
+            b_.record(stream)
+        stream.synchronize()
+        t_wall = time.perf_counter() - t_wall
+        torch.cuda.synchronize(dev)
+        barrier()
+        ms = [a_.elapsed_time(b_) for a_, b_ in evs]
+        _, total_ms = job_throughput(nsub or nq, steps, sum(ms), world, dist, dev)
+        return (nsub or nq) * world * steps / (total_ms / 1e3), total_ms / steps, t_wall
+
+    res = {}
+    with ClockSampler(local) as clk:
+        for name, mode, pl, lz, what in LARGE_FORMS:
+            place(pl)
+            L, sweep = operating_point(mode, lz)
+            search(L, mode, lz, stats=True)
+            stream.synchronize()
+            r = rec_now()
+            derr = dist_error(ids.cpu().numpy().view(np.uint32), dout.cpu().numpy(), w["base"],
+                              w["queries"])
+            it = iters.cpu().numpy().astype(np.int64)
+            nd = ndist.cpu().numpy().astype(np.int64)
+            value, ms, t_wall = timed(L, mode, lz, args.steps)
+            res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, L=L, sweep=sweep,
+                             recall=round(r, 4), dist_error=derr, iters=it, ndist=nd, value=value,
+                             ms_per_step=ms, t_wall=t_wall)
+    # the paper's placement (graph and vectors read in place from page-locked
+    # host memory), and the vectors alone in HBM, each at the FP32 form's
+    # operating point, on a bounded sample of the batch (the same results)
+    fp = res["fp32_hbm"]
+    host = {}
+    for name, pl, what in (("fp32_host", 0, "FP32 PQ table, graph and vectors read in place from "
+                                           "page-locked host memory (the paper's placement, Alg. 2)"),
+                           ("fp32_vectors_hbm", 2 | 4, "FP32 PQ table, vectors in HBM, graph rows "
+                                                       "(packed ids) read in place from host memory")):
+        place(pl)
+        m = min(nq, 1000)
+        t0 = time.perf_counter()
+        search(fp["L"], 0, fp["lz"], nsub=200)
+        stream.synchronize()
+        est = 200 / max(1e-6, time.perf_counter() - t0)
+        m = int(min(nq, max(200, min(1000, est * 2.0))))      # about two seconds per step
+        value, ms, _ = timed(fp["L"], 0, fp["lz"], 2, nsub=m)
+        host[name] = dict(what=what, value=value, ms_per_step=ms, L=fp["L"], queries=m,
+                          placement=pl)
+    place(3)
+
+    # autotuned settings (table precision, Bloom size, L) for recall@10 >= 0.9 in HBM
+    t0 = time.perf_counter()
+    try:
+        tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
+                           target_recall=TARGET_RECALL, bloom_min=14, bloom_max=17, stream=sptr)
+        tune["seconds"] = round(time.perf_counter() - t0, 2)
+        search(tune["L"], tune["mode"], tune["bloom_log2"])
+        stream.synchronize()
+        tune_rec = rec_now()
+        tv, tms, _ = timed(tune["L"], tune["mode"], tune["bloom_log2"], args.steps)
+        tuned = dict(value=tv, ms_per_step=tms, L=tune["L"], mode=tune["mode"],
+                     bloom_log2=tune["bloom_log2"], recall=round(tune_rec, 4),
+                     seconds=tune["seconds"], candidates=tune["candidates"])
+    except bang.BangError as e:
+        tuned = {"failed": str(e)}
+
+    # batched form: per-query k in {1, 10, 100} and L in {32, ..., 256} (at
+    # least k), one persistent launch replayed from a CUDA graph
+    q8 = res["q8_hbm"]
+    rng = np.random.default_rng(44)
+    kq = rng.choice([1, 10, 100], size=nq).astype(np.uint32)
+    Lq = np.maximum(rng.choice([64, 128, 192, 256], size=nq), kq).astype(np.uint32)
+    kd = torch.from_numpy(kq.view(np.int32)).to(dev)
+    Ld = torch.from_numpy(Lq.view(np.int32)).to(dev)
+    bids = torch.empty((nq, 100), dtype=torch.int32, device=dev)
+    bdist = torch.empty((nq, 100), dtype=torch.float32, device=dev)
+    bp = bang.make_params(bloom_log2=q8["lz"], mode=q8["mode"])
+    ix.search_batched(q_dev, kd, Ld, 100, 256, bids, bdist, bp, stream=sptr)
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        ix.search_batched(q_dev, kd, Ld, 100, 256, bids, bdist, bp, stream=sptr)
+    for _ in range(args.warmup):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(max(3, min(args.steps, 10)))]
+    for a_, b_ in evs:
+        with torch.cuda.stream(stream):
+            flush.fill_(3)
+            a_.record(stream)
+            graph.replay()
+            b_.record(stream)
+    stream.synchronize()
+    bms = statistics.mean(a_.elapsed_time(b_) for a_, b_ in evs)
+    got = bids.cpu().numpy().view(np.uint32)
+    brec = {}
+    for kk in (1, 10, 100):
+        sel = np.where(kq == kk)[0]
+        brec["recall@%d" % kk] = round(recall(got[sel, :kk], w["gt_ids"][sel], kk), 4)
+    batched = {"value": nq / (bms / 1e3), "unit": "queries/s", "ms_per_step": bms,
+               "launch": "one persistent launch (bang_search_batched) replayed from a CUDA graph, "
+                         "8-bit table, graph and vectors in HBM",
+               "k_mix": "uniform over {1, 10, 100}", "L_mix": "uniform over {64, 128, 192, 256}, "
+               "at least k", **brec}
+    del graph
+
+    # the headline: the fastest FP32-table form reaching the target recall
+    head = fp
+    it, nd = head["iters"], head["ndist"]
+    launch_s = head["ms_per_step"] / 1e3
+    # end to end through the C ABI: pinned host queries and results
+    q_host = torch.from_numpy(w["queries"]).pin_memory()
+    ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
+    dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
+    hp = bang.make_params(bloom_log2=head["lz"], mode=head["mode"])
+    for _ in range(2):
+        ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
+    e2e_steps = max(3, min(args.steps, 10))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
+    e2e_s = (time.perf_counter() - t0) / e2e_steps
+    search(head["L"], head["mode"], head["lz"])
+    stream.synchronize()
+    assert (ids_h.numpy() == ids.cpu().numpy()).all()
+
+    # serving: continuous batching with the 8-bit table in HBM
+    serving_rec = None
+    if not args.no_serving:
+        serving_rec = serving(bang, ix, w, q8["L"], q8["mode"], q8["value"], q8["lz"])
+
+    # rooflines: HBM binds the headline (graph, vectors and codes in HBM);
+    # per expansion the row (R ids), the vector and one code row per new
+    # neighbour (M bytes; nd counts them)
+    row_bytes = R * 4
+    hbm_bytes = int(it.sum()) * (row_bytes + d * esz) + int(nd.sum()) * M + nq * d * esz + nq * K * 8
+    peaks = measured_peaks()
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    hbm_gbs = hbm_bytes / launch_s / 1e9
+    link = bang.bang_probe_host_link(local, 1 << 30, row_bytes)
+    foot = int(min(n * (row_bytes + d * esz), 32 << 30))
+    link_far = bang.bang_probe_host_link(local, foot, row_bytes)
+    hf = host["fp32_host"]
+    host_bytes_q = float(it.mean()) * (row_bytes + d * esz)
+    host_gbs = hf["value"] * host_bytes_q / 1e9
+
+    def brief(r):
+        return {"what": r["what"], "value": r["value"], "ms_per_step": r["ms_per_step"],
+                "L": r["L"], "recall@%d" % K: r["recall"], "sweep": r["sweep"],
+                "mean_iterations": float(r["iters"].mean()),
+                "dist_error_vs_fp64": r["dist_error"]}
+
+    served = None
+    if serving_rec is not None:
+        top = serving_rec["points"][-1]
+        served = {"what": "continuous batching (bang_server_*), 8-bit table, graph and vectors in "
+                          "HBM, L=%d, recall@%d %.4f" % (q8["L"], K, q8["recall"]),
+                  "achieved_qps": top["achieved_qps"], "p50_ms": top["p50_ms"], "p99_ms": top["p99_ms"],
+                  "offered_qps": top["offered_qps"],
+                  "vs_plain_form": top["achieved_qps"] / hf["value"],
+                  "vs_fp32_hbm": top["achieved_qps"] / fp["value"]}
+    summary = {
+        "plain_form": {"value": hf["value"], "L": fp["L"], "recall@%d" % K: fp["recall"],
+                       "what": "FP32 table, graph and vectors in page-locked host memory"},
+        "fp32_hbm": {"value": fp["value"], "L": fp["L"], "recall@%d" % K: fp["recall"]},
+        "bf16_hbm": {"value": res["bf16_hbm"]["value"], "L": res["bf16_hbm"]["L"],
+                     "recall@%d" % K: res["bf16_hbm"]["recall"]},
+        "q8_hbm": {"value": q8["value"], "L": q8["L"], "recall@%d" % K: q8["recall"]},
+        "exact_hbm": {"value": res["exact_hbm"]["value"], "L": res["exact_hbm"]["L"],
+                      "recall@%d" % K: res["exact_hbm"]["recall"]},
+        "served": None if served is None else {k_: served[k_] for k_ in (
+            "achieved_qps", "p50_ms", "p99_ms", "vs_plain_form")},
+        "batched": {"value": batched["value"], "recall@10": batched["recall@10"]},
+        "precision": {"recall@10": {f: res[f]["recall"] for f in ("fp32_hbm", "bf16_hbm", "q8_hbm")},
+                      "L": {f: res[f]["L"] for f in ("fp32_hbm", "bf16_hbm", "q8_hbm")},
+                      "max_rel_dist_error_vs_fp64": max(res[f]["dist_error"]["max_rel"]
+                                                        for f in ("fp32_hbm", "bf16_hbm", "q8_hbm"))},
+    }
+    line = {
+        "metric": metric_name(), "value": head["value"], "unit": "queries/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": head["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": workload_name(args), "form": head["form"], "form_what": head["what"],
+                   "L": head["L"], "recall@%d" % K: head["recall"], "k": K, "bloom_log2": head["lz"],
+                   "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
+                   "n": n, "nq": nq, "parallelism": "replica per GPU" if world > 1 else "single GPU",
+                   "l2": "512 MB flush written between timed steps; the index (77 GB) is larger "
+                         "than L2",
+                   "index_build": w["index_build"], "ground_truth": w["truth"],
+                   "summary": summary},
+        "forms": {f: brief(r) for f, r in res.items()},
+        "host_forms": host,
+        "autotuned": tuned,
+        "batched_form": batched,
+        "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": hbm_gbs / hbm_peak, "traffic": None,
+                     "traffic_note": "no ncu capture of this kernel at this size yet",
+                     "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks
+                                    else "fallback",
+                     "algorithmic_bytes_per_launch": hbm_bytes,
+                     "per_unit": "%d B per expansion (row %d B + vector %d B) + %d B per PQ distance"
+                                 % (row_bytes + d * esz, row_bytes, d * esz, M),
+                     "units_per_launch": int(it.sum())},
+        "host_link": {"plain_form_gbs": host_gbs, "gather_gbs_1GiB": link["gather_gbs"],
+                      "gather_gbs_index_footprint": link_far["gather_gbs"],
+                      "footprint_bytes": foot, "copy_engine_gbs": link["h2d_copy_gbs"],
+                      "host_threads_gather_gbs": link["cpu_gather_gbs"],
+                      "load_latency_ns": link["latency_ns"],
+                      "load_latency_ns_index_footprint": link_far["latency_ns"],
+                      "note": "random %d-byte row gathers in place from page-locked host memory: "
+                              "the GPU reaches 1 GiB at full speed and the index's footprint far "
+                              "slower, which is why the headline keeps graph and vectors in HBM"
+                              % row_bytes},
+        "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d * esz,
+                "d2h_bytes_per_step": nq * K * 8},
+        "gpu_launches": args.steps,
+        "clocks": clk.summary(),
+        "wall_s_timed_region": sum(r["t_wall"] for r in res.values()),
+    }
+    if serving_rec is not None:
+        line["serving"] = serving_rec
+        line["served_form"] = served
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, fp["L"], min(args.cpu_sample, nq), 16)
+    line["plain_form"] = summary["plain_form"]
+    ix.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
+    if args.config in (4, 5):
+        return run_large(args)
     import torch
     import torch.distributed as dist
 
