@@ -534,6 +534,24 @@ def run_large(args):
             res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, L=L, sweep=sweep,
                              recall=round(r, 4), dist_error=derr, iters=it, ndist=nd, value=value,
                              ms_per_step=ms, t_wall=t_wall)
+    # sampled queries of the FP32, 8-bit and Exact-distance forms at their
+    # operating points, bit for bit against the oracle on the same index
+    import oracle
+    oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
+    sel = np.linspace(0, nq - 1, 16).astype(np.int64)
+    parity = {}
+    for name, okw in (("fp32_hbm", {}), ("q8_hbm", {"q8": True}), ("exact_hbm", {"exact": True})):
+        r = res[name]
+        search(r["L"], r["mode"], r["lz"], stats=True)
+        stream.synchronize()
+        o = oix.search(w["queries"][sel], K, r["L"], log2z=r["lz"], **okw)
+        gi = ids.cpu().numpy().view(np.uint32)[sel]
+        gd = dout.cpu().numpy()[sel]
+        git = iters.cpu().numpy().view(np.uint32)[sel]
+        parity[name] = bool((gi == o["ids"]).all() and (git == o["iters"]).all() and
+                            np.array_equal(gd, o["dist"]))
+    del oix
+
     # the paper's placement (graph and vectors read in place from page-locked
     # host memory), and the vectors alone in HBM, each at the FP32 form's
     # operating point, on a bounded sample of the batch (the same results)
@@ -696,6 +714,8 @@ def run_large(args):
                    "l2": "512 MB flush written between timed steps; the index (77 GB) is larger "
                          "than L2",
                    "index_build": w["index_build"], "ground_truth": w["truth"],
+                   "parity": {"what": "16 sampled queries: ids, distances and iteration counts "
+                                      "equal to the oracle's on this index", **parity},
                    "summary": summary},
         "forms": {f: brief(r) for f, r in res.items()},
         "host_forms": host,

@@ -12,8 +12,11 @@ on sampled queries (the oracle computes those one by one):
       largest size that does, 200M u8, d=128, M=32, R=64): the serving loop.
 
 Configurations 3-5 use indexes from workload.scale_index (cluster-local rows,
-uniform data) because building their clustered graphs on the host cores takes
-hours; the search does the same work on any graph.  Each test checks the
+uniform data) because building their graphs on the host cores takes hours; the
+search does the same work on any graph.  The large configurations' own
+pipeline (counter-based data, PQ and overlapping-shard graph built on the GPU)
+is checked end to end at 4M points, and the benchmark itself compares 16
+sampled queries with the oracle on the full 200M-point index.  Each test checks the
 memory it needs first and is skipped when the machine lacks it."""
 import gc
 import os
@@ -182,4 +185,45 @@ def test_configuration5_shape_serving():
         assert (ids == o["ids"]).all()
         assert (dist == o["dist"]).all()
     del w, oix
+    gc.collect()
+
+
+def test_overlapping_shard_index_end_to_end():
+    """The large configurations' pipeline at 4M points (configuration 5's
+    recipe): data from the counter-based generator, PQ and the
+    overlapping-shard graph built on the GPU; the rows are sorted by exact
+    distance without repeats; searches in the FP32, 8-bit and Exact-distance
+    modes, with the index in host memory and in HBM, are bit-exact with the
+    oracle on sampled queries; and recall@10 reaches 0.9 at L = 128."""
+    _need(3)
+    w = workload.large_data(5, n=4_000_000, nq=1000)
+    c = w["params"]
+    cb, codes = bang.bang_build_pq(w["base"], c["M"], w["pq_sample"], w["pq_init"].reshape(c["M"], 256), 10)
+    adj = workload.aligned_empty((w["base"].shape[0], c["R"]), np.uint32)
+    bang.bang_build_shard_graph(w["base"], w["shard_centres"], c["ell"], c["R"], c["Lb"], c["alpha"],
+                                c["batch_frac"], c["bloom_build"], adj=adj)
+    X = w["base"]
+    for i in np.linspace(0, X.shape[0] - 1, 200).astype(np.int64):
+        row = adj[i][adj[i] != oracle.NONE].astype(np.int64)
+        assert 1 <= len(row) and i not in row.tolist() and len(set(row.tolist())) == len(row)
+        dd = ((X[row].astype(np.int64) - X[i].astype(np.int64)) ** 2).sum(1)
+        assert list(zip(dd.tolist(), row.tolist())) == sorted(zip(dd.tolist(), row.tolist()))
+    gt, _ = bang.bang_ground_truth(X, w["queries"], 10)
+    ix = bang.Index(X, cb, codes, adj, w["medoid"], c["M"])
+    oix = oracle.Index(X, cb, codes, adj, w["medoid"], c["M"])
+    q = torch.from_numpy(np.ascontiguousarray(w["queries"])).cuda()
+    sel = np.arange(0, 1000, 25)
+    for place in (0, 3):
+        ix.set_placement(place)
+        for mode, lz, L in ((0, 16, 128), (3, 15, 128), (2, 16, 32)):
+            g = _run(ix, q, 10, L, mode, lz, trace_cap=512)
+            o = oix.search(w["queries"][sel], 10, L, log2z=lz, trace_cap=512, exact=mode == 2,
+                           q8=mode == 3)
+            _compare(g, o, sel, 512)
+            if mode == 0:
+                f = g["ids"].astype(np.int64)
+                rec = (f[:, :, None] == gt[:, None, :].astype(np.int64)).any(-1).mean()
+                assert rec >= 0.9, rec
+    ix.close()
+    del w, oix, adj
     gc.collect()
