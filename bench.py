@@ -424,14 +424,18 @@ def large_workload(args, device):
 # Forms of the large configurations: (name, distance mode, placement, Bloom
 # log2, what).  Results do not depend on the placement (tested), so every
 # operating point is found with graph and vectors in HBM.
+# early: request every neighbour's code row as soon as the node's row arrives
+# (early_codes; same results; measured faster with the FP32 and BF16 tables,
+# slower with the 8-bit table).
 LARGE_FORMS = [
-    ("fp32_hbm", 0, 3, 16, "FP32 PQ table (the paper's precision), graph and vectors in HBM (the "
-                           "In-memory variant, §5.1)"),
-    ("bf16_hbm", 1, 3, 16, "BF16 PQ table (reduced precision) summed in FP32, graph and vectors in HBM"),
-    ("q8_hbm", 3, 3, 15, "8-bit PQ table (reduced precision) summed in integers, graph and vectors "
-                         "in HBM"),
-    ("exact_hbm", 2, 3, 16, "Exact-distance variant (§5.2): exact distances in the loop, no table "
-                            "and no re-rank, graph and vectors in HBM"),
+    ("fp32_hbm", 0, 3, 16, 1, "FP32 PQ table (the paper's precision), graph and vectors in HBM (the "
+                              "In-memory variant, §5.1)"),
+    ("bf16_hbm", 1, 3, 16, 1, "BF16 PQ table (reduced precision) summed in FP32, graph and vectors in "
+                              "HBM"),
+    ("q8_hbm", 3, 3, 15, 0, "8-bit PQ table (reduced precision) summed in integers, graph and vectors "
+                            "in HBM"),
+    ("exact_hbm", 2, 3, 16, 0, "Exact-distance variant (§5.2): exact distances in the loop, no table "
+                               "and no re-rank, graph and vectors in HBM"),
 ]
 
 
@@ -472,9 +476,11 @@ def run_large(args):
             ix.set_placement(flags)
             placement[0] = flags
 
+    early = [0]                     # early_codes of the form being measured
+
     def search(L, mode, lz, nsub=None, stats=False):
         p = bang.make_params(bloom_log2=lz, mode=mode, out_iters=iters if stats else None,
-                             out_ndist=ndist if stats else None)
+                             out_ndist=ndist if stats else None, early_codes=early[0])
         m = nsub or nq
         ix.search(q_dev[:m], K, L, ids[:m], dout[:m], p, stream=sptr)
 
@@ -520,7 +526,8 @@ def run_large(args):
 
     res = {}
     with ClockSampler(local) as clk:
-        for name, mode, pl, lz, what in LARGE_FORMS:
+        for name, mode, pl, lz, ec, what in LARGE_FORMS:
+            early[0] = ec
             place(pl)
             L, sweep = operating_point(mode, lz)
             search(L, mode, lz, stats=True)
@@ -531,7 +538,8 @@ def run_large(args):
             it = iters.cpu().numpy().astype(np.int64)
             nd = ndist.cpu().numpy().astype(np.int64)
             value, ms, t_wall = timed(L, mode, lz, args.steps)
-            res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, L=L, sweep=sweep,
+            res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, early=ec, L=L,
+                             sweep=sweep,
                              recall=round(r, 4), dist_error=derr, iters=it, ndist=nd, value=value,
                              ms_per_step=ms, t_wall=t_wall)
     # sampled queries of the FP32, 8-bit and Exact-distance forms at their
@@ -542,6 +550,7 @@ def run_large(args):
     parity = {}
     for name, okw in (("fp32_hbm", {}), ("q8_hbm", {"q8": True}), ("exact_hbm", {"exact": True})):
         r = res[name]
+        early[0] = r["early"]
         search(r["L"], r["mode"], r["lz"], stats=True)
         stream.synchronize()
         o = oix.search(w["queries"][sel], K, r["L"], log2z=r["lz"], **okw)
@@ -556,6 +565,7 @@ def run_large(args):
     # host memory), and the vectors alone in HBM, each at the FP32 form's
     # operating point, on a bounded sample of the batch (the same results)
     fp = res["fp32_hbm"]
+    early[0] = fp["early"]
     host = {}
     for name, pl, what in (("fp32_host", 0, "FP32 PQ table, graph and vectors read in place from "
                                            "page-locked host memory (the paper's placement, Alg. 2)"),
@@ -574,6 +584,7 @@ def run_large(args):
     place(3)
 
     # autotuned settings (table precision, Bloom size, L) for recall@10 >= 0.9 in HBM
+    early[0] = 0
     t0 = time.perf_counter()
     try:
         tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
@@ -638,7 +649,7 @@ def run_large(args):
     q_host = torch.from_numpy(w["queries"]).pin_memory()
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-    hp = bang.make_params(bloom_log2=head["lz"], mode=head["mode"])
+    hp = bang.make_params(bloom_log2=head["lz"], mode=head["mode"], early_codes=head["early"])
     for _ in range(2):
         ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))
@@ -646,6 +657,7 @@ def run_large(args):
     for _ in range(e2e_steps):
         ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
+    early[0] = head["early"]
     search(head["L"], head["mode"], head["lz"])
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
@@ -723,6 +735,7 @@ def run_large(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(args), "form": head["form"], "form_what": head["what"],
                    "L": head["L"], "recall@%d" % K: head["recall"], "k": K, "bloom_log2": head["lz"],
+                   "early_codes": head["early"],
                    "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
                    "n": n, "nq": nq, "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "l2": "512 MB flush written between timed steps; the index (77 GB) is larger "

@@ -102,6 +102,12 @@ typedef struct bang_search_params {
      * the iteration (used when it is chosen, wasted otherwise).  Results do
      * not depend on it. */
     uint32_t prefetch_depth;
+    /* When the new neighbours' PQ code rows are requested: 0 = after the seen
+     * filter, only the new ones; 1 = every neighbour's row as soon as the
+     * expanded node's row arrives, so that the filter runs while they are in
+     * flight (used when R <= 64, d <= 128 and M <= 32, and without
+     * BANG_NEIGHBOR_CODES; otherwise ignored).  Results do not depend on it. */
+    uint32_t early_codes;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,

@@ -788,6 +788,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.queue = queue;
     a.grid_mult = p.grid_mult;
     a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
+    a.early_codes = p.early_codes ? 1u : 0u;
     a.tables = tables;
     a.tables_err = static_cast<const unsigned int *>(ix->tc_err.p);
     a.out_ids = static_cast<uint32_t *>(dptr(1));
@@ -1143,6 +1144,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.queue = scratch;
     a.grid_mult = p.grid_mult;
     a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
+    a.early_codes = p.early_codes ? 1u : 0u;
     const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
     const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
     a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;

@@ -89,6 +89,7 @@ struct SearchArgs {
     const unsigned int *tables_err;  // set when the table kernel gave up
     unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
     const uint32_t *entry;    // device or null: per-query start node (null: every query starts at medoid)
+    uint32_t early_codes;     // request every neighbour's code row as soon as the row arrives (see CS)
 };
 
 // Phases timed when SearchArgs::phase_cycles is set.
@@ -573,11 +574,17 @@ template <bool ON> struct PhaseClock {
     }
 };
 
-template <int DT, int RPL, int DCH, int MODE, bool NC, bool PH>
+// CS, where the new neighbours' code rows come from: 0 = each requested
+// after the seen filter (only the new ones); 1 = the neighbour-code layout
+// (every neighbour's row arrives with the node); 2 = every neighbour's row
+// requested from the codes as soon as the node's row arrives, so that the
+// filter runs while they are in flight (rows of at most 32 bytes).
+template <int DT, int RPL, int DCH, int MODE, int CS, bool PH>
 __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 {
     using E = typename Elem<DT>::T;
     constexpr bool kPQ = MODE != kModeExact;
+    constexpr bool NC = CS == 1;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x;
     const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d, a.R, MODE);
@@ -717,6 +724,18 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             clk.mark(kPhSelect);
 
             unpack_ids<RPL>(a, lane, nd.nb);
+            // early code rows (CS 2): every neighbour's row requested now
+            uint4 ec[CS == 2 ? 2 * RPL : 1];
+            if constexpr (CS == 2) {
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    const uint32_t id = nd.nb[r];
+                    const uint4 *row16 = reinterpret_cast<const uint4 *>(
+                        a.codes + static_cast<uint64_t>(id == kNone ? 0u : id) * a.Mpad);
+                    ec[2 * r] = id != kNone ? __ldg(row16) : make_uint4(0u, 0u, 0u, 0u);
+                    ec[2 * r + 1] = (id != kNone && a.Mpad > 16u) ? __ldg(row16 + 1) : make_uint4(0u, 0u, 0u, 0u);
+                }
+            }
             // ---- filter seen neighbours, §4.3: test all, then insert all
             bool fresh[RPL];
             uint32_t p1[RPL], p2[RPL], slot[RPL];
@@ -767,6 +786,14 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 for (int r = 0; r < RPL; ++r) {
                     if (!fresh[r]) continue;
                     const uint4 c0 = nd.code[2 * r], c1 = nd.code[2 * r + 1];
+                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(T, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
+                                                                a.M, a.Mpad), nd.nb[r]);
+                }
+            } else if constexpr (CS == 2) {   // code rows requested before the filter
+#pragma unroll
+                for (int r = 0; r < RPL; ++r) {
+                    if (!fresh[r]) continue;
+                    const uint4 c0 = ec[2 * r], c1 = ec[2 * r + 1];
                     Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(T, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
                                                                 a.M, a.Mpad), nd.nb[r]);
                 }
@@ -1091,10 +1118,10 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
 
 // Launch for one mode: dispatch on element type, neighbours per lane
 // (R <= 64 or <= 128) and 128-dimension chunks per lane (d <= 128 or <= 512).
-template <int DT, int RPL, int DCH, int MODE, bool NC, bool PH>
+template <int DT, int RPL, int DCH, int MODE, int CS, bool PH>
 cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
 {
-    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, NC, PH>,
+    cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, CS, PH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     uint32_t grid = a.nq;
@@ -1102,24 +1129,24 @@ cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
         int dev = 0, sms = 0, per_sm = 0;
         if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
         if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE, NC, PH>,
+        if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, search_kernel<DT, RPL, DCH, MODE, CS, PH>,
                                                                32, smem)) != cudaSuccess)
             return e;
         const uint64_t want = static_cast<uint64_t>(sms) * (per_sm > 0 ? per_sm : 1) *
                               (a.grid_mult ? a.grid_mult : 1u);
         grid = static_cast<uint32_t>(want < a.nq ? want : a.nq);
     }
-    search_kernel<DT, RPL, DCH, MODE, NC, PH><<<grid, 32, smem, st>>>(a);
+    search_kernel<DT, RPL, DCH, MODE, CS, PH><<<grid, 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 
 // The per-phase clock (SearchArgs::phase_cycles) is a separate instantiation,
 // so the timed kernel carries none of its registers or branches.
-template <int DT, int RPL, int DCH, int MODE, bool NC = false>
+template <int DT, int RPL, int DCH, int MODE, int CS = 0>
 cudaError_t launch_ph(const SearchArgs &a, size_t smem, cudaStream_t st)
 {
-    return a.phase_cycles ? launch_one<DT, RPL, DCH, MODE, NC, true>(a, smem, st)
-                          : launch_one<DT, RPL, DCH, MODE, NC, false>(a, smem, st);
+    return a.phase_cycles ? launch_one<DT, RPL, DCH, MODE, CS, true>(a, smem, st)
+                          : launch_one<DT, RPL, DCH, MODE, CS, false>(a, smem, st);
 }
 
 template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st)
@@ -1127,9 +1154,14 @@ template <int MODE> cudaError_t launch_mode(const SearchArgs &a, int dtype, size
     const bool narrow = a.d <= 128, wide_r = a.R > 64;
     if constexpr (MODE != kModeExact) {
         if (a.ncodes) {                // neighbour-code layout: R <= 64, d <= 128, checked by the caller
-            if (dtype == 0) return launch_ph<0, 2, 1, MODE, true>(a, smem, st);
-            if (dtype == 1) return launch_ph<1, 2, 1, MODE, true>(a, smem, st);
-            return launch_ph<2, 2, 1, MODE, true>(a, smem, st);
+            if (dtype == 0) return launch_ph<0, 2, 1, MODE, 1>(a, smem, st);
+            if (dtype == 1) return launch_ph<1, 2, 1, MODE, 1>(a, smem, st);
+            return launch_ph<2, 2, 1, MODE, 1>(a, smem, st);
+        }
+        if (a.early_codes && !wide_r && narrow && a.Mpad <= 32u) {   // early code rows
+            if (dtype == 0) return launch_ph<0, 2, 1, MODE, 2>(a, smem, st);
+            if (dtype == 1) return launch_ph<1, 2, 1, MODE, 2>(a, smem, st);
+            return launch_ph<2, 2, 1, MODE, 2>(a, smem, st);
         }
     }
 #define BANG_DISPATCH(DT)                                                                    \

@@ -18,7 +18,7 @@ RTOL = 1e-5
 
 
 def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
-               placement=0, prefetch_depth=0, phases=False):
+               placement=0, prefetch_depth=0, phases=False, early_codes=0):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     if placement:
@@ -38,7 +38,8 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     ph = torch.zeros((nq, len(bang.PHASES)), dtype=torch.int64, device=dev) if phases else None
     p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
                          out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
-                         mode=mode, prefetch_depth=prefetch_depth, out_phase_cycles=ph)
+                         mode=mode, prefetch_depth=prefetch_depth, out_phase_cycles=ph,
+                         early_codes=early_codes)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
@@ -295,6 +296,21 @@ def test_speculative_prefetch_gives_identical_results(u8small, cfg1, mode, flags
         g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags, prefetch_depth=2)
         for f in ("ids", "dist", "iters", "ndist", "trace"):
             assert (g[f] == ref[f]).all(), (mode, flags, f)
+
+
+@pytest.mark.parametrize("mode,flags", [(0, 0), (1, 0), (3, 0), (0, 3), (3, 3), (3, 4), (1, 6),
+                                        (0, 16), (3, 8)])
+def test_early_code_rows_give_identical_results(u8small, cfg1, mode, flags):
+    # early_codes requests every neighbour's code row as soon as the node's
+    # row arrives (the neighbour-code layout, flag 8, takes precedence);
+    # visits, counts and results are unchanged and equal to the oracle's
+    for w, Q, L in ((u8small, u8small["queries"][:120], 64), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags)
+        g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags, early_codes=1)
+        for f in ("ids", "dist", "iters", "ndist", "trace"):
+            assert (g[f] == ref[f]).all(), (mode, flags, f)
+        o = oracle_search(w, Q, 10, L, trace_cap=400, q8=mode == 3, bf16=mode == 1)
+        assert (g["ids"] == o["ids"]).all() and (g["iters"] == o["iters"]).all()
 
 
 @pytest.mark.parametrize("mode,flags", [(0, 0), (1, 0), (2, 3), (3, 4)])
