@@ -446,13 +446,16 @@ int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, 
                   void *stream);
 
 /* ---- Serving: continuous batching (north of the paper's batch-at-a-time
- * evaluation, §6.2 runs one batch of 10,000 queries).  A server owns
- * `streams` slots, each with page-locked and device buffers for max_batch
- * queries allocated at start (admission is by device memory: a request waits
- * for a free slot).  A dispatcher thread packs pending requests into one
- * bang_search_batched launch per free slot; launches on different slots
- * overlap on the GPU.  Results are identical to searching each request alone
- * with the same k, L and settings. */
+ * evaluation, §6.2 runs one batch of 10,000 queries).  Admission is by device
+ * memory: a server owns a device arena of mem_bytes (and a page-locked host
+ * mirror of it) allocated at start; a dispatcher thread packs pending
+ * requests, in arrival order, into one bang_search_batched launch (at most
+ * max_batch queries) as soon as one of `streams` streams is free and the
+ * arena has room for the batch's queries and results; a request that does
+ * not fit waits until earlier launches release their memory (first in,
+ * first out).  Launches on different streams overlap on the GPU.  Results
+ * are identical to searching each request alone with the same k, L and
+ * settings. */
 typedef struct bang_server bang_server;
 typedef struct bang_server_config {
     uint32_t k_max, L_max;   /* bounds of every request's k and L */
@@ -460,15 +463,19 @@ typedef struct bang_server_config {
     uint32_t streams;        /* slots (launches in flight at once), 1..16 */
     uint32_t mode;           /* bang_mode of the searches */
     uint32_t bloom_log2;     /* as bang_search_params (0 = 16) */
+    uint64_t mem_bytes;      /* device bytes for batches in flight (0: room for `streams`
+                                full batches); a batch of nq queries takes about
+                                nq * (d * elem + 8 + 8 * k_max) bytes */
 } bang_server_config;
 
 /* Start a server on the calling thread's current device for a fully loaded
  * index (which must outlive the server).  While the server runs, its
  * dispatcher thread is the index's caller: make no other call on that index
- * until bang_server_stop returns.  BANG_ENOMEM if the slots do not fit. */
+ * until bang_server_stop returns.  BANG_ENOMEM if the arena does not fit. */
 int bang_server_start(bang_index *ix, const bang_server_config *cfg, bang_server **out);
 /* Queue nq (1..max_batch) host queries with their k and L (host arrays,
- * copied before return); *ticket identifies the request. */
+ * copied before return); *ticket identifies the request.  BANG_EINVAL if the
+ * request alone needs more than mem_bytes. */
 int bang_server_submit(bang_server *s, const void *queries, uint32_t nq, const uint32_t *k_per_q,
                        const uint32_t *L_per_q, uint64_t *ticket);
 /* Wait up to timeout_ms (negative: no limit) for a request, copy its results

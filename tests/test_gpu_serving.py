@@ -105,3 +105,35 @@ def test_requests_wait_for_a_busy_slot(index):
     # queued behind the single slot: later requests waited longer
     assert lat[-1] > lat[0]
     srv.stop()
+
+
+def test_admission_by_device_memory(index):
+    """A memory budget of about one and a half full batches with four
+    streams: small requests run several at a time, full-size ones wait for
+    memory to be released (first in, first out), a request larger than the
+    budget is refused, and every result equals the request searched alone."""
+    w, ix = index
+    kmax, Lmax, d = 10, 64, w["base"].shape[1]
+    per_q = d + 8 + 8 * kmax                       # bytes of one query's buffers
+    srv = bang.Server(ix, kmax, Lmax, max_batch=256, streams=4, mem_bytes=int(1.5 * 256 * per_q) + 4096)
+    rng = np.random.default_rng(31)
+    reqs = []
+    for i in range(40):
+        n = 256 if i % 5 == 0 else int(rng.integers(1, 64))
+        sel = rng.choice(w["queries"].shape[0], n, replace=True)
+        reqs.append((w["queries"][sel], np.full(n, 10, np.uint32), np.full(n, 64, np.uint32)))
+    tickets = [srv.submit(*r) for r in reqs]
+    for i, (Q, k, L) in enumerate(reqs):
+        ids, dist, _ = srv.wait(tickets[i], timeout_ms=60_000)
+        ids_a, dist_a = _alone(ix, Q, k, L, kmax, Lmax)
+        assert (ids == ids_a).all(), i
+        assert (dist == dist_a).all(), i
+    srv.stop()
+    small = bang.Server(ix, kmax, Lmax, max_batch=256, streams=2, mem_bytes=64 * per_q + 4096)
+    with pytest.raises(bang.BangError) as e:      # 256 queries need more than the budget
+        small.submit(w["queries"][:256], np.full(256, 10, np.uint32), np.full(256, 64, np.uint32))
+    assert e.value.code == bang.BANG_EINVAL
+    t = small.submit(w["queries"][:32], np.full(32, 10, np.uint32), np.full(32, 64, np.uint32))
+    ids, _, _ = small.wait(t, timeout_ms=60_000)
+    assert (ids != bang.BANG_NONE).any()
+    small.stop()
