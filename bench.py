@@ -390,7 +390,19 @@ def large_workload(args, device):
     truth rows checked against the oracle's brute force."""
     import workload
     import paper_2401_11324_gb300 as bang
-    w = workload.large_data(args.config, n=args.n, nq=args.nq, ncomp=args.ncomp, verbose=True)
+    n_req = args.n
+    _, world, _ = dist_env()
+    if n_req is None and world > 1:
+        # every replica holds the data and graph in host memory while it
+        # builds (about 420 bytes per point): fit all ranks on this node
+        avail = 0
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("MemAvailable:"):
+                    avail = int(line.split()[1]) * 1024
+        n_req = int(min(workload.CONFIGS[args.config]["n"], 0.7 * avail / (world * 420)))
+        n_req -= n_req % 1_000_000
+    w = workload.large_data(args.config, n=n_req, nq=args.nq, ncomp=args.ncomp, verbose=True)
     c = w["params"]
     n = w["base"].shape[0]
     t0 = time.perf_counter()
@@ -1077,6 +1089,10 @@ def main():
                      "frac": host_bytes / launch_s / 1e9 / link["gather_gbs"],
                      "traffic": NCU_HOST_TRAFFIC.get((mode, lz, L, head["placement"])) if args.n is None
                      else None,
+                     "traffic_note": "host sectors x 32 B from the capture of this head's settings"
+                                     if args.n is None and (mode, lz, L, head["placement"]) in NCU_HOST_TRAFFIC
+                                     else "no capture of this head's settings (mode %d, 2^%d bits, L %d, "
+                                          "placement %d)" % (mode, lz, L, head["placement"]),
                      "peak_source": "measured in this run: random %d-byte row gathers in place "
                                     "from mapped host memory over NVLink-C2C" % link["gather_row_bytes"],
                      "algorithmic_bytes_per_launch": host_bytes,
