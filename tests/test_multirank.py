@@ -59,8 +59,11 @@ def test_reference_arm_json_line(tmp_path):
     import sys
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     env = dict(os.environ, BANG_WORKLOAD_CACHE=str(tmp_path), RANK="0", WORLD_SIZE="1")
+    # configuration 2's small instance: its index comes from the host
+    # generator, so the arm runs without a GPU (the large configurations build
+    # theirs on the GPU)
     out = subprocess.run([sys.executable, os.path.join(root, "bench.py"), "--impl", "reference",
-                          "--n", "20000", "--nq", "200", "--ncomp", "8", "--L", "64",
+                          "--config", "2", "--n", "20000", "--nq", "200", "--ncomp", "8", "--L", "64",
                           "--cpu-sample", "100", "--steps", "1", "--warmup", "3"],
                          cwd=root, env=env, capture_output=True, text=True, timeout=600)
     assert out.returncode == 0, out.stderr[-2000:]
