@@ -4,7 +4,7 @@ Workload: the mid-scale plain-method configuration (n = 1,000,000 uint8
 points, d = 128, 256-component mixture, 10,000 queries, PQ M = 32 on the
 device, clustered graph R = 64 and full vectors in page-locked host memory,
 k = 10).  The worklist size L is the smallest of the sweep
-{16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024} (values
+{16, 24, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256, 288, 320, 384, 512, 768, 1024} (values
 >= k) whose mean recall@k reaches 0.9 (ground truth: exact k-NN); a step is one
 search of the whole batch at that L.  `--k 100` measures 100-recall@100 and
 `--M` another PQ code size (the paper's second workload and compression study).
@@ -40,7 +40,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-L_SWEEP = (16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512, 768, 1024)
+L_SWEEP = (16, 24, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256, 288, 320, 384, 512, 768, 1024)
 TARGET_RECALL = 0.9
 K = 10                      # k of the search and of recall@k (--k)
 def workload_name(args):

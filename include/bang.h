@@ -404,8 +404,9 @@ int bang_ground_truth(int device, const void *base, const void *queries, bang_dt
  *                 its recall is at least the FP32 form's (mode 0, 2^16 bits)
  *                 minus recall_tolerance (default 0.005).
  *   target_recall in (0, 1]: every candidate takes the smallest worklist of
- *                 {16, 24, 32, 48, 64, 96, 128, 160, 192, 256, 320, 384, 512,
- *                 768, 1024} (at least k, at most L unless L is 0) whose
+ *                 {16, 24, 32, 48, 64, 80, 96, 112, 128, 160, 192, 224, 256,
+ *                 288, 320, 384, 512, 768, 1024} (at least k, at most L unless
+ *                 L is 0) whose
  *                 recall reaches the target.
  * The fastest qualifying candidate is returned in *out with its L, time and
  * recall, beside the FP32 form's (ref_ms, ref_recall at its own L).  With

@@ -258,7 +258,8 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
     // worklist sizes: the given L, or the sweep for the target recall
     std::vector<uint32_t> Ls;
     if (o.target_recall > 0.f) {
-        for (uint32_t c : {16u, 24u, 32u, 48u, 64u, 96u, 128u, 160u, 192u, 256u, 320u, 384u, 512u, 768u, 1024u})
+        for (uint32_t c : {16u, 24u, 32u, 48u, 64u, 80u, 96u, 112u, 128u, 160u, 192u, 224u, 256u, 288u, 320u,
+                            384u, 512u, 768u, 1024u})
             if (c >= k && (L == 0 || c <= L)) Ls.push_back(c);
         if (Ls.empty()) return tfail(BANG_EINVAL, "bang_autotune: no worklist size between k and L");
     } else {
