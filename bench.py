@@ -617,17 +617,20 @@ def run_large(args):
     q8 = res["q8_hbm"]
     rng = np.random.default_rng(44)
     kq = rng.choice([1, 10, 100], size=nq).astype(np.uint32)
-    Lq = np.maximum(rng.choice([64, 128, 192, 256], size=nq), kq).astype(np.uint32)
+    lmix = [q8["L"], q8["L"] * 5 // 4, q8["L"] * 3 // 2, 2 * q8["L"]]   # the operating point up to 2x
+    lmix = [min(x, 1024) for x in lmix]
+    Lq = np.maximum(rng.choice(lmix, size=nq), kq).astype(np.uint32)
+    Lmax_b = int(Lq.max())
     kd = torch.from_numpy(kq.view(np.int32)).to(dev)
     Ld = torch.from_numpy(Lq.view(np.int32)).to(dev)
     bids = torch.empty((nq, 100), dtype=torch.int32, device=dev)
     bdist = torch.empty((nq, 100), dtype=torch.float32, device=dev)
     bp = bang.make_params(bloom_log2=q8["lz"], mode=q8["mode"])
-    ix.search_batched(q_dev, kd, Ld, 100, 256, bids, bdist, bp, stream=sptr)
+    ix.search_batched(q_dev, kd, Ld, 100, Lmax_b, bids, bdist, bp, stream=sptr)
     stream.synchronize()
     graph = torch.cuda.CUDAGraph()
     with torch.cuda.graph(graph, stream=stream):
-        ix.search_batched(q_dev, kd, Ld, 100, 256, bids, bdist, bp, stream=sptr)
+        ix.search_batched(q_dev, kd, Ld, 100, Lmax_b, bids, bdist, bp, stream=sptr)
     for _ in range(args.warmup):
         graph.replay()
     torch.cuda.synchronize(dev)
@@ -649,8 +652,9 @@ def run_large(args):
     batched = {"value": nq / (bms / 1e3), "unit": "queries/s", "ms_per_step": bms,
                "launch": "one persistent launch (bang_search_batched) replayed from a CUDA graph, "
                          "8-bit table, graph and vectors in HBM",
-               "k_mix": "uniform over {1, 10, 100}", "L_mix": "uniform over {64, 128, 192, 256}, "
-               "at least k", **brec}
+               "k_mix": "uniform over {1, 10, 100}",
+               "L_mix": "uniform over {%s} (the 8-bit form's operating point up to twice it), at least k"
+                        % ", ".join(str(x) for x in lmix), **brec}
     del graph
 
     # the headline: the fastest FP32-table form reaching the target recall
