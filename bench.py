@@ -440,15 +440,23 @@ def large_workload(args, device):
 # (early_codes; same results; measured faster with the FP32 and BF16 tables,
 # slower with the 8-bit table).
 LARGE_FORMS = [
-    ("fp32_hbm", 0, 3, 16, 1, "FP32 PQ table (the paper's precision), graph and vectors in HBM (the "
-                              "In-memory variant, §5.1)"),
-    ("bf16_hbm", 1, 3, 16, 1, "BF16 PQ table (reduced precision) summed in FP32, graph and vectors in "
-                              "HBM"),
-    ("q8_hbm", 3, 3, 15, 0, "8-bit PQ table (reduced precision) summed in integers, graph and vectors "
-                            "in HBM"),
-    ("exact_hbm", 2, 3, 16, 0, "Exact-distance variant (§5.2): exact distances in the loop, no table "
-                               "and no re-rank, graph and vectors in HBM"),
+    ("fp32_hbm", 0, 3, 16, 1, 0, "FP32 PQ table (the paper's precision), graph and vectors in HBM (the "
+                                 "In-memory variant, §5.1)"),
+    ("bf16_hbm", 1, 3, 16, 1, 0, "BF16 PQ table (reduced precision) summed in FP32, graph and vectors "
+                                 "in HBM"),
+    ("q8_hbm", 3, 3, 15, 0, 0, "8-bit PQ table (reduced precision) summed in integers, graph and "
+                               "vectors in HBM"),
+    ("exact_hbm", 2, 3, 16, 0, 0, "Exact-distance variant (§5.2): exact distances in the loop, no "
+                                  "table and no re-rank, graph and vectors in HBM"),
+    ("fp32_tc_hbm", 0, 3, 16, 1, 1, "FP32 search on tables built by the tensor cores (three-way BF16 "
+                                    "splits, about FP32), graph and vectors in HBM"),
+    ("tf32_tc_hbm", 0, 3, 16, 1, 2, "TF32 tables: the tensor-core contraction with both operands "
+                                    "rounded to TF32 and FP32 accumulation, FP32 search, HBM"),
 ]
+
+
+# FP32 (the paper's precision) first, then the reduced and tensor-core table forms
+PRECISION_FORMS = ("fp32_hbm", "bf16_hbm", "q8_hbm", "tf32_tc_hbm", "fp32_tc_hbm")
 
 
 def run_large(args):
@@ -489,10 +497,12 @@ def run_large(args):
             placement[0] = flags
 
     early = [0]                     # early_codes of the form being measured
+    tsrc = [0]                      # table_source of the form being measured
 
     def search(L, mode, lz, nsub=None, stats=False):
         p = bang.make_params(bloom_log2=lz, mode=mode, out_iters=iters if stats else None,
-                             out_ndist=ndist if stats else None, early_codes=early[0])
+                             out_ndist=ndist if stats else None, early_codes=early[0],
+                             table_source=tsrc[0])
         m = nsub or nq
         ix.search(q_dev[:m], K, L, ids[:m], dout[:m], p, stream=sptr)
 
@@ -538,8 +548,9 @@ def run_large(args):
 
     res = {}
     with ClockSampler(local) as clk:
-        for name, mode, pl, lz, ec, what in LARGE_FORMS:
+        for name, mode, pl, lz, ec, ts, what in LARGE_FORMS:
             early[0] = ec
+            tsrc[0] = ts
             place(pl)
             L, sweep = operating_point(mode, lz)
             search(L, mode, lz, stats=True)
@@ -550,8 +561,8 @@ def run_large(args):
             it = iters.cpu().numpy().astype(np.int64)
             nd = ndist.cpu().numpy().astype(np.int64)
             value, ms, t_wall = timed(L, mode, lz, args.steps)
-            res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, early=ec, L=L,
-                             sweep=sweep,
+            res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, early=ec, tsrc=ts,
+                             L=L, sweep=sweep,
                              recall=round(r, 4), dist_error=derr, iters=it, ndist=nd, value=value,
                              ms_per_step=ms, t_wall=t_wall)
     # sampled queries of the FP32, 8-bit and Exact-distance forms at their
@@ -563,6 +574,7 @@ def run_large(args):
     for name, okw in (("fp32_hbm", {}), ("q8_hbm", {"q8": True}), ("exact_hbm", {"exact": True})):
         r = res[name]
         early[0] = r["early"]
+        tsrc[0] = r["tsrc"]
         search(r["L"], r["mode"], r["lz"], stats=True)
         stream.synchronize()
         o = oix.search(w["queries"][sel], K, r["L"], log2z=r["lz"], **okw)
@@ -578,6 +590,7 @@ def run_large(args):
     # operating point, on a bounded sample of the batch (the same results)
     fp = res["fp32_hbm"]
     early[0] = fp["early"]
+    tsrc[0] = fp["tsrc"]
     host = {}
     for name, pl, what in (("fp32_host", 0, "FP32 PQ table, graph and vectors read in place from "
                                            "page-locked host memory (the paper's placement, Alg. 2)"),
@@ -597,6 +610,7 @@ def run_large(args):
 
     # autotuned settings (table precision, Bloom size, L) for recall@10 >= 0.9 in HBM
     early[0] = 0
+    tsrc[0] = 0
     t0 = time.perf_counter()
     try:
         tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
@@ -665,7 +679,8 @@ def run_large(args):
     q_host = torch.from_numpy(w["queries"]).pin_memory()
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
-    hp = bang.make_params(bloom_log2=head["lz"], mode=head["mode"], early_codes=head["early"])
+    hp = bang.make_params(bloom_log2=head["lz"], mode=head["mode"], early_codes=head["early"],
+                          table_source=head["tsrc"])
     for _ in range(2):
         ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))
@@ -674,6 +689,7 @@ def run_large(args):
         ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     early[0] = head["early"]
+    tsrc[0] = head["tsrc"]
     search(head["L"], head["mode"], head["lz"])
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
@@ -731,6 +747,10 @@ def run_large(args):
         "q8_hbm": {"value": q8["value"], "L": q8["L"], "recall@%d" % K: q8["recall"]},
         "exact_hbm": {"value": res["exact_hbm"]["value"], "L": res["exact_hbm"]["L"],
                       "recall@%d" % K: res["exact_hbm"]["recall"]},
+        "tensor_core_tables": {f: {"value": res[f]["value"], "L": res[f]["L"],
+                                   "recall@%d" % K: res[f]["recall"],
+                                   "recall_vs_fp32": round(res[f]["recall"] - fp["recall"], 4)}
+                               for f in ("fp32_tc_hbm", "tf32_tc_hbm")},
         "served": None if served is None else {k_: served[k_] for k_ in (
             "achieved_qps", "p50_ms", "p99_ms", "vs_plain_form", "vs_fp32_hbm")},
         "served_q8": None if served_q8 is None else {k_: served_q8[k_] for k_ in (
@@ -738,11 +758,11 @@ def run_large(args):
         "batched": {"value": batched["value"], "recall@10": batched["recall@10"]},
         "precision": {"tolerance": "reduced forms within 0.005 of FP32's recall@10",
                       "within": {f: abs(res[f]["recall"] - fp["recall"]) <= 0.005
-                                 for f in ("bf16_hbm", "q8_hbm")},
-                      "recall@10": {f: res[f]["recall"] for f in ("fp32_hbm", "bf16_hbm", "q8_hbm")},
-                      "L": {f: res[f]["L"] for f in ("fp32_hbm", "bf16_hbm", "q8_hbm")},
+                                 for f in PRECISION_FORMS[1:]},
+                      "recall@10": {f: res[f]["recall"] for f in PRECISION_FORMS},
+                      "L": {f: res[f]["L"] for f in PRECISION_FORMS},
                       "max_rel_dist_error_vs_fp64": max(res[f]["dist_error"]["max_rel"]
-                                                        for f in ("fp32_hbm", "bf16_hbm", "q8_hbm"))},
+                                                        for f in PRECISION_FORMS)},
     }
     line = {
         "metric": metric_name(), "value": head["value"], "unit": "queries/s",

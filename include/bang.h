@@ -91,10 +91,13 @@ typedef struct bang_search_params {
     /* bang_search_batched only: the persistent grid is grid_mult times the
      * CTAs that fit on the device at once (0 or 1: exactly that many). */
     uint32_t grid_mult;
-    /* Where the PQ tables of mode 1 come from: 0 = built by each query's warp
-     * on CUDA cores; 1 = built for the whole batch by the tensor-core kernel
-     * of bang_pq_tables into per-stream device scratch owned by the index
-     * (nq*M*512 bytes), then read by the search. */
+    /* Where the PQ tables of modes 0 and 1 come from: 0 = built by each
+     * query's warp on CUDA cores (mode 0: bit-exact); 1 = built for the whole
+     * batch by the tensor-core kernel of bang_pq_tables (three-way BF16
+     * splits, about FP32-accurate) into per-stream device scratch owned by the
+     * index (nq*M*256 entries of 4 bytes in mode 0, 2 in mode 1), then read by
+     * the search; 2 = the same with both operands rounded to TF32 (the
+     * numerics of a TF32 GEMM with FP32 accumulation: the TF32 table form). */
     uint32_t table_source;
     /* How many candidates for the next node are requested per iteration: 0
      * or 1 = the chosen one only, after the distances (§4.5's eager choice);
@@ -261,8 +264,10 @@ int bang_set_placement(bang_index *ix, uint32_t flags);
 /* PQ distance tables of nq queries on the tensor cores (§4.1 as a dense
  * queries x centroids contraction: tcgen05 MMAs with BF16 high/low operand
  * splits and FP32 accumulation, about FP32-accurate):
- * out[q][s][c] = ||q_s - C_s[c]||^2, M x 256 per query, FP32 or (out_bf16)
- * BF16.  queries and out are device memory; waits for the stream.  Needs the
+ * out[q][s][c] = ||q_s - C_s[c]||^2, M x 256 per query, FP32 or (bit 0 of
+ * out_bf16) BF16; bit 1 of out_bf16 rounds both operands to TF32 first (a
+ * TF32 value is two exact BF16 parts, so the products are those of a TF32
+ * GEMM).  queries and out are device memory; waits for the stream.  Needs the
  * vectors registered (for the element type); BANG_EINVAL if a subspace
  * spans more than 4 blocks of 16 dimensions; BANG_ETIMEOUT if a bounded
  * tensor-core wait gave up. */

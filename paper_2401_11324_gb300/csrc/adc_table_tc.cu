@@ -11,7 +11,12 @@
 // 24 significant bits), and the products that matter (high x all, middle x
 // high and middle, low x high) are summed in the FP32 accumulator, which
 // gives the cross term to about FP32 accuracy; the norms are FP32.  Tables come out FP32 or
-// BF16 (the reduced-precision search form reads BF16 tables).
+// BF16 (the reduced-precision search form reads BF16 tables).  The TF32 form
+// (a.tf32 with centroid tiles rounded to TF32 on the host) rounds both
+// operands to TF32 first; a TF32 value is exactly the sum of two BF16 parts,
+// so the same MMAs then form exact TF32 x TF32 products with FP32
+// accumulation: the numerics of a TF32 GEMM, at about its tensor-pipe cost
+// (two BF16 MMAs per TF32 MMA).
 //
 // Per CTA: 128 threads; thread t owns query row t of the tile (TMEM lane t)
 // and writes that row of the query operand for each subspace's K blocks.
@@ -106,6 +111,16 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float *v)
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Round to TF32 (10 mantissa bits), to nearest with ties to even: the
+// operands of the TF32 form, whose products the split parts then carry
+// exactly (a TF32 value is the sum of two BF16 values).
+__device__ __forceinline__ float tf32_rne(float x)
+{
+    uint32_t u = __float_as_uint(x);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    return __uint_as_float(u & ~0x1FFFu);
+}
+
 // Offset of element (row, k) of a K-major no-swizzle operand with 16 K
 // columns: core (row/8, k/8), 8 rows of 16 bytes per core.
 __device__ __forceinline__ uint32_t core_off(uint32_t row, uint32_t k)
@@ -165,7 +180,8 @@ __global__ void __launch_bounds__(128) adc_table_tc_kernel(TcTableArgs a)
         for (uint32_t b = 0; b < nb; ++b)
             for (uint32_t kk = 0; kk < 16; ++kk) {
                 const uint32_t j = (kb0 + b) * 16u + kk;
-                const float x = (valid && j < a.d) ? static_cast<float>(qp[j]) : 0.0f;
+                float x = (valid && j < a.d) ? static_cast<float>(qp[j]) : 0.0f;
+                if (a.tf32) x = tf32_rne(x);
                 const __nv_bfloat16 h = __float2bfloat16_rn(x);
                 const float r1 = x - __bfloat162float(h);
                 const __nv_bfloat16 m = __float2bfloat16_rn(r1);

@@ -23,6 +23,7 @@ struct TcTableArgs {
     const float *cnorm;         // device, M*256 squared centroid norms
     void *out;                  // device, nq*M*256 FP32 or BF16
     uint32_t out_bf16;
+    uint32_t tf32;              // queries rounded to TF32 (pair with the TF32 centroid tiles)
     unsigned int *err;          // device flag, set to 1 if a wait gave up
 };
 

@@ -245,6 +245,7 @@ struct bang_index {
     // first tile per subspace, squared centroid norms; per-stream table
     // scratch for searches that read precomputed tables; error flag.
     DevBuf tc_btiles, tc_bfirst, tc_cnorm, tc_err;
+    DevBuf tc_btiles_tf32;    // the same tiles with the centroids rounded to TF32
     bool tc_ok = false;
     std::map<cudaStream_t, DevBuf> tables;
 };
@@ -290,8 +291,24 @@ float bf16_to_f32(uint16_t h)
 // every 16-wide K block it touches, a 256 x 16 BF16 tile of the centroids
 // (zero outside the subspace's dimensions) in the no-swizzle K-major
 // core-matrix layout, split into high, middle and low BF16 parts.
+// Round to TF32 (10 mantissa bits), to nearest with ties to even.
+float tf32_rne_host(float x)
+{
+    uint32_t u;
+    std::memcpy(&u, &x, 4);
+    u += 0xFFFu + ((u >> 13) & 1u);
+    u &= ~0x1FFFu;
+    float y;
+    std::memcpy(&y, &u, 4);
+    return y;
+}
+
+// Centroid tiles of the tensor-core tables: per 16-dimension block three BF16
+// parts of every centroid value (hi, mid, lo: about FP32), or, for the TF32
+// form, the value rounded to TF32 as two exact BF16 parts and a zero part.
 bool build_tc_tiles(const float *codebook, uint32_t d, uint32_t M, const std::vector<uint32_t> &off,
-                    std::vector<uint16_t> &tiles, std::vector<uint32_t> &first, std::vector<float> &cnorm)
+                    std::vector<uint16_t> &tiles, std::vector<uint32_t> &first, std::vector<float> &cnorm,
+                    bool tf32 = false)
 {
     const uint32_t elems = 256u * 16u;                  // one tile
     first.assign(M, 0);
@@ -314,11 +331,12 @@ bool build_tc_tiles(const float *codebook, uint32_t d, uint32_t M, const std::ve
             for (uint32_t c = 0; c < 256; ++c)
                 for (uint32_t kk = 0; kk < 16; ++kk) {
                     const uint32_t j = kb * 16 + kk;
-                    const float x = (j >= o && j < o + ds) ? cb[c * ds + (j - o)] : 0.0f;
+                    float x = (j >= o && j < o + ds) ? cb[c * ds + (j - o)] : 0.0f;
+                    if (tf32) x = tf32_rne_host(x);
                     const uint16_t hi = bf16_rne(x);
                     const float r1 = x - bf16_to_f32(hi);
                     const uint16_t mid = bf16_rne(r1);
-                    const uint16_t lo = bf16_rne(r1 - bf16_to_f32(mid));
+                    const uint16_t lo = tf32 ? 0 : bf16_rne(r1 - bf16_to_f32(mid));
                     const size_t e = (((c >> 3) * 2 + (kk >> 3)) * 128 + (c & 7) * 16 + (kk & 7) * 2) / 2;
                     tiles[base + e] = hi;
                     tiles[base + elems + e] = mid;
@@ -580,6 +598,12 @@ int bang_load_pq(bang_index *ix, uint32_t d, uint32_t M, const float *codebook,
         ix->tc_ok = build_tc_tiles(codebook, d, M, off, tiles, first, cn) &&
                     bang::tc_table_smem_bytes(d, 2) <= 227u * 1024u;
         if (ix->tc_ok) {
+            std::vector<uint16_t> tiles32;
+            std::vector<uint32_t> first32;
+            std::vector<float> cn32;
+            build_tc_tiles(codebook, d, M, off, tiles32, first32, cn32, true);
+            CUDA_TRY(ix->tc_btiles_tf32.ensure(tiles32.size() * 2));
+            CUDA_TRY(cudaMemcpy(ix->tc_btiles_tf32.p, tiles32.data(), tiles32.size() * 2, cudaMemcpyHostToDevice));
             CUDA_TRY(ix->tc_btiles.ensure(tiles.size() * 2));
             CUDA_TRY(ix->tc_bfirst.ensure(first.size() * 4));
             CUDA_TRY(ix->tc_cnorm.ensure(cn.size() * 4));
@@ -727,27 +751,30 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     // searches start first.
     // Tensor-core tables (reduced-precision form): all tables of the batch
     // into per-stream scratch, then the search reads them.
-    const uint16_t *tables = nullptr;
-    if (p.table_source == 1) {
-        if (p.mode != 1) return fail(BANG_EINVAL, "bang_search: table_source 1 needs mode 1 (BF16 tables)");
+    const void *tables = nullptr;
+    if (p.table_source == 1 || p.table_source == 2) {
+        if (p.mode != 0 && p.mode != 1)
+            return fail(BANG_EINVAL, "bang_search: table_source %u needs mode 0 (FP32 tables) or 1 (BF16)",
+                        p.table_source);
         if (!ix->tc_ok) return fail(BANG_EINVAL, "bang_search: tensor-core tables unavailable for this "
                                     "PQ layout (a subspace spans more than %u 16-dim blocks)", bang::kMaxKbPerSub);
         DevBuf &tb = ix->tables[st];
-        CUDA_TRY(tb.ensure((size_t)nq * ix->M * 256 * 2));
+        CUDA_TRY(tb.ensure((size_t)nq * ix->M * 256 * (p.mode == 1 ? 2 : 4)));
         CUDA_TRY(cudaMemsetAsync(ix->tc_err.p, 0, 4, st));
         bang::TcTableArgs ta;
         ta.queries = dptr(0);
         ta.nq = nq; ta.d = ix->d; ta.M = ix->M;
         ta.off = ix->off;
-        ta.btiles = static_cast<const unsigned char *>(ix->tc_btiles.p);
+        ta.btiles = static_cast<const unsigned char *>(p.table_source == 2 ? ix->tc_btiles_tf32.p : ix->tc_btiles.p);
         ta.bfirst = static_cast<const uint32_t *>(ix->tc_bfirst.p);
         ta.cnorm = static_cast<const float *>(ix->tc_cnorm.p);
         ta.out = tb.p;
-        ta.out_bf16 = 1;
+        ta.out_bf16 = p.mode == 1 ? 1u : 0u;
+        ta.tf32 = p.table_source == 2 ? 1u : 0u;
         ta.err = static_cast<unsigned int *>(ix->tc_err.p);
         cudaError_t te = bang::launch_tc_tables(ta, ix->dtype, st);
         if (te != cudaSuccess) return fail(BANG_ECUDA, "table kernel launch failed: %s", cudaGetErrorString(te));
-        tables = static_cast<const uint16_t *>(tb.p);
+        tables = tb.p;
     } else if (p.table_source != 0) {
         return fail(BANG_EINVAL, "bang_search: unknown table_source %u", p.table_source);
     }
@@ -862,11 +889,12 @@ int bang_pq_tables(bang_index *ix, const void *queries, uint32_t nq, void *out, 
     ta.queries = queries;
     ta.nq = nq; ta.d = ix->d; ta.M = ix->M;
     ta.off = ix->off;
-    ta.btiles = static_cast<const unsigned char *>(ix->tc_btiles.p);
+    ta.btiles = static_cast<const unsigned char *>((out_bf16 & 2u) ? ix->tc_btiles_tf32.p : ix->tc_btiles.p);
     ta.bfirst = static_cast<const uint32_t *>(ix->tc_bfirst.p);
     ta.cnorm = static_cast<const float *>(ix->tc_cnorm.p);
     ta.out = out;
-    ta.out_bf16 = out_bf16 ? 1u : 0u;
+    ta.out_bf16 = (out_bf16 & 1u) ? 1u : 0u;
+    ta.tf32 = (out_bf16 & 2u) ? 1u : 0u;
     ta.err = static_cast<unsigned int *>(ix->tc_err.p);
     CUDA_TRY(cudaMemsetAsync(ix->tc_err.p, 0, 4, st));
     cudaError_t te = bang::launch_tc_tables(ta, ix->dtype, st);
@@ -972,6 +1000,7 @@ int bang_destroy(bang_index *ix)
         for (auto &kv : ix->work) kv.second.release();
         for (auto &kv : ix->tables) kv.second.release();
         ix->tc_btiles.release();
+        ix->tc_btiles_tf32.release();
         ix->tc_bfirst.release();
         ix->tc_cnorm.release();
         ix->tc_err.release();

@@ -85,7 +85,7 @@ struct SearchArgs {
     const uint32_t *order;
     unsigned int *queue;      // device counter, zero at launch; null: grid covers the queries
     uint32_t grid_mult;       // persistent grid = grid_mult x resident CTAs (>= 1)
-    const uint16_t *tables;   // BF16 mode: nq*M*256 precomputed tables (tensor cores), or null
+    const void *tables;       // BF16 or FP32 mode: nq*M*256 precomputed tables (tensor cores), or null
     const unsigned int *tables_err;  // set when the table kernel gave up
     unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
     const uint32_t *entry;    // device or null: per-query start node (null: every query starts at medoid)
@@ -646,11 +646,13 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         for (uint32_t w = lane; w < nwords; w += kWarp) bloom[w] = 0u;
         __syncwarp();
         bool table_failed = false;
-        if (MODE == kModeBF16 && a.tables) {             // precomputed on the tensor cores
+        if ((MODE == kModeBF16 || MODE == kModeF32) && a.tables) {   // precomputed on the tensor cores
+            constexpr uint32_t esz = MODE == kModeBF16 ? 2u : 4u;      // BF16 or FP32 entries
             table_failed = *a.tables_err != 0u;
-            const uint4 *src = reinterpret_cast<const uint4 *>(a.tables + static_cast<uint64_t>(q) * a.M * 256u);
+            const uint4 *src = reinterpret_cast<const uint4 *>(static_cast<const unsigned char *>(a.tables) +
+                                                               static_cast<uint64_t>(q) * a.M * 256u * esz);
             uint4 *dst = reinterpret_cast<uint4 *>(T);
-            for (uint32_t i = lane; i < a.M * 256u * 2u / 16u; i += kWarp) dst[i] = src[i];
+            for (uint32_t i = lane; i < a.M * 256u * esz / 16u; i += kWarp) dst[i] = src[i];
         } else if (kPQ) {
             build_table<MODE>(a, qv, offs, T, lo8, lane);
         }
