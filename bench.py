@@ -439,19 +439,27 @@ def large_workload(args, device):
 # early: request every neighbour's code row as soon as the node's row arrives
 # (early_codes; same results; measured faster with the FP32 and BF16 tables,
 # slower with the 8-bit table).
+def _form(name, mode, placement, lz, early, tsrc, what, rerank=0):
+    return dict(name=name, mode=mode, placement=placement, lz=lz, early=early, tsrc=tsrc,
+                rerank=rerank, what=what)
+
+
 LARGE_FORMS = [
-    ("fp32_hbm", 0, 3, 16, 1, 0, "FP32 PQ table (the paper's precision), graph and vectors in HBM (the "
-                                 "In-memory variant, §5.1)"),
-    ("bf16_hbm", 1, 3, 16, 1, 0, "BF16 PQ table (reduced precision) summed in FP32, graph and vectors "
-                                 "in HBM"),
-    ("q8_hbm", 3, 3, 15, 0, 0, "8-bit PQ table (reduced precision) summed in integers, graph and "
-                               "vectors in HBM"),
-    ("exact_hbm", 2, 3, 16, 0, 0, "Exact-distance variant (§5.2): exact distances in the loop, no "
-                                  "table and no re-rank, graph and vectors in HBM"),
-    ("fp32_tc_hbm", 0, 3, 16, 1, 1, "FP32 search on tables built by the tensor cores (three-way BF16 "
-                                    "splits, about FP32), graph and vectors in HBM"),
-    ("tf32_tc_hbm", 0, 3, 16, 1, 2, "TF32 tables: the tensor-core contraction with both operands "
-                                    "rounded to TF32 and FP32 accumulation, FP32 search, HBM"),
+    _form("fp32_hbm", 0, 3, 16, 1, 0, "FP32 PQ table (the paper's precision), graph and vectors in HBM "
+                                      "(the In-memory variant, §5.1)"),
+    _form("bf16_hbm", 1, 3, 16, 1, 0, "BF16 PQ table (reduced precision) summed in FP32, graph and "
+                                      "vectors in HBM"),
+    _form("q8_hbm", 3, 3, 15, 0, 0, "8-bit PQ table (reduced precision) summed in integers, graph and "
+                                    "vectors in HBM"),
+    _form("exact_hbm", 2, 3, 16, 0, 0, "Exact-distance variant (§5.2): exact distances in the loop, no "
+                                       "table and no re-rank, graph and vectors in HBM"),
+    _form("fp32_tc_hbm", 0, 3, 16, 1, 1, "FP32 search on tables built by the tensor cores (three-way "
+                                         "BF16 splits, about FP32), graph and vectors in HBM"),
+    _form("tf32_tc_hbm", 0, 3, 16, 1, 2, "TF32 tables: the tensor-core contraction with both operands "
+                                         "rounded to TF32 and FP32 accumulation, FP32 search, HBM"),
+    _form("fp32_staged_hbm", 0, 3, 16, 1, 0, "FP32 table with the re-rank staged as a separate kernel "
+                                             "after the search (§4.8), graph and vectors in HBM",
+          rerank=1),
 ]
 
 
@@ -498,11 +506,12 @@ def run_large(args):
 
     early = [0]                     # early_codes of the form being measured
     tsrc = [0]                      # table_source of the form being measured
+    rerank = [0]                    # re-rank of the form being measured (0 fused, 1 staged)
 
     def search(L, mode, lz, nsub=None, stats=False):
         p = bang.make_params(bloom_log2=lz, mode=mode, out_iters=iters if stats else None,
                              out_ndist=ndist if stats else None, early_codes=early[0],
-                             table_source=tsrc[0])
+                             table_source=tsrc[0], rerank=rerank[0])
         m = nsub or nq
         ix.search(q_dev[:m], K, L, ids[:m], dout[:m], p, stream=sptr)
 
@@ -548,33 +557,39 @@ def run_large(args):
 
     res = {}
     with ClockSampler(local) as clk:
-        for name, mode, pl, lz, ec, ts, what in LARGE_FORMS:
+        for f in LARGE_FORMS:
+            name, mode, pl, lz, ec, ts, what = (f["name"], f["mode"], f["placement"], f["lz"],
+                                                f["early"], f["tsrc"], f["what"])
             early[0] = ec
             tsrc[0] = ts
+            rerank[0] = f["rerank"]
             place(pl)
             L, sweep = operating_point(mode, lz)
             search(L, mode, lz, stats=True)
             stream.synchronize()
             r = rec_now()
-            derr = dist_error(ids.cpu().numpy().view(np.uint32), dout.cpu().numpy(), w["base"],
-                              w["queries"])
+            ids_np, dout_np = ids.cpu().numpy().view(np.uint32), dout.cpu().numpy()
+            derr = dist_error(ids_np, dout_np, w["base"], w["queries"])
+            digest = hash((ids_np.tobytes(), dout_np.tobytes()))
             it = iters.cpu().numpy().astype(np.int64)
             nd = ndist.cpu().numpy().astype(np.int64)
             value, ms, t_wall = timed(L, mode, lz, args.steps)
             res[name] = dict(form=name, what=what, mode=mode, placement=pl, lz=lz, early=ec, tsrc=ts,
-                             L=L, sweep=sweep,
+                             rerank=f["rerank"], L=L, sweep=sweep,
                              recall=round(r, 4), dist_error=derr, iters=it, ndist=nd, value=value,
-                             ms_per_step=ms, t_wall=t_wall)
+                             ms_per_step=ms, t_wall=t_wall, digest=digest)
     # sampled queries of the FP32, 8-bit and Exact-distance forms at their
     # operating points, bit for bit against the oracle on the same index
     import oracle
     oix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     sel = np.linspace(0, nq - 1, 16).astype(np.int64)
     parity = {}
-    for name, okw in (("fp32_hbm", {}), ("q8_hbm", {"q8": True}), ("exact_hbm", {"exact": True})):
+    for name, okw in (("fp32_hbm", {}), ("q8_hbm", {"q8": True}), ("exact_hbm", {"exact": True}),
+                      ("fp32_staged_hbm", {})):
         r = res[name]
         early[0] = r["early"]
         tsrc[0] = r["tsrc"]
+        rerank[0] = r["rerank"]
         search(r["L"], r["mode"], r["lz"], stats=True)
         stream.synchronize()
         o = oix.search(w["queries"][sel], K, r["L"], log2z=r["lz"], **okw)
@@ -591,6 +606,7 @@ def run_large(args):
     fp = res["fp32_hbm"]
     early[0] = fp["early"]
     tsrc[0] = fp["tsrc"]
+    rerank[0] = fp["rerank"]
     host = {}
     for name, pl, what in (("fp32_host", 0, "FP32 PQ table, graph and vectors read in place from "
                                            "page-locked host memory (the paper's placement, Alg. 2)"),
@@ -611,6 +627,7 @@ def run_large(args):
     # autotuned settings (table precision, Bloom size, L) for recall@10 >= 0.9 in HBM
     early[0] = 0
     tsrc[0] = 0
+    rerank[0] = 0
     t0 = time.perf_counter()
     try:
         tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
@@ -680,7 +697,7 @@ def run_large(args):
     ids_h = torch.empty((nq, K), dtype=torch.int32).pin_memory()
     dist_h = torch.empty((nq, K), dtype=torch.float32).pin_memory()
     hp = bang.make_params(bloom_log2=head["lz"], mode=head["mode"], early_codes=head["early"],
-                          table_source=head["tsrc"])
+                          table_source=head["tsrc"], rerank=head["rerank"])
     for _ in range(2):
         ix.search(q_host, K, head["L"], ids_h, dist_h, hp, stream=sptr)
     e2e_steps = max(3, min(args.steps, 10))
@@ -690,6 +707,7 @@ def run_large(args):
     e2e_s = (time.perf_counter() - t0) / e2e_steps
     early[0] = head["early"]
     tsrc[0] = head["tsrc"]
+    rerank[0] = head["rerank"]
     search(head["L"], head["mode"], head["lz"])
     stream.synchronize()
     assert (ids_h.numpy() == ids.cpu().numpy()).all()
@@ -747,6 +765,11 @@ def run_large(args):
         "q8_hbm": {"value": q8["value"], "L": q8["L"], "recall@%d" % K: q8["recall"]},
         "exact_hbm": {"value": res["exact_hbm"]["value"], "L": res["exact_hbm"]["L"],
                       "recall@%d" % K: res["exact_hbm"]["recall"]},
+        "rerank_ablation": {"fused_value": fp["value"], "staged_value": res["fp32_staged_hbm"]["value"],
+                            "staged_over_fused": res["fp32_staged_hbm"]["value"] / fp["value"],
+                            "L": fp["L"], "same_results": res["fp32_staged_hbm"]["digest"] == fp["digest"],
+                            "what": "FP32 table: re-rank fused into the loop vs staged as a separate "
+                                    "kernel over the recorded candidates (§4.8)"},
         "tensor_core_tables": {f: {"value": res[f]["value"], "L": res[f]["L"],
                                    "recall@%d" % K: res[f]["recall"],
                                    "recall_vs_fp32": round(res[f]["recall"] - fp["recall"], 4)}

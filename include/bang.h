@@ -111,6 +111,18 @@ typedef struct bang_search_params {
      * flight (used when R <= 64, d <= 128 and M <= 32, and without
      * BANG_NEIGHBOR_CODES; otherwise ignored).  Results do not depend on it. */
     uint32_t early_codes;
+    /* How the re-rank of §4.8 runs (modes 0, 1 and 3; mode 2 has none):
+     * 0 = fused into the loop (each expanded node's vector arrives with its
+     * row and its exact distance enters the top-k at once); 1 = staged, as the
+     * paper structures it: the search fetches no vectors and records every
+     * expanded node (the candidate set) in device scratch owned by the index,
+     * one list per query as long as the iteration cap (nq * iter_cap * 4
+     * bytes per stream; iter_cap 0 counts as 8*L + 64), then a separate
+     * kernel computes the candidates' exact distances and keeps the k
+     * nearest.  Both return the k smallest (distance, id) keys of the same
+     * candidates in the same arithmetic: the results are identical.  Not
+     * accepted by bang_search_batched_noalloc.  Any other value: BANG_EINVAL. */
+    uint32_t rerank;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,

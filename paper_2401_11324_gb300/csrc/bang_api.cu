@@ -21,6 +21,7 @@
 #include "bang.h"
 #include "adc_table_tc.h"
 #include "bang_internal.h"
+#include "rerank.h"
 #include "search_kernel.cuh"
 
 namespace {
@@ -248,6 +249,9 @@ struct bang_index {
     DevBuf tc_btiles_tf32;    // the same tiles with the centroids rounded to TF32
     bool tc_ok = false;
     std::map<cudaStream_t, DevBuf> tables;
+    // Staged re-rank: per-stream candidate lists (nq rows of the iteration
+    // cap) and their lengths.
+    std::map<cudaStream_t, DevBuf> cands;
 };
 
 namespace bang {
@@ -697,6 +701,9 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search: trace_cap is 0");
 
     if (p.mode > 3) return fail(BANG_EINVAL, "bang_search: unknown mode %u", p.mode);
+    if (p.rerank > 1) return fail(BANG_EINVAL, "bang_search: unknown rerank %u", p.rerank);
+    if (p.rerank == 1 && p.mode == 2)
+        return fail(BANG_EINVAL, "bang_search: mode 2 (exact distances) has no re-rank to stage");
     bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, ix->R, (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search: %u bytes of shared memory per query exceed 227 KB "
@@ -826,6 +833,15 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.trace = static_cast<uint32_t *>(dptr(6));
     a.trace_cap = p.trace_cap;
     a.phase_cycles = static_cast<unsigned long long *>(dptr(7));
+    if (p.rerank == 1) {       // staged re-rank: candidate lists sized by the iteration cap
+        const uint64_t cap = p.iter_cap ? p.iter_cap : 8ull * L + 64ull;
+        const size_t lists = ((size_t)nq * cap * 4 + 255) & ~size_t(255);
+        DevBuf &cb = ix->cands[st];
+        CUDA_TRY(cb.ensure(lists + (size_t)nq * 4));
+        a.cand = static_cast<uint32_t *>(cb.p);
+        a.cand_cap = (uint32_t)cap;
+        a.cand_n = reinterpret_cast<uint32_t *>(static_cast<char *>(cb.p) + lists);
+    }
 
     {
         // 4-element vector loads need rows that start on 16-byte boundaries
@@ -840,6 +856,26 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     else if (p.mode == 3) le = bang::launch_search_q8(a, ix->dtype, lay.total, st);
     else le = bang::launch_search_exact(a, ix->dtype, lay.total, st);
     if (le != cudaSuccess) return fail(BANG_ECUDA, "search kernel launch failed: %s", cudaGetErrorString(le));
+    if (a.cand) {
+        bang::RerankArgs ra;
+        std::memset(&ra, 0, sizeof ra);
+        ra.queries = a.queries;
+        ra.base = a.base;
+        ra.vstride = a.vstride;
+        ra.d = a.d;
+        ra.vec_ok = a.vec_ok;
+        ra.vecb_ok = a.vecb_ok;
+        ra.cand = a.cand;
+        ra.cand_cap = a.cand_cap;
+        ra.cand_n = a.cand_n;
+        ra.nq = nq; ra.k = k; ra.L = L;
+        ra.k_per_q = a.k_per_q;
+        ra.L_per_q = a.L_per_q;
+        ra.out_ids = a.out_ids;
+        ra.out_dist = a.out_dist;
+        le = bang::launch_rerank(ra, ix->dtype, st);
+        if (le != cudaSuccess) return fail(BANG_ECUDA, "re-rank kernel launch failed: %s", cudaGetErrorString(le));
+    }
     for (int i = 1; i < 8; ++i) {
         Slot &s = slots[i];
         if (s.user && !s.dev && !s.in)
@@ -999,6 +1035,7 @@ int bang_destroy(bang_index *ix)
         ix->base_hbm.release();
         for (auto &kv : ix->work) kv.second.release();
         for (auto &kv : ix->tables) kv.second.release();
+        for (auto &kv : ix->cands) kv.second.release();
         ix->tc_btiles.release();
         ix->tc_btiles_tf32.release();
         ix->tc_bfirst.release();
@@ -1118,6 +1155,8 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     }
     if (p.table_source != 0)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0 (tables need scratch)");
+    if (p.rerank != 0)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: rerank must be 0 (candidate lists need scratch)");
     bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: %u bytes of shared memory per query "

@@ -90,6 +90,14 @@ struct SearchArgs {
     unsigned long long *phase_cycles;  // device or null: nq*kPhases SM cycles per phase
     const uint32_t *entry;    // device or null: per-query start node (null: every query starts at medoid)
     uint32_t early_codes;     // request every neighbour's code row as soon as the row arrives (see CS)
+    // Staged re-rank (PQ modes): when `cand` is set the loop fetches no
+    // vectors and keeps no top-k; it records every expanded node, the
+    // candidate set of §4.8, in row q of `cand` (cand_cap >= the iteration
+    // cap, so no candidate is lost) and their number in cand_n[q], and
+    // rerank_kernel computes the exact distances and the top-k afterwards.
+    uint32_t *cand;
+    uint32_t cand_cap;
+    uint32_t *cand_n;
 };
 
 // Phases timed when SearchArgs::phase_cycles is set.
@@ -403,7 +411,7 @@ __device__ __forceinline__ void load_node(const SearchArgs &a, uint32_t u, int l
         uint32_t i = static_cast<uint32_t>(lane + kWarp * r);
         nd.nb[r] = i < W ? row[i] : kNone;
     }
-    if (WITH_VECTOR) {
+    if (WITH_VECTOR && !a.cand) {     // staged re-rank: the vectors are read after the search
         const E *x = static_cast<const E *>(a.base) + static_cast<uint64_t>(u) * a.vstride;
         load_share<DT, DCH>(x, a.d, a.vecb_ok != 0, lane, nd.x);
     }
@@ -628,6 +636,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 if (a.out_iters) a.out_iters[q] = 0;
                 if (a.out_status) a.out_status[q] = -1;
                 if (a.out_ndist) a.out_ndist[q] = 0;
+                if (a.cand_n) a.cand_n[q] = 0;
             }
             __syncwarp();
             continue;
@@ -700,6 +709,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 Lk[first] = ukey | 1ull;
                 if (a.trace && iters < a.trace_cap)
                     a.trace[static_cast<uint64_t>(q) * a.trace_cap + iters] = u;
+                if (a.cand && iters < a.cand_cap)
+                    a.cand[static_cast<uint64_t>(q) * a.cand_cap + iters] = u;
             }
             ++iters;
             if (u != cur) {  // the prefetched node is always u*; reload if not
@@ -920,7 +931,8 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
             clk.mark(kPhNext);
             // ---- re-rank candidate: exact distance of u* (§4.8), off the
             // critical path: the next node's lists are already requested
-            if (kPQ) {
+            // (staged re-rank: recorded above, ranked by rerank_kernel)
+            if (kPQ && !a.cand) {
                 const uint64_t e = make_key(exact_distance_bits<DT, DCH>(qs, xu), u);
                 if (regk) {
                     const uint32_t pos = __popc(__ballot_sync(0xFFFFFFFFu, ck < e));
@@ -1061,8 +1073,11 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         }
 
         // ---- output: re-ranked top-k (§4.8), or in the exact mode the first
-        // k worklist entries (Alg. 1's result); padded
-        if (!kPQ) {
+        // k worklist entries (Alg. 1's result); padded.  With the staged
+        // re-rank only the number of candidates.
+        if (kPQ && a.cand) {
+            if (lane == 0) a.cand_n[q] = iters < a.cand_cap ? iters : a.cand_cap;
+        } else if (!kPQ) {
             for (uint32_t i = lane; i < kstride; i += kWarp) {
                 const uint64_t o = static_cast<uint64_t>(q) * kstride + i;
                 if (i < nl && i < k) {

@@ -56,3 +56,36 @@ def test_null_and_range_checks_without_gpu(lib):
     assert lib.bang_destroy(None) == bang.BANG_OK
     assert lib.bang_create(0, None) == bang.BANG_EINVAL
     assert lib.bang_load_pq(None, 4, 2, None, None, 1) == bang.BANG_EINVAL
+
+
+def _header_fields(struct):
+    """(name, is_pointer, array_length) of each field of a struct in bang.h, in order."""
+    src = open(os.path.join(ROOT, "include", "bang.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (struct, struct), src, re.S).group(1)
+    out = []
+    for decl in body.split(";"):
+        decl = " ".join(decl.split())
+        if not decl:
+            continue
+        for item in decl.split(","):                # "uint32_t k_max, L_max"
+            f = re.search(r"(\*?) ?(\w+)(?:\[(\w+)\])?$", item.strip())
+            assert f, decl
+            out.append((f.group(2), f.group(1) == "*", f.group(3)))
+    return out
+
+
+@pytest.mark.parametrize("struct", ["bang_search_params", "bang_server_config", "bang_autotune_opts",
+                                    "bang_autotune_result", "bang_link_probe"])
+def test_binding_structs_follow_the_header(struct):
+    # the ctypes mirrors of the C structs: same fields, same order, pointers
+    # where the header has pointers (a missing or misplaced field would shift
+    # every later one)
+    want = _header_fields(struct)
+    got = getattr(bang, struct)._fields_
+    assert [n for n, _, _ in want] == [f[0] for f in got]
+    for (name, ptr, _), (_, ctype) in zip(want, got):
+        if ptr:
+            assert ctype in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(ctype, "contents"), name
+        else:
+            assert ctype not in (ctypes.c_void_p,), name

@@ -18,7 +18,7 @@ RTOL = 1e-5
 
 
 def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
-               placement=0, prefetch_depth=0, phases=False, early_codes=0):
+               placement=0, prefetch_depth=0, phases=False, early_codes=0, rerank=0):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     if placement:
@@ -39,7 +39,7 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
                          out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
                          mode=mode, prefetch_depth=prefetch_depth, out_phase_cycles=ph,
-                         early_codes=early_codes)
+                         early_codes=early_codes, rerank=rerank)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
@@ -589,4 +589,127 @@ def test_batched_invalid_rows_are_flagged(u8small):
     assert (ids[0] == o["ids"][0]).all()
     o5 = oracle_search(u8small, Q[[3]], 5, 64)
     assert (ids[3, :5] == o5["ids"][0]).all() and (ids[3, 5:] == bang.BANG_NONE).all()
+    ix.close()
+
+
+# ---- staged re-rank (§4.8 as a separate kernel after the search)
+
+def _same(g, ref, fields=("ids", "dist", "iters", "status", "ndist", "trace")):
+    for f in fields:
+        assert (g[f] == ref[f]).all(), (f, np.argwhere(g[f] != ref[f])[:5])
+
+
+@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("flags", [0, 3, 3 | 4, 16, 8])
+def test_staged_rerank_equals_fused_and_oracle(u8small, cfg1, mode, flags):
+    # the loop records its expanded nodes and a second kernel ranks them:
+    # the same visits, counts and results as the fused re-rank, and the
+    # oracle's ids and distances
+    for w, Q, L in ((u8small, u8small["queries"][:150], 64), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags)
+        g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags, rerank=1)
+        _same(g, ref)
+        o = oracle_search(w, Q, 10, L, trace_cap=400, q8=mode == 3, bf16=mode == 1)
+        assert (g["ids"] == o["ids"]).all() and (g["iters"] == o["iters"]).all()
+        fin = np.isfinite(o["dist"])
+        assert (g["dist"][fin] == o["dist"][fin]).all()
+
+
+@pytest.mark.parametrize("k,L", [(1, 1), (32, 64), (33, 80), (100, 256)])
+def test_staged_rerank_k_beyond_registers(u8small, k, L):
+    # k <= 32 keeps the top-k in registers, larger k in shared memory; L = k = 1 too
+    Q = u8small["queries"][:70]
+    ref = gpu_search(u8small, Q, k, L, trace_cap=0)
+    g = gpu_search(u8small, Q, k, L, rerank=1)
+    _same(g, ref, ("ids", "dist", "iters", "status", "ndist"))
+    o = oracle_search(u8small, Q, k, L)
+    assert (g["ids"] == o["ids"]).all()
+
+
+@pytest.mark.parametrize("shape", ["i8_d100_M30", "f32_d96_M48", "f32_d200_M50", "u8_d130_M26"])
+def test_staged_rerank_element_types_and_widths(shape):
+    # int8 (biased lanes), FP32 (the 32-lane summation order), d > 128 (four
+    # chunks per lane) and rows that are not 4-byte aligned
+    spec = {"i8_d100_M30": dict(n=6_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40, centre="uniform100"),
+            "f32_d96_M48": dict(n=5_000, nq=40, ncomp=4, dtype="f32", d=96, M=48, R=68, centre="uniform255"),
+            "f32_d200_M50": dict(n=4_000, nq=30, ncomp=4, dtype="f32", d=200, M=50, R=48, centre="uniform255"),
+            "u8_d130_M26": dict(n=4_000, nq=30, ncomp=4, dtype="u8", d=130, M=26, R=32, centre="uniform255")}[shape]
+    w = cases.clustered(**spec)
+    Q = w["queries"]
+    for mode in (0, 3):
+        ref = gpu_search(w, Q, 10, 48, trace_cap=300, mode=mode)
+        g = gpu_search(w, Q, 10, 48, trace_cap=300, mode=mode, rerank=1)
+        _same(g, ref)
+    o = oracle_search(w, Q, 10, 48)
+    g = gpu_search(w, Q, 10, 48, rerank=1)
+    assert (g["ids"] == o["ids"]).all()
+    fin = np.isfinite(o["dist"])
+    assert (g["dist"][fin] == o["dist"][fin]).all()
+
+
+def test_staged_rerank_iteration_cap_and_host_buffers(u8small):
+    # a capped search (status 1) keeps the candidates it expanded; host
+    # buffers are staged like the fused form's
+    Q = u8small["queries"][:50]
+    ref = gpu_search(u8small, Q, 10, 64, iter_cap=7)
+    g = gpu_search(u8small, Q, 10, 64, iter_cap=7, rerank=1)
+    _same(g, ref, ("ids", "dist", "iters", "status", "ndist"))
+    assert (g["status"] == 1).all()
+    gh = gpu_search(u8small, Q, 10, 64, host=True, rerank=1)
+    gd = gpu_search(u8small, Q, 10, 64)
+    _same(gh, gd, ("ids", "dist", "iters", "status", "ndist"))
+
+
+def test_staged_rerank_batched_uneven_k_and_L(u8small):
+    Q = u8small["queries"][:160]
+    k, L = _mixed_kl(len(Q), 12)
+    k[3], L[5] = 0, 2000                                  # two invalid rows
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    kmax, Lmax = 100, 256
+    out = []
+    for rr in (0, 1):
+        ids = np.zeros((len(Q), kmax), np.uint32)
+        dist = np.zeros((len(Q), kmax), np.float32)
+        status = np.zeros(len(Q), np.int32)
+        ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist,
+                          bang.make_params(out_status=status, rerank=rr))
+        out.append((ids, dist, status))
+    ix.close()
+    (i0, d0, s0), (i1, d1, s1) = out
+    assert (i0 == i1).all() and (s0 == s1).all()
+    assert (np.isfinite(d0) == np.isfinite(d1)).all() and (d0[np.isfinite(d0)] == d1[np.isfinite(d1)]).all()
+    assert s1[3] == -1 and s1[5] == -1 and (i1[3] == bang.BANG_NONE).all()
+    ok = np.array([i for i in range(len(Q)) if i not in (3, 5)])
+    ids_o, _, _ = _oracle_mixed(u8small, Q[ok], k[ok], L[ok])
+    assert (i1[ok, :ids_o.shape[1]] == ids_o).all()
+
+
+def test_staged_rerank_graph_capture_and_rejections(u8small):
+    Q = u8small["queries"][:64]
+    ref = gpu_search(u8small, Q, 10, 64)
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    q = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    ids = torch.zeros((64, 10), dtype=torch.int32, device="cuda")
+    dist = torch.zeros((64, 10), dtype=torch.float32, device="cuda")
+    s = torch.cuda.Stream()
+    p = bang.make_params(rerank=1)
+    ix.search(q, 10, 64, ids, dist, p, stream=s.cuda_stream)       # allocates the candidate lists
+    s.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ix.search(q, 10, 64, ids, dist, p, stream=s.cuda_stream)
+    for _ in range(2):
+        ids.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        assert (ids.cpu().numpy().view(np.uint32) == ref["ids"]).all()
+    for bad in (bang.make_params(rerank=2), bang.make_params(rerank=1, mode=bang.BANG_MODE_EXACT)):
+        with pytest.raises(bang.BangError):
+            ix.search(q, 10, 64, ids, dist, bad)
+    kd = torch.full((64,), 10, dtype=torch.int32, device="cuda")
+    Ld = torch.full((64,), 64, dtype=torch.int32, device="cuda")
+    with pytest.raises(bang.BangError):
+        bang.bang_search_batched_noalloc(ix.h, q, 64, kd, Ld, 10, 64, bang.make_params(rerank=1), ids, dist)
     ix.close()
