@@ -97,7 +97,13 @@ typedef struct bang_search_params {
      * splits, about FP32-accurate) into per-stream device scratch owned by the
      * index (nq*M*256 entries of 4 bytes in mode 0, 2 in mode 1), then read by
      * the search; 2 = the same with both operands rounded to TF32 (the
-     * numerics of a TF32 GEMM with FP32 accumulation: the TF32 table form). */
+     * numerics of a TF32 GEMM with FP32 accumulation: the TF32 table form);
+     * 3 = no table (mode 0 only): each FP32 entry a PQ distance needs is
+     * computed from the query and the codebook (read through the L1 cache)
+     * in the table build's own order, so results are bit-exact with
+     * table_source 0, while a query holds no M*256*4-byte table in shared
+     * memory and more queries are resident per SM.  Also accepted by
+     * bang_search_batched_noalloc. */
     uint32_t table_source;
     /* How many candidates for the next node are requested per iteration: 0
      * or 1 = the chosen one only, after the distances (§4.5's eager choice);
@@ -123,6 +129,11 @@ typedef struct bang_search_params {
      * candidates in the same arithmetic: the results are identical.  Not
      * accepted by bang_search_batched_noalloc.  Any other value: BANG_EINVAL. */
     uint32_t rerank;
+    /* Preferred share of each SM's unified L1/shared storage given to shared
+     * memory, in percent (1..100; 0 = the driver's choice; above 100:
+     * BANG_EINVAL).  A hint that trades resident queries against L1 capacity
+     * (the codebook, for table_source 3); results do not depend on it. */
+    uint32_t smem_carveout;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(CSRC, "libbang.so")
 SOURCES = ["bang_api.cu", "link_probe.cu", "server.cu", "adc_table_tc.cu", "search_f32.cu",
            "search_bf16.cu", "search_exact.cu", "search_q8.cu", "autotune.cu", "build_graph.cu", "build_pq.cu", "ground_truth.cu",
-           "build_shard.cu", "rerank.cu"]
+           "build_shard.cu", "rerank.cu", "search_f32lazy.cu"]
 HEADERS = ["search_kernel.cuh", "bang_internal.h", "adc_table_tc.h", "rerank.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -704,7 +704,11 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     if (p.rerank > 1) return fail(BANG_EINVAL, "bang_search: unknown rerank %u", p.rerank);
     if (p.rerank == 1 && p.mode == 2)
         return fail(BANG_EINVAL, "bang_search: mode 2 (exact distances) has no re-rank to stage");
-    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, ix->R, (int)p.mode);
+    if (p.smem_carveout > 100) return fail(BANG_EINVAL, "bang_search: smem_carveout %u above 100", p.smem_carveout);
+    if (p.table_source == 3 && p.mode != 0)
+        return fail(BANG_EINVAL, "bang_search: table_source 3 (no table) needs mode 0");
+    const bool lazy = p.table_source == 3;
+    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, ix->R, lazy ? (int)bang::kModeF32Lazy : (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search: %u bytes of shared memory per query exceed 227 KB "
                     "(reduce L, k, M or bloom_log2)", lay.total);
@@ -782,7 +786,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
         cudaError_t te = bang::launch_tc_tables(ta, ix->dtype, st);
         if (te != cudaSuccess) return fail(BANG_ECUDA, "table kernel launch failed: %s", cudaGetErrorString(te));
         tables = tb.p;
-    } else if (p.table_source != 0) {
+    } else if (p.table_source != 0 && p.table_source != 3) {
         return fail(BANG_EINVAL, "bang_search: unknown table_source %u", p.table_source);
     }
 
@@ -833,6 +837,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.trace = static_cast<uint32_t *>(dptr(6));
     a.trace_cap = p.trace_cap;
     a.phase_cycles = static_cast<unsigned long long *>(dptr(7));
+    a.carveout = p.smem_carveout;
     if (p.rerank == 1) {       // staged re-rank: candidate lists sized by the iteration cap
         const uint64_t cap = p.iter_cap ? p.iter_cap : 8ull * L + 64ull;
         const size_t lists = ((size_t)nq * cap * 4 + 255) & ~size_t(255);
@@ -851,7 +856,8 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
         a.vecb_ok = (ix->d % 4 == 0) && (ba % 16 == 0) ? 1u : 0u;
     }
     cudaError_t le;
-    if (p.mode == 0) le = bang::launch_search_f32(a, ix->dtype, lay.total, st);
+    if (lazy) le = bang::launch_search_f32lazy(a, ix->dtype, lay.total, st);
+    else if (p.mode == 0) le = bang::launch_search_f32(a, ix->dtype, lay.total, st);
     else if (p.mode == 1) le = bang::launch_search_bf16(a, ix->dtype, lay.total, st);
     else if (p.mode == 3) le = bang::launch_search_q8(a, ix->dtype, lay.total, st);
     else le = bang::launch_search_exact(a, ix->dtype, lay.total, st);
@@ -1153,11 +1159,15 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
                         "of the index's device %d (host buffers would need staging allocations)",
                         ix->device);
     }
-    if (p.table_source != 0)
-        return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0 (tables need scratch)");
+    if (p.table_source != 0 && !(p.table_source == 3 && p.mode == 0))
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: table_source must be 0, or 3 with mode 0 "
+                    "(tensor-core tables need scratch)");
     if (p.rerank != 0)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: rerank must be 0 (candidate lists need scratch)");
-    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, (int)p.mode);
+    if (p.smem_carveout > 100)
+        return fail(BANG_EINVAL, "bang_search_batched_noalloc: smem_carveout %u above 100", p.smem_carveout);
+    const bool lazy = p.table_source == 3;
+    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, lazy ? (int)bang::kModeF32Lazy : (int)p.mode);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: %u bytes of shared memory per query "
                     "exceed 227 KB", lay.total);
@@ -1213,11 +1223,13 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.grid_mult = p.grid_mult;
     a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
     a.early_codes = p.early_codes ? 1u : 0u;
+    a.carveout = p.smem_carveout;
     const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
     const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
     a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;
     a.vecb_ok = (ix->d % 4 == 0) && (ba % 16 == 0) ? 1u : 0u;
-    if (p.mode == 0) e = bang::launch_search_f32(a, ix->dtype, lay.total, st);
+    if (lazy) e = bang::launch_search_f32lazy(a, ix->dtype, lay.total, st);
+    else if (p.mode == 0) e = bang::launch_search_f32(a, ix->dtype, lay.total, st);
     else if (p.mode == 1) e = bang::launch_search_bf16(a, ix->dtype, lay.total, st);
     else if (p.mode == 3) e = bang::launch_search_q8(a, ix->dtype, lay.total, st);
     else e = bang::launch_search_exact(a, ix->dtype, lay.total, st);

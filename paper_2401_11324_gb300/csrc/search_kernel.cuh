@@ -27,6 +27,7 @@
 //    unsigned integers.
 #pragma once
 
+#include <atomic>
 #include <cstdint>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -51,7 +52,12 @@ constexpr int kRegK = 32;         // k up to this keeps the re-rank top-k in reg
 //  kModeQ8:    PQ distances from an 8-bit table (per-subspace offset, one
 //              scale per query) summed exactly in integers: a quarter of the
 //              FP32 table's shared memory; not in the paper
-enum { kModeF32 = 0, kModeBF16 = 1, kModeExact = 2, kModeQ8 = 3 };
+//  kModeF32Lazy: the FP32 form with no table: each entry a distance needs is
+//              computed from the query and the codebook (read through L1)
+//              in the table's own arithmetic, so the sums are kModeF32's bit
+//              for bit while a query holds no 32 KB table in shared memory
+//              and more queries fit on an SM
+enum { kModeF32 = 0, kModeBF16 = 1, kModeExact = 2, kModeQ8 = 3, kModeF32Lazy = 4 };
 
 struct SearchArgs {
     const void *queries;      // device, nq*d elements
@@ -98,6 +104,7 @@ struct SearchArgs {
     uint32_t *cand;
     uint32_t cand_cap;
     uint32_t *cand_n;
+    uint32_t carveout;        // preferred shared-memory share of L1 in percent (0: the driver's choice)
 };
 
 // Phases timed when SearchArgs::phase_cycles is set.
@@ -113,6 +120,7 @@ struct SmemLayout {
     {
         uint32_t o = 0;
         const uint32_t tsz = mode == kModeF32 ? 4u : mode == kModeBF16 ? 2u : mode == kModeQ8 ? 1u : 0u;
+        const bool lazy = mode == kModeF32Lazy;       // query and offsets stay live in the loop
         const uint32_t rw = (R + 31u) & ~31u;          // neighbour slots: whole lanes' worth
         off_T = o;      o += up16(M * 256u * tsz);
         off_bloom = o;  o += up16(((1u << log2z) / 8u) < 4u ? 4u : (1u << log2z) / 8u);
@@ -122,10 +130,10 @@ struct SmemLayout {
         off_Ck = o;     o += up16(k > (uint32_t)kRegK && mode != kModeExact ? k * 8u : 0u);
         // table-build scratch (query, subspace offsets, 8-bit-table minima):
         // dead once the table is built, so it shares the worklist's space
-        // when that is large enough
+        // when that is large enough (not without a table: the loop reads it)
         const uint32_t sq = up16(mode != kModeExact ? d * 4u : 0u), so = up16((M + 1u) * 4u),
                        sl = up16(mode == kModeQ8 ? M * 4u : 0u);
-        uint32_t b = up16(L * 8u) >= sq + so + sl ? off_L : o;
+        uint32_t b = !lazy && up16(L * 8u) >= sq + so + sl ? off_L : o;
         off_q = b;      b += sq;
         off_offs = b;   b += so;
         off_lo = b;     b += sl;
@@ -191,12 +199,53 @@ __device__ __forceinline__ uint64_t shfl_up_u64(uint64_t v, int delta)
     return (static_cast<uint64_t>(hi) << 32) | lo;
 }
 
-// Table entry as FP32: FP32 tables are read directly, BF16 entries widened.
-template <int MODE> __device__ __forceinline__ float table_entry(const void *T, uint32_t i)
+// Where a query's table entries come from: its table in shared memory, or,
+// without a table (kModeF32Lazy), the query, the subspace offsets and the
+// codebook, from which an entry is computed when a distance needs it.
+struct TableRef {
+    const void *T;              // the table (modes with one)
+    const float *qv;            // the query in FP32 (shared memory)
+    const uint32_t *offs;       // subspace offsets, M + 1 (shared memory)
+    const float *codebook;      // 256 centroids per subspace, subspace-major (global)
+    uint32_t ds;                // dimensions per subspace when all are equal, else 0
+};
+
+// Table entry T[s][c] as FP32: FP32 tables are read directly, BF16 entries
+// widened; without a table the entry is computed in the table build's
+// arithmetic (fmaf of the differences in ascending j, from 0), so it has
+// the bits the FP32 table would hold.
+template <int MODE> __device__ __forceinline__ float table_entry(const TableRef &t, uint32_t s, uint32_t c)
 {
-    if (MODE == kModeBF16)
-        return __uint_as_float(static_cast<uint32_t>(static_cast<const uint16_t *>(T)[i]) << 16);
-    return static_cast<const float *>(T)[i];
+    if constexpr (MODE == kModeBF16) {
+        return __uint_as_float(static_cast<uint32_t>(static_cast<const uint16_t *>(t.T)[s * 256u + c]) << 16);
+    } else if constexpr (MODE == kModeF32Lazy) {
+        uint32_t o, ds;
+        if (t.ds) {
+            ds = t.ds;
+            o = s * ds;
+        } else {
+            o = t.offs[s];
+            ds = t.offs[s + 1] - o;
+        }
+        const float *cc = t.codebook + 256u * o + c * ds;
+        float acc = 0.0f, df;
+        if (ds == 4 && (o & 3u) == 0) {
+            const float4 q4 = *reinterpret_cast<const float4 *>(t.qv + o);
+            const float4 c4 = __ldg(reinterpret_cast<const float4 *>(cc));
+            df = __fsub_rn(q4.x, c4.x); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q4.y, c4.y); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q4.z, c4.z); acc = __fmaf_rn(df, df, acc);
+            df = __fsub_rn(q4.w, c4.w); acc = __fmaf_rn(df, df, acc);
+        } else {
+            for (uint32_t j = 0; j < ds; ++j) {
+                df = __fsub_rn(t.qv[o + j], __ldg(cc + j));
+                acc = __fmaf_rn(df, df, acc);
+            }
+        }
+        return acc;
+    } else {
+        return static_cast<const float *>(t.T)[s * 256u + c];
+    }
 }
 
 // PQ distance of one code row on the 8-bit table: the exact integer sum of
@@ -226,8 +275,7 @@ __device__ __forceinline__ uint32_t adc_distance_q8(const uint8_t *__restrict__ 
 
 // PQ distance of one code row (§4.4), in the fixed order described above.
 template <int MODE, typename Get>
-__device__ __forceinline__ float adc_distance(const void *__restrict__ T, Get get, uint32_t M,
-                                              uint32_t Mpad)
+__device__ __forceinline__ float adc_distance(const TableRef &t, Get get, uint32_t M, uint32_t Mpad)
 {
     float p[8];
 #pragma unroll
@@ -235,16 +283,16 @@ __device__ __forceinline__ float adc_distance(const void *__restrict__ T, Get ge
     for (uint32_t c16 = 0; c16 < Mpad / 16u; ++c16) {
         uint4 v = get(c16);
         uint32_t w[4] = {v.x, v.y, v.z, v.w};
-        const uint32_t tc = c16 * 16u * 256u;
-        if (c16 * 16u + 16u <= M) {
+        const uint32_t s0 = c16 * 16u;
+        if (s0 + 16u <= M) {
 #pragma unroll
             for (int b = 0; b < 16; ++b)
-                p[b & 7] = __fadd_rn(p[b & 7], table_entry<MODE>(T, tc + b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)));
+                p[b & 7] = __fadd_rn(p[b & 7], table_entry<MODE>(t, s0 + b, (w[b >> 2] >> (8 * (b & 3))) & 0xFFu));
         } else {
 #pragma unroll
             for (int b = 0; b < 16; ++b)
-                if (c16 * 16u + b < M)
-                    p[b & 7] = __fadd_rn(p[b & 7], table_entry<MODE>(T, tc + b * 256 + ((w[b >> 2] >> (8 * (b & 3))) & 0xFFu)));
+                if (s0 + b < M)
+                    p[b & 7] = __fadd_rn(p[b & 7], table_entry<MODE>(t, s0 + b, (w[b >> 2] >> (8 * (b & 3))) & 0xFFu));
         }
     }
 #pragma unroll
@@ -264,20 +312,20 @@ __device__ __forceinline__ float adc_distance(const void *__restrict__ T, Get ge
 // Ordering bits of a PQ distance: FP32 distances (all >= +0) through their
 // bit patterns, 8-bit-table sums as integers.
 template <int MODE, typename Get>
-__device__ __forceinline__ uint32_t pq_dist_bits_g(const void *T, Get get, uint32_t M, uint32_t Mpad)
+__device__ __forceinline__ uint32_t pq_dist_bits_g(const TableRef &t, Get get, uint32_t M, uint32_t Mpad)
 {
     if constexpr (MODE == kModeQ8)
-        return adc_distance_q8(static_cast<const uint8_t *>(T), get, M, Mpad);
+        return adc_distance_q8(static_cast<const uint8_t *>(t.T), get, M, Mpad);
     else
-        return __float_as_uint(adc_distance<MODE>(T, get, M, Mpad));
+        return __float_as_uint(adc_distance<MODE>(t, get, M, Mpad));
 }
 
 template <int MODE>
-__device__ __forceinline__ uint32_t pq_dist_bits(const void *T, const uint8_t *row, uint32_t M,
+__device__ __forceinline__ uint32_t pq_dist_bits(const TableRef &t, const uint8_t *row, uint32_t M,
                                                  uint32_t Mpad)
 {
     const uint4 *row16 = reinterpret_cast<const uint4 *>(row);
-    return pq_dist_bits_g<MODE>(T, [row16](uint32_t c16) { return __ldg(row16 + c16); }, M, Mpad);
+    return pq_dist_bits_g<MODE>(t, [row16](uint32_t c16) { return __ldg(row16 + c16); }, M, Mpad);
 }
 
 // Part of an 8-bit-table PQ distance: the 8-byte chunks c = part, part + P,
@@ -662,10 +710,11 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                                                                static_cast<uint64_t>(q) * a.M * 256u * esz);
             uint4 *dst = reinterpret_cast<uint4 *>(T);
             for (uint32_t i = lane; i < a.M * 256u * esz / 16u; i += kWarp) dst[i] = src[i];
-        } else if (kPQ) {
+        } else if (kPQ && MODE != kModeF32Lazy) {
             build_table<MODE>(a, qv, offs, T, lo8, lane);
         }
         __syncwarp();
+        const TableRef tr{T, qv, offs, a.codebook, a.d % a.M == 0 ? a.d / a.M : 0u};
         clk.mark(kPhTable);
 
         // ---- start: worklist = {medoid}, medoid marked seen
@@ -680,7 +729,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         if (lane == 0) {
             const uint32_t s = s0;
             if (kPQ)
-                dm_bits = pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(s) * a.Mpad, a.M, a.Mpad);
+                dm_bits = pq_dist_bits<MODE>(tr, a.codes + static_cast<uint64_t>(s) * a.Mpad, a.M, a.Mpad);
             Lk[0] = make_key(dm_bits, s);
             uint32_t p1 = fnv1a32_id(s) & zmask, p2 = fnv1a64_id_folded(s) & zmask;
             bloom[p1 >> 5] |= 1u << (p1 & 31u);
@@ -799,7 +848,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 for (int r = 0; r < RPL; ++r) {
                     if (!fresh[r]) continue;
                     const uint4 c0 = nd.code[2 * r], c1 = nd.code[2 * r + 1];
-                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(T, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
+                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(tr, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
                                                                 a.M, a.Mpad), nd.nb[r]);
                 }
             } else if constexpr (CS == 2) {   // code rows requested before the filter
@@ -807,7 +856,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 for (int r = 0; r < RPL; ++r) {
                     if (!fresh[r]) continue;
                     const uint4 c0 = ec[2 * r], c1 = ec[2 * r + 1];
-                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(T, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
+                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(tr, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
                                                                 a.M, a.Mpad), nd.nb[r]);
                 }
             } else if (kPQ) {
@@ -822,7 +871,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                         const uint32_t j = lane + kWarp * t;
                         if (j < nn) {
                             const uint32_t id = Nid[j];
-                            kk[t] = make_key(pq_dist_bits<MODE>(T, a.codes + static_cast<uint64_t>(id) * a.Mpad,
+                            kk[t] = make_key(pq_dist_bits<MODE>(tr, a.codes + static_cast<uint64_t>(id) * a.Mpad,
                                                                 a.M, a.Mpad), id);
                             kv[t] = true;
                         }
@@ -1141,6 +1190,16 @@ cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
     cudaError_t e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, CS, PH>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
+    // the carve-out is a hint that stays with the function: set it when the
+    // request changes (back to the driver's choice, -1, when it is 0)
+    static std::atomic<uint32_t> carveout_set{0};
+    if (carveout_set.load() != a.carveout) {
+        e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, CS, PH>,
+                                 cudaFuncAttributePreferredSharedMemoryCarveout,
+                                 a.carveout ? static_cast<int>(a.carveout) : -1);
+        if (e != cudaSuccess) return e;
+        carveout_set.store(a.carveout);
+    }
     uint32_t grid = a.nq;
     if (a.queue) {                     // persistent: a multiple of the resident CTAs
         int dev = 0, sms = 0, per_sm = 0;
@@ -1195,5 +1254,6 @@ cudaError_t launch_search_f32(const SearchArgs &a, int dtype, size_t smem, cudaS
 cudaError_t launch_search_bf16(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 cudaError_t launch_search_exact(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 cudaError_t launch_search_q8(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
+cudaError_t launch_search_f32lazy(const SearchArgs &a, int dtype, size_t smem, cudaStream_t st);
 
 }  // namespace bang

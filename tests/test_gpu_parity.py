@@ -18,7 +18,8 @@ RTOL = 1e-5
 
 
 def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
-               placement=0, prefetch_depth=0, phases=False, early_codes=0, rerank=0):
+               placement=0, prefetch_depth=0, phases=False, early_codes=0, rerank=0, table_source=0,
+               carveout=0):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     if placement:
@@ -39,7 +40,8 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
     p = bang.make_params(bloom_log2=log2z, iter_cap=iter_cap, out_iters=iters, out_status=status,
                          out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
                          mode=mode, prefetch_depth=prefetch_depth, out_phase_cycles=ph,
-                         early_codes=early_codes, rerank=rerank)
+                         early_codes=early_codes, rerank=rerank, table_source=table_source,
+                         smem_carveout=carveout)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
@@ -712,4 +714,74 @@ def test_staged_rerank_graph_capture_and_rejections(u8small):
     Ld = torch.full((64,), 64, dtype=torch.int32, device="cuda")
     with pytest.raises(bang.BangError):
         bang.bang_search_batched_noalloc(ix.h, q, 64, kd, Ld, 10, 64, bang.make_params(rerank=1), ids, dist)
+    ix.close()
+
+
+# ---- FP32 form without a table (table_source 3): entries computed from the
+# codebook when a distance needs them, in the table build's arithmetic
+
+@pytest.mark.parametrize("flags,early", [(0, 0), (3, 1), (3, 0), (3 | 4, 1), (16, 1), (8, 0)])
+def test_table_free_fp32_equals_table_and_oracle(u8small, cfg1, flags, early):
+    for w, Q, L in ((u8small, u8small["queries"][:150], 64), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, placement=flags, early_codes=early)
+        g = gpu_search(w, Q, 10, L, trace_cap=400, placement=flags, early_codes=early, table_source=3)
+        _same(g, ref)
+        o = oracle_search(w, Q, 10, L, trace_cap=400)
+        assert_parity(g, o, trace_cap=400)
+
+
+@pytest.mark.parametrize("shape", ["i8_d100_M30", "f32_d96_M48", "f32_d200_M50", "u8_d130_M26"])
+def test_table_free_fp32_subspace_shapes(shape):
+    # uneven subspaces (offsets read per entry), 2, 4 and 5 dimensions per
+    # subspace, d > 128, rows that are not 4-byte aligned
+    spec = {"i8_d100_M30": dict(n=6_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40, centre="uniform100"),
+            "f32_d96_M48": dict(n=5_000, nq=40, ncomp=4, dtype="f32", d=96, M=48, R=68, centre="uniform255"),
+            "f32_d200_M50": dict(n=4_000, nq=30, ncomp=4, dtype="f32", d=200, M=50, R=48, centre="uniform255"),
+            "u8_d130_M26": dict(n=4_000, nq=30, ncomp=4, dtype="u8", d=130, M=26, R=32, centre="uniform255")}[shape]
+    w = cases.clustered(**spec)
+    Q = w["queries"]
+    g = gpu_search(w, Q, 10, 48, trace_cap=300, table_source=3)
+    _same(g, gpu_search(w, Q, 10, 48, trace_cap=300))
+    assert_parity(g, oracle_search(w, Q, 10, 48, trace_cap=300), trace_cap=300)
+
+
+@pytest.mark.parametrize("carveout", [0, 25, 60, 100])
+def test_carveout_hint_leaves_results_unchanged(u8small, carveout):
+    Q = u8small["queries"][:100]
+    ref = gpu_search(u8small, Q, 10, 64, trace_cap=300, placement=3)
+    for ts in (0, 3):
+        g = gpu_search(u8small, Q, 10, 64, trace_cap=300, placement=3, table_source=ts, carveout=carveout)
+        _same(g, ref)
+
+
+def test_table_free_fp32_long_lists_batched_and_noalloc(u8small, cfg1):
+    Q = cfg1["queries"][:20]
+    assert_parity(gpu_search(cfg1, Q, 64, 512, 17, trace_cap=900, table_source=3),
+                  oracle_search(cfg1, Q, 64, 512, 17, trace_cap=900), trace_cap=900)
+    Q = u8small["queries"][:160]
+    k, L = _mixed_kl(len(Q), 21)
+    ids_o, dist_o, iters_o = _oracle_mixed(u8small, Q, k, L)
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    kmax, Lmax = int(k.max()), int(L.max())
+    ids = np.zeros((len(Q), kmax), np.uint32)
+    dist = np.zeros((len(Q), kmax), np.float32)
+    iters = np.zeros(len(Q), np.uint32)
+    ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist,
+                      bang.make_params(out_iters=iters, table_source=3))
+    assert (ids == ids_o).all() and (iters == iters_o).all()
+    q = torch.from_numpy(np.ascontiguousarray(Q)).cuda()
+    kd = torch.from_numpy(k.view(np.int32)).cuda()
+    Ld = torch.from_numpy(L.view(np.int32)).cuda()
+    idd = torch.zeros((len(Q), kmax), dtype=torch.int32, device="cuda")
+    dd = torch.zeros((len(Q), kmax), dtype=torch.float32, device="cuda")
+    bang.bang_search_batched_noalloc(ix.h, q, len(Q), kd, Ld, kmax, Lmax,
+                                     bang.make_params(table_source=3, smem_carveout=50), idd, dd)
+    torch.cuda.synchronize()
+    assert (idd.cpu().numpy().view(np.uint32) == ids_o).all()
+    for bad in (bang.make_params(table_source=3, mode=bang.BANG_MODE_PQ_BF16),
+                bang.make_params(table_source=3, mode=bang.BANG_MODE_PQ_Q8),
+                bang.make_params(smem_carveout=101), bang.make_params(table_source=4)):
+        with pytest.raises(bang.BangError):
+            ix.search(q, 10, 64, idd[:, :10].contiguous(), dd[:, :10].contiguous(), bad)
     ix.close()
