@@ -102,8 +102,8 @@ typedef struct bang_search_params {
      * computed from the query and the codebook (read through the L1 cache)
      * in the table build's own order, so results are bit-exact with
      * table_source 0, while a query holds no M*256*4-byte table in shared
-     * memory and more queries are resident per SM.  Also accepted by
-     * bang_search_batched_noalloc. */
+     * memory and more queries are resident per SM (table_subspaces below
+     * keeps part of the table).  Also accepted by bang_search_batched_noalloc. */
     uint32_t table_source;
     /* How many candidates for the next node are requested per iteration: 0
      * or 1 = the chosen one only, after the distances (§4.5's eager choice);
@@ -134,6 +134,12 @@ typedef struct bang_search_params {
      * BANG_EINVAL).  A hint that trades resident queries against L1 capacity
      * (the codebook, for table_source 3); results do not depend on it. */
     uint32_t smem_carveout;
+    /* With table_source 3: how many subspaces, the first ones, keep their
+     * FP32 entries in shared memory (table_subspaces*256*4 bytes per query);
+     * the others are computed when needed.  0 = none; M or more = all (the
+     * table form's memory, computed the same way).  Results do not depend
+     * on it (bit-exact with mode 0). */
+    uint32_t table_subspaces;
 } bang_search_params;
 
 typedef enum { BANG_MODE_PQ_F32 = 0, BANG_MODE_PQ_BF16 = 1, BANG_MODE_EXACT = 2,

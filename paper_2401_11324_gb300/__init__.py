@@ -37,7 +37,7 @@ class bang_search_params(ctypes.Structure):
                 ("mode", ctypes.c_uint32), ("grid_mult", ctypes.c_uint32),
                 ("table_source", ctypes.c_uint32), ("prefetch_depth", ctypes.c_uint32),
                 ("early_codes", ctypes.c_uint32), ("rerank", ctypes.c_uint32),
-                ("smem_carveout", ctypes.c_uint32)]
+                ("smem_carveout", ctypes.c_uint32), ("table_subspaces", ctypes.c_uint32)]
 
 
 class bang_link_probe(ctypes.Structure):
@@ -191,11 +191,12 @@ BANG_NODE_RECORDS = 16
 
 def make_params(bloom_log2=0, iter_cap=0, out_iters=None, out_status=None, out_ndist=None,
                 trace=None, trace_cap=0, out_phase_cycles=None, mode=0, grid_mult=0,
-                table_source=0, prefetch_depth=0, early_codes=0, rerank=0, smem_carveout=0):
+                table_source=0, prefetch_depth=0, early_codes=0, rerank=0, smem_carveout=0,
+                table_subspaces=0):
     return bang_search_params(bloom_log2, iter_cap, _ptr(out_iters), _ptr(out_status),
                               _ptr(out_ndist), _ptr(trace), trace_cap, _ptr(out_phase_cycles), mode,
                               grid_mult, table_source, prefetch_depth, early_codes, rerank,
-                              smem_carveout)
+                              smem_carveout, table_subspaces)
 
 
 def bang_search(ix, queries, nq, k, L, params, out_ids, out_dist, stream=None):

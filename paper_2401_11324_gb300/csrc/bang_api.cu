@@ -708,7 +708,8 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     if (p.table_source == 3 && p.mode != 0)
         return fail(BANG_EINVAL, "bang_search: table_source 3 (no table) needs mode 0");
     const bool lazy = p.table_source == 3;
-    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, ix->R, lazy ? (int)bang::kModeF32Lazy : (int)p.mode);
+    const uint32_t ntab = lazy ? std::min(p.table_subspaces, ix->M) : 0u;
+    bang::SmemLayout lay(ix->M, log2z, L, k, ix->d, ix->R, lazy ? (int)bang::kModeF32Lazy : (int)p.mode, ntab);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search: %u bytes of shared memory per query exceed 227 KB "
                     "(reduce L, k, M or bloom_log2)", lay.total);
@@ -838,6 +839,7 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.trace_cap = p.trace_cap;
     a.phase_cycles = static_cast<unsigned long long *>(dptr(7));
     a.carveout = p.smem_carveout;
+    a.ntab = ntab;
     if (p.rerank == 1) {       // staged re-rank: candidate lists sized by the iteration cap
         const uint64_t cap = p.iter_cap ? p.iter_cap : 8ull * L + 64ull;
         const size_t lists = ((size_t)nq * cap * 4 + 255) & ~size_t(255);
@@ -1167,7 +1169,9 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     if (p.smem_carveout > 100)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: smem_carveout %u above 100", p.smem_carveout);
     const bool lazy = p.table_source == 3;
-    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, lazy ? (int)bang::kModeF32Lazy : (int)p.mode);
+    const uint32_t ntab = lazy ? std::min(p.table_subspaces, ix->M) : 0u;
+    bang::SmemLayout lay(ix->M, log2z, L_max, k_max, ix->d, ix->R, lazy ? (int)bang::kModeF32Lazy : (int)p.mode,
+                         ntab);
     if (lay.total > 227u * 1024u)
         return fail(BANG_EINVAL, "bang_search_batched_noalloc: %u bytes of shared memory per query "
                     "exceed 227 KB", lay.total);
@@ -1224,6 +1228,7 @@ int bang_search_batched_noalloc(bang_index *ix, const void *queries, uint32_t nq
     a.spec = p.prefetch_depth >= 2 ? 1u : 0u;
     a.early_codes = p.early_codes ? 1u : 0u;
     a.carveout = p.smem_carveout;
+    a.ntab = ntab;
     const uintptr_t qa = reinterpret_cast<uintptr_t>(a.queries);
     const uintptr_t ba = reinterpret_cast<uintptr_t>(a.base);
     a.vec_ok = (ix->d % 4 == 0) && (qa % 16 == 0) ? 1u : 0u;

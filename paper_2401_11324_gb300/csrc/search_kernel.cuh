@@ -52,11 +52,12 @@ constexpr int kRegK = 32;         // k up to this keeps the re-rank top-k in reg
 //  kModeQ8:    PQ distances from an 8-bit table (per-subspace offset, one
 //              scale per query) summed exactly in integers: a quarter of the
 //              FP32 table's shared memory; not in the paper
-//  kModeF32Lazy: the FP32 form with no table: each entry a distance needs is
-//              computed from the query and the codebook (read through L1)
-//              in the table's own arithmetic, so the sums are kModeF32's bit
-//              for bit while a query holds no 32 KB table in shared memory
-//              and more queries fit on an SM
+//  kModeF32Lazy: the FP32 form with a partial table or none: the first ntab
+//              subspaces' entries are kept in shared memory, every other
+//              entry a distance needs is computed from the query and the
+//              codebook (read through L1) in the table's own arithmetic, so
+//              the sums are kModeF32's bit for bit while a query holds less
+//              than the 32 KB table and more queries fit on an SM
 enum { kModeF32 = 0, kModeBF16 = 1, kModeExact = 2, kModeQ8 = 3, kModeF32Lazy = 4 };
 
 struct SearchArgs {
@@ -105,6 +106,7 @@ struct SearchArgs {
     uint32_t cand_cap;
     uint32_t *cand_n;
     uint32_t carveout;        // preferred shared-memory share of L1 in percent (0: the driver's choice)
+    uint32_t ntab;            // kModeF32Lazy: subspaces (the first ones) whose entries stay in a table
 };
 
 // Phases timed when SearchArgs::phase_cycles is set.
@@ -115,14 +117,16 @@ enum Phase { kPhTable = 0, kPhSelect, kPhFilter, kPhDistance, kPhNext, kPhRerank
 struct SmemLayout {
     uint32_t off_T, off_bloom, off_L, off_Nk, off_Nid, off_Ck, off_q, off_offs, off_lo, total;
     __host__ __device__ static uint32_t up16(uint32_t x) { return (x + 15u) & ~15u; }
+    // ntab: kModeF32Lazy only, the subspaces whose FP32 entries are kept
     __host__ __device__ SmemLayout(uint32_t M, uint32_t log2z, uint32_t L, uint32_t k, uint32_t d,
-                                   uint32_t R, int mode)
+                                   uint32_t R, int mode, uint32_t ntab = 0)
     {
         uint32_t o = 0;
-        const uint32_t tsz = mode == kModeF32 ? 4u : mode == kModeBF16 ? 2u : mode == kModeQ8 ? 1u : 0u;
         const bool lazy = mode == kModeF32Lazy;       // query and offsets stay live in the loop
+        const uint32_t tsz = mode == kModeF32 || lazy ? 4u : mode == kModeBF16 ? 2u : mode == kModeQ8 ? 1u : 0u;
+        const uint32_t tsub = lazy ? (ntab < M ? ntab : M) : M;
         const uint32_t rw = (R + 31u) & ~31u;          // neighbour slots: whole lanes' worth
-        off_T = o;      o += up16(M * 256u * tsz);
+        off_T = o;      o += up16(tsub * 256u * tsz);
         off_bloom = o;  o += up16(((1u << log2z) / 8u) < 4u ? 4u : (1u << log2z) / 8u);
         off_L = o;      o += up16(L * 8u);
         off_Nk = o;     o += up16(rw * 8u);
@@ -208,6 +212,7 @@ struct TableRef {
     const uint32_t *offs;       // subspace offsets, M + 1 (shared memory)
     const float *codebook;      // 256 centroids per subspace, subspace-major (global)
     uint32_t ds;                // dimensions per subspace when all are equal, else 0
+    uint32_t ntab;              // kModeF32Lazy: subspaces s < ntab read from T (FP32)
 };
 
 // Table entry T[s][c] as FP32: FP32 tables are read directly, BF16 entries
@@ -219,6 +224,7 @@ template <int MODE> __device__ __forceinline__ float table_entry(const TableRef 
     if constexpr (MODE == kModeBF16) {
         return __uint_as_float(static_cast<uint32_t>(static_cast<const uint16_t *>(t.T)[s * 256u + c]) << 16);
     } else if constexpr (MODE == kModeF32Lazy) {
+        if (s < t.ntab) return static_cast<const float *>(t.T)[s * 256u + c];
         uint32_t o, ds;
         if (t.ds) {
             ds = t.ds;
@@ -566,7 +572,8 @@ __device__ __forceinline__ void subspace_entries(const SearchArgs &a, const floa
 // patterns order like their values.
 template <int MODE>
 __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv,
-                                            const uint32_t *offs, void *T, float *lo, int lane)
+                                            const uint32_t *offs, void *T, float *lo, int lane,
+                                            uint32_t nsub)
 {
     float v[8];
     if constexpr (MODE == kModeQ8) {
@@ -603,7 +610,7 @@ __device__ __forceinline__ void build_table(const SearchArgs &a, const float *qv
             }
         }
     } else {
-        for (uint32_t s = 0; s < a.M; ++s) {
+        for (uint32_t s = 0; s < nsub; ++s) {       // nsub < M: the first nsub subspaces only
             subspace_entries(a, qv, offs, s, lane, v);
             unsigned char *Ts = static_cast<unsigned char *>(T) + s * 256u * (MODE == kModeBF16 ? 2u : 4u);
 #pragma unroll
@@ -643,7 +650,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
     constexpr bool NC = CS == 1;
     extern __shared__ __align__(16) unsigned char smem[];
     const int lane = threadIdx.x;
-    const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d, a.R, MODE);
+    const SmemLayout lay(a.M, a.log2z, a.L, a.k, a.d, a.R, MODE, a.ntab);
     void *T = smem + lay.off_T;
     uint32_t *bloom = reinterpret_cast<uint32_t *>(smem + lay.off_bloom);
     uint64_t *Lk = reinterpret_cast<uint64_t *>(smem + lay.off_L);
@@ -710,11 +717,14 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                                                                static_cast<uint64_t>(q) * a.M * 256u * esz);
             uint4 *dst = reinterpret_cast<uint4 *>(T);
             for (uint32_t i = lane; i < a.M * 256u * esz / 16u; i += kWarp) dst[i] = src[i];
-        } else if (kPQ && MODE != kModeF32Lazy) {
-            build_table<MODE>(a, qv, offs, T, lo8, lane);
+        } else if (MODE == kModeF32Lazy) {             // the kept subspaces' entries, in FP32
+            build_table<kModeF32>(a, qv, offs, T, lo8, lane, a.ntab < a.M ? a.ntab : a.M);
+        } else if (kPQ) {
+            build_table<MODE>(a, qv, offs, T, lo8, lane, a.M);
         }
         __syncwarp();
-        const TableRef tr{T, qv, offs, a.codebook, a.d % a.M == 0 ? a.d / a.M : 0u};
+        const TableRef tr{T, qv, offs, a.codebook, a.d % a.M == 0 ? a.d / a.M : 0u,
+                          MODE == kModeF32Lazy ? a.ntab : a.M};
         clk.mark(kPhTable);
 
         // ---- start: worklist = {medoid}, medoid marked seen

@@ -19,7 +19,7 @@ RTOL = 1e-5
 
 def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None, mode=0,
                placement=0, prefetch_depth=0, phases=False, early_codes=0, rerank=0, table_source=0,
-               carveout=0):
+               carveout=0, table_subspaces=0):
     M = M or w["M"]
     ix = bang.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     if placement:
@@ -41,7 +41,7 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
                          out_ndist=ndist, trace=trace if trace_cap else None, trace_cap=trace_cap,
                          mode=mode, prefetch_depth=prefetch_depth, out_phase_cycles=ph,
                          early_codes=early_codes, rerank=rerank, table_source=table_source,
-                         smem_carveout=carveout)
+                         smem_carveout=carveout, table_subspaces=table_subspaces)
     ix.search(q, k, L, ids, dist, p)
     torch.cuda.synchronize()
     out = dict(ids=ids.cpu().numpy().view(np.uint32), dist=dist.cpu().numpy(),
@@ -785,3 +785,25 @@ def test_table_free_fp32_long_lists_batched_and_noalloc(u8small, cfg1):
         with pytest.raises(bang.BangError):
             ix.search(q, 10, 64, idd[:, :10].contiguous(), dd[:, :10].contiguous(), bad)
     ix.close()
+
+
+@pytest.mark.parametrize("ntab", [1, 8, 16, 31, 32, 40])
+def test_partial_table_equals_table_and_oracle(u8small, cfg1, ntab):
+    # the first ntab subspaces from the table, the others computed: the same
+    # bits as the whole table (ntab >= M is the whole table)
+    for w, Q in ((u8small, u8small["queries"][:120]), (cfg1, cfg1["queries"])):
+        for early in (0, 1):
+            ref = gpu_search(w, Q, 10, 64, trace_cap=400, placement=3, early_codes=early)
+            g = gpu_search(w, Q, 10, 64, trace_cap=400, placement=3, early_codes=early, table_source=3,
+                           table_subspaces=ntab)
+            _same(g, ref)
+    o = oracle_search(cfg1, cfg1["queries"], 10, 64, trace_cap=400)
+    assert_parity(g, o, trace_cap=400)
+
+
+def test_partial_table_uneven_subspaces():
+    w = cases.clustered(n=6_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40, centre="uniform100")
+    Q = w["queries"]
+    ref = gpu_search(w, Q, 10, 48, trace_cap=300)
+    for ntab in (7, 10, 29):
+        _same(gpu_search(w, Q, 10, 48, trace_cap=300, table_source=3, table_subspaces=ntab), ref)
