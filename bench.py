@@ -688,8 +688,10 @@ def run_large(args):
                         % ", ".join(str(x) for x in lmix), **brec}
     del graph
 
-    # the headline: the fastest FP32-table form reaching the target recall
-    head = fp
+    # the headline: the faster of the two FP32-table forms (re-rank fused or
+    # staged: the same results), at the operating point of the target recall
+    st_ = res["fp32_staged_hbm"]
+    head = st_ if st_["value"] > fp["value"] and st_["digest"] == fp["digest"] else fp
     it, nd = head["iters"], head["ndist"]
     launch_s = head["ms_per_step"] / 1e3
     # end to end through the C ABI: pinned host queries and results
@@ -794,7 +796,7 @@ def run_large(args):
         "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": workload_name(args), "form": head["form"], "form_what": head["what"],
                    "L": head["L"], "recall@%d" % K: head["recall"], "k": K, "bloom_log2": head["lz"],
-                   "early_codes": head["early"],
+                   "early_codes": head["early"], "rerank": "staged" if head["rerank"] else "fused",
                    "mean_iterations": float(it.mean()), "mean_pq_distances": float(nd.mean()),
                    "n": n, "nq": nq, "parallelism": "replica per GPU" if world > 1 else "single GPU",
                    "l2": "512 MB flush written between timed steps; the index (77 GB) is larger "
@@ -831,7 +833,7 @@ def run_large(args):
                               % row_bytes},
         "e2e": {"value": nq / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": nq * d * esz,
                 "d2h_bytes_per_step": nq * K * 8},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * (2 if head["rerank"] else 1),   # search (+ re-rank) per step
         "clocks": clk.summary(),
         "wall_s_timed_region": sum(r["t_wall"] for r in res.values()),
     }

@@ -107,9 +107,130 @@ __global__ void __launch_bounds__(kRerankWarps * kWarp) rerank_kernel(const Rera
     }
 }
 
+// 64-bit key exchange across lanes at xor distance j.
+__device__ __forceinline__ uint64_t shfl_xor_u64(uint64_t v, int j)
+{
+    const uint32_t lo = __shfl_xor_sync(0xFFFFFFFFu, static_cast<uint32_t>(v), j);
+    const uint32_t hi = __shfl_xor_sync(0xFFFFFFFFu, static_cast<uint32_t>(v >> 32), j);
+    return (static_cast<uint64_t>(hi) << 32) | lo;
+}
+
+// Ascending bitonic sort of one key per lane (lane i ends with rank i).
+__device__ __forceinline__ uint64_t warp_sort_keys(uint64_t v, int lane)
+{
+#pragma unroll
+    for (int size = 2; size <= kWarp; size <<= 1) {
+        const bool up = (lane & size) == 0;          // segment sorted ascending
+#pragma unroll
+        for (int j = size >> 1; j > 0; j >>= 1) {
+            const uint64_t o = shfl_xor_u64(v, j);
+            const bool keep_min = ((lane & j) == 0) == up;
+            v = keep_min ? (o < v ? o : v) : (o > v ? o : v);
+        }
+    }
+    return v;
+}
+
+// Integer vectors (u8, int8) with d a multiple of 16 up to 128 and k <= 32:
+// exact distances are integer sums, equal in any order, so one lane takes one
+// candidate's whole row (up to eight 16-byte loads, 32 rows in flight per
+// warp and two batches requested at once); a batch's 32 keys are sorted and
+// merged into the running top 32 (lane i holds rank i): the element-wise
+// minimum of the top list and the reversed batch holds the 32 smallest keys of
+// both as a bitonic sequence, which five exchange steps sort.  The k smallest
+// keys of the candidate set come out, as in the warp-per-candidate kernel.
+template <int DT>
+__global__ void __launch_bounds__(kRerankWarps * kWarp) rerank_lanes_kernel(const RerankArgs a)
+{
+    __shared__ uint4 qsm[kRerankWarps][8];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    const uint32_t kstride = a.k, nw16 = a.d / 16u;
+    const uint32_t bias = DT == 1 ? 0x80808080u : 0u;    // int8: bytes biased, differences unsigned
+    for (uint32_t q = blockIdx.x * kRerankWarps + wid; q < a.nq; q += gridDim.x * kRerankWarps) {
+        const uint32_t k = a.k_per_q ? a.k_per_q[q] : a.k;
+        const uint32_t L = a.L_per_q ? a.L_per_q[q] : a.L;
+        if (k == 0 || k > a.k || L < k || L > a.L) continue;    // padded by the search
+        const uint32_t n = a.cand_n[q];
+        const uint32_t *cq = a.cand + static_cast<uint64_t>(q) * a.cand_cap;
+        {   // the query's words, biased like the rows (byte loads: any alignment)
+            const uint8_t *qb = static_cast<const uint8_t *>(a.queries) + static_cast<uint64_t>(q) * a.d;
+            uint32_t w = 0;
+            if (static_cast<uint32_t>(lane) * 4u < a.d)
+                w = (static_cast<uint32_t>(qb[4 * lane]) | static_cast<uint32_t>(qb[4 * lane + 1]) << 8 |
+                     static_cast<uint32_t>(qb[4 * lane + 2]) << 16 | static_cast<uint32_t>(qb[4 * lane + 3]) << 24) ^ bias;
+            reinterpret_cast<uint32_t *>(qsm[wid])[lane] = w;
+        }
+        __syncwarp();
+        uint64_t top = ~0ull;
+        for (uint32_t c0 = 0; c0 < n; c0 += 2 * kWarp) {
+            uint4 row[2][8];
+            uint32_t id[2];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const uint32_t i = c0 + h * kWarp + lane;
+                id[h] = i < n ? cq[i] : kNone;
+                const uint4 *rp = reinterpret_cast<const uint4 *>(static_cast<const uint8_t *>(a.base) +
+                                                                  static_cast<uint64_t>(id[h] == kNone ? 0u : id[h]) * a.vstride);
+#pragma unroll
+                for (int c = 0; c < 8; ++c)
+                    row[h][c] = (id[h] != kNone && static_cast<uint32_t>(c) < nw16) ? __ldg(rp + c)
+                                                                                  : make_uint4(0u, 0u, 0u, 0u);
+            }
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                if (c0 + h * kWarp >= n) break;                       // warp-uniform
+                uint32_t acc = 0;
+#pragma unroll
+                for (int c = 0; c < 8; ++c) {
+                    if (static_cast<uint32_t>(c) >= nw16) break;
+                    const uint4 qv = qsm[wid][c];
+                    const uint32_t xw[4] = {row[h][c].x ^ bias, row[h][c].y ^ bias, row[h][c].z ^ bias,
+                                            row[h][c].w ^ bias};
+                    const uint32_t qw[4] = {qv.x, qv.y, qv.z, qv.w};
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const uint32_t df = __vabsdiffu4(qw[i], xw[i]);
+                        acc = __dp4a(df, df, acc);
+                    }
+                }
+                uint64_t key = id[h] != kNone ? make_key(acc, id[h]) : ~0ull;
+                key = warp_sort_keys(key, lane);
+                const uint64_t rev = shfl_u64(key, kWarp - 1 - lane);
+                uint64_t m = rev < top ? rev : top;
+#pragma unroll
+                for (int j = kWarp / 2; j > 0; j >>= 1) {
+                    const uint64_t o = shfl_xor_u64(m, j);
+                    m = (lane & j) == 0 ? (o < m ? o : m) : (o > m ? o : m);
+                }
+                top = m;
+            }
+        }
+        const uint32_t nc = n < k ? n : k;
+        for (uint32_t i = lane; i < kstride; i += kWarp) {
+            const uint64_t o = static_cast<uint64_t>(q) * kstride + i;
+            if (i < nc) {                   // nc <= k <= 32: rank i is lane i's key
+                a.out_ids[o] = key_id(top);
+                a.out_dist[o] = static_cast<float>(static_cast<uint32_t>(top >> 32));
+            } else {
+                a.out_ids[o] = kNone;
+                a.out_dist[o] = __uint_as_float(0x7F800000u);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 template <int DT, int DCH>
 cudaError_t launch_dt(const RerankArgs &a, cudaStream_t st)
 {
+    if constexpr (DT != 2 && DCH == 1) {
+        // rows reachable with 16-byte loads; k within one lane per rank
+        if (a.d % 16u == 0 && a.k <= static_cast<uint32_t>(kRegK) && a.vecb_ok && a.vstride % 16u == 0) {
+            const uint32_t blocks = (a.nq + kRerankWarps - 1) / kRerankWarps;
+            rerank_lanes_kernel<DT><<<blocks, kRerankWarps * kWarp, 0, st>>>(a);
+            return cudaGetLastError();
+        }
+    }
     const uint32_t blocks = (a.nq + kRerankWarps - 1) / kRerankWarps;
     rerank_kernel<DT, DCH><<<blocks, kRerankWarps * kWarp, 0, st>>>(a);
     return cudaGetLastError();

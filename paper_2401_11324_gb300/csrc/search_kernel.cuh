@@ -862,12 +862,49 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                                                                 a.M, a.Mpad), nd.nb[r]);
                 }
             } else if constexpr (CS == 2) {   // code rows requested before the filter
+                // compacted: new neighbour j goes to lane j % 32, which takes
+                // its code row from the lane that loaded it (shuffles), so a
+                // pass computes up to 32 distances instead of one per slot
+                in_regs = true;
+                uint32_t *src = reinterpret_cast<uint32_t *>(Nk);    // scratch until the keys
 #pragma unroll
-                for (int r = 0; r < RPL; ++r) {
-                    if (!fresh[r]) continue;
-                    const uint4 c0 = ec[2 * r], c1 = ec[2 * r + 1];
-                    Nk[slot[r]] = make_key(pq_dist_bits_g<MODE>(tr, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
-                                                                a.M, a.Mpad), nd.nb[r]);
+                for (int r = 0; r < RPL; ++r)
+                    if (fresh[r]) src[slot[r]] = static_cast<uint32_t>(lane) | (static_cast<uint32_t>(r) << 5);
+                __syncwarp();
+#pragma unroll
+                for (int t = 0; t < RPL; ++t) {
+                    if (static_cast<uint32_t>(kWarp * t) >= nn) break;           // warp-uniform
+                    const uint32_t j = lane + kWarp * t;
+                    const uint32_t sv = j < nn ? src[j] : 0u;
+                    const int sl = static_cast<int>(sv & 31u);
+                    const uint32_t sr = sv >> 5;
+                    uint4 c0 = make_uint4(0u, 0u, 0u, 0u), c1 = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int r = 0; r < RPL; ++r) {
+                        uint4 v0, v1;
+                        v0.x = __shfl_sync(0xFFFFFFFFu, ec[2 * r].x, sl);
+                        v0.y = __shfl_sync(0xFFFFFFFFu, ec[2 * r].y, sl);
+                        v0.z = __shfl_sync(0xFFFFFFFFu, ec[2 * r].z, sl);
+                        v0.w = __shfl_sync(0xFFFFFFFFu, ec[2 * r].w, sl);
+                        if (a.Mpad > 16u) {                                      // uniform
+                            v1.x = __shfl_sync(0xFFFFFFFFu, ec[2 * r + 1].x, sl);
+                            v1.y = __shfl_sync(0xFFFFFFFFu, ec[2 * r + 1].y, sl);
+                            v1.z = __shfl_sync(0xFFFFFFFFu, ec[2 * r + 1].z, sl);
+                            v1.w = __shfl_sync(0xFFFFFFFFu, ec[2 * r + 1].w, sl);
+                        } else {
+                            v1 = make_uint4(0u, 0u, 0u, 0u);
+                        }
+                        if (sr == static_cast<uint32_t>(r)) {
+                            c0 = v0;
+                            c1 = v1;
+                        }
+                    }
+                    if (j < nn) {
+                        const uint32_t id = Nid[j];
+                        kk[t] = make_key(pq_dist_bits_g<MODE>(tr, [c0, c1](uint32_t c16) { return c16 ? c1 : c0; },
+                                                              a.M, a.Mpad), id);
+                        kv[t] = true;
+                    }
                 }
             } else if (kPQ) {
                 in_regs = true;

@@ -628,11 +628,15 @@ def test_staged_rerank_k_beyond_registers(u8small, k, L):
     assert (g["ids"] == o["ids"]).all()
 
 
-@pytest.mark.parametrize("shape", ["i8_d100_M30", "f32_d96_M48", "f32_d200_M50", "u8_d130_M26"])
+@pytest.mark.parametrize("shape", ["i8_d100_M30", "f32_d96_M48", "f32_d200_M50", "u8_d130_M26",
+                                   "i8_d128_M32", "u8_d64_M16"])
 def test_staged_rerank_element_types_and_widths(shape):
     # int8 (biased lanes), FP32 (the 32-lane summation order), d > 128 (four
-    # chunks per lane) and rows that are not 4-byte aligned
-    spec = {"i8_d100_M30": dict(n=6_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40, centre="uniform100"),
+    # chunks per lane), rows that are not 4-byte aligned, and integer rows of
+    # 16-byte multiples (one lane per candidate row)
+    spec = {"i8_d128_M32": dict(n=6_000, nq=50, ncomp=4, dtype="i8", d=128, M=32, R=40, centre="uniform100"),
+            "u8_d64_M16": dict(n=6_000, nq=50, ncomp=4, dtype="u8", d=64, M=16, R=32, centre="uniform255"),
+            "i8_d100_M30": dict(n=6_000, nq=40, ncomp=4, dtype="i8", d=100, M=30, R=40, centre="uniform100"),
             "f32_d96_M48": dict(n=5_000, nq=40, ncomp=4, dtype="f32", d=96, M=48, R=68, centre="uniform255"),
             "f32_d200_M50": dict(n=4_000, nq=30, ncomp=4, dtype="f32", d=200, M=50, R=48, centre="uniform255"),
             "u8_d130_M26": dict(n=4_000, nq=30, ncomp=4, dtype="u8", d=130, M=26, R=32, centre="uniform255")}[shape]
