@@ -811,3 +811,20 @@ def test_partial_table_uneven_subspaces():
     ref = gpu_search(w, Q, 10, 48, trace_cap=300)
     for ntab in (7, 10, 29):
         _same(gpu_search(w, Q, 10, 48, trace_cap=300, table_source=3, table_subspaces=ntab), ref)
+
+
+@pytest.mark.parametrize("mode,flags", [(0, 0), (0, 3), (1, 3), (3, 3), (0, 3 | 4), (0, 16), (1, 6)])
+def test_speculated_row_with_early_code_rows(u8small, cfg1, mode, flags):
+    # prefetch depth 2 with early code rows: the first unvisited worklist
+    # entry's row is requested at the start of an iteration and, when it is
+    # chosen, its neighbours' code rows at once; visits and results unchanged
+    for w, Q, L in ((u8small, u8small["queries"][:150], 96), (cfg1, cfg1["queries"], 64)):
+        ref = gpu_search(w, Q, 10, L, trace_cap=600, mode=mode, placement=flags)
+        g = gpu_search(w, Q, 10, L, trace_cap=600, mode=mode, placement=flags, early_codes=1,
+                       prefetch_depth=2)
+        _same(g, ref)
+        g2 = gpu_search(w, Q, 10, L, trace_cap=600, mode=mode, placement=flags, early_codes=1,
+                        prefetch_depth=2, rerank=1)
+        _same(g2, ref)
+        o = oracle_search(w, Q, 10, L, trace_cap=600, q8=mode == 3, bf16=mode == 1)
+        assert (g["ids"] == o["ids"]).all() and (g["iters"] == o["iters"]).all()
