@@ -108,6 +108,8 @@ def lib():
         L.orc_search.argtypes = [ctypes.POINTER(OrcIndex), vp, i32, u32, u32, u32, u32, u32, vp,
                                  vp, vp, vp, vp, vp, u32, i32]
         L.orc_search.restype = i32
+        L.orc_search_rr.argtypes = L.orc_search.argtypes + [i32]
+        L.orc_search_rr.restype = i32
         L.orc_max_threads.restype = i32
         L.orc_bruteforce_knn.argtypes = [vp, vp, i32, u64, u32, u32, u32, vp, vp, i32]
         _lib = L
@@ -308,9 +310,11 @@ class Index:
                            self.base.ctypes.data)
 
     def search(self, queries, k, L, log2z=16, iter_cap=None, trace_cap=0, nthreads=0, exact=False,
-               q8=False, bf16=False):
+               q8=False, bf16=False, rerank_list=False):
         """Alg. 2 search; exact=True runs the Exact-distance variant (§5.2),
-        q8=True the search on the 8-bit table, bf16=True on the BF16 table."""
+        q8=True the search on the 8-bit table, bf16=True on the BF16 table;
+        rerank_list=True re-ranks the final worklist instead of the expanded
+        nodes (PQ modes)."""
         assert exact + q8 + bf16 <= 1
         mode = 1 if exact else (2 if q8 else (3 if bf16 else 0))
         q = np.ascontiguousarray(queries, dtype=self.base.dtype)
@@ -323,10 +327,10 @@ class Index:
         status = np.zeros(nq, np.int32)
         ndist = np.zeros(nq, np.uint64)
         trace = np.zeros((nq, trace_cap), np.uint32) if trace_cap else None
-        rc = lib().orc_search(ctypes.byref(self._s), _p(q), mode, nq, k, L, log2z,
-                              iter_cap, _p(ids),
-                              _p(dist), _p(iters), _p(status), _p(ndist), _p(trace), trace_cap,
-                              nthreads)
+        rc = lib().orc_search_rr(ctypes.byref(self._s), _p(q), mode, nq, k, L, log2z,
+                                 iter_cap, _p(ids),
+                                 _p(dist), _p(iters), _p(status), _p(ndist), _p(trace), trace_cap,
+                                 nthreads, 1 if rerank_list else 0)
         if rc != 0:
             raise ValueError("oracle search rejected its arguments")
         out = dict(ids=ids, dist=dist, iters=iters, status=status, ndist=ndist)

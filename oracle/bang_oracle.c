@@ -46,7 +46,8 @@
  *   orc_search               Alg. 1, Alg. 2, §4.3-§4.8; mode 1: the Exact-distance
  *                            variant of §5.2 (exact distances, no table, no re-rank);
  *                            mode 2: mode 0 with the 8-bit table; mode 3: with the
- *                            BF16 table
+ *                            BF16 table; orc_search_rr: the re-rank candidates
+ *                            are the expanded nodes (§4.8) or the final worklist
  *   orc_bruteforce_knn       §6.3 (ground truth S for k-recall@k)
  */
 #include <math.h>
@@ -820,7 +821,7 @@ static float search_dist(const orc_index *ix, int mode, const float *T, const ui
 static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k, uint32_t Lsz,
                        uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
                        uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
-                       uint32_t *trace, uint32_t trace_cap)
+                       uint32_t *trace, uint32_t trace_cap, int rerank_list)
 {
     uint32_t d = ix->d, M = ix->M, R = ix->R, i, r;
     float *qf = (float *)malloc(sizeof(float) * d);
@@ -886,6 +887,14 @@ static void search_one(const orc_index *ix, const void *q, int mode, uint32_t k,
     if (mode == 1) {                    /* Alg. 1: the k nearest entries of the worklist */
         nc = 0;
         for (i = 0; i < nl; i++) { C[nc].id = Lst[i].id; C[nc].dist = (double)Lst[i].dist; nc++; }
+    } else if (rerank_list) {           /* re-rank the final worklist only (reading c9's option) */
+        nc = 0;
+        for (i = 0; i < nl; i++) {
+            C[nc].id = Lst[i].id;
+            C[nc].dist = orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)Lst[i].id * d * esz,
+                                        ix->dtype, d);
+            nc++;
+        }
     }
     qsort(C, nc, sizeof(orc_dpair), dpair_cmp_stable);
     for (i = 0; i < k; i++) {
@@ -903,6 +912,15 @@ int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, 
                uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
                uint32_t *trace, uint32_t trace_cap, int nthreads)
 {
+    return orc_search_rr(ix, queries, mode, nq, k, L, log2z, iter_cap, out_ids, out_dist, out_iters,
+                         out_status, out_ndist, trace, trace_cap, nthreads, 0);
+}
+
+int orc_search_rr(const orc_index *ix, const void *queries, int mode, uint32_t nq, uint32_t k,
+                  uint32_t L, uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
+                  uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
+                  uint32_t *trace, uint32_t trace_cap, int nthreads, int rerank_list)
+{
     int64_t qi;
     size_t esz = ix->dtype == ORC_F32 ? 4 : 1;
     if (k == 0 || L < k || ix->M == 0 || ix->d == 0 || mode < 0 || mode > 3) return -1;
@@ -917,7 +935,7 @@ int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, 
                    iter_cap, out_ids + (uint64_t)qi * k, out_dist + (uint64_t)qi * k,
                    out_iters ? out_iters + qi : NULL, out_status ? out_status + qi : NULL,
                    out_ndist ? out_ndist + qi : NULL,
-                   trace ? trace + (uint64_t)qi * trace_cap : NULL, trace_cap);
+                   trace ? trace + (uint64_t)qi * trace_cap : NULL, trace_cap, rerank_list);
     }
     return 0;
 }
@@ -1171,7 +1189,7 @@ int orc_shard_graph(const void *X, int dtype, uint64_t n, uint32_t d, const floa
                 ix.d = d; ix.M = 1; ix.R = R; ix.medoid = entry[gg]; ix.n = nv; ix.dtype = dtype;
                 ix.adj = vadj; ix.base = vbase;
                 search_one(&ix, vbase + (uint64_t)p * d * esz, 1, 1, Lb, log2z, iter_cap, &k1, &d1,
-                           &nvis[bb], &st, &nd, V + (uint64_t)bb * iter_cap, iter_cap);
+                           &nvis[bb], &st, &nd, V + (uint64_t)bb * iter_cap, iter_cap, 0);
                 if (nvis[bb] > iter_cap) nvis[bb] = iter_cap;
             }
             /* RobustPrune of every member's visited set and current list */

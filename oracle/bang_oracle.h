@@ -73,6 +73,14 @@ int orc_search(const orc_index *ix, const void *queries, int mode, uint32_t nq, 
                uint32_t L, uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
                uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
                uint32_t *trace, uint32_t trace_cap, int nthreads);
+/* orc_search with the choice of re-rank candidates in the PQ modes: 0 = the
+ * expanded nodes (§4.8, as orc_search); 1 = the final worklist only (the
+ * exact re-rank of the top-L, including entries a capped search left
+ * unexpanded). */
+int orc_search_rr(const orc_index *ix, const void *queries, int mode, uint32_t nq, uint32_t k,
+                  uint32_t L, uint32_t log2z, uint32_t iter_cap, uint32_t *out_ids, float *out_dist,
+                  uint32_t *out_iters, int32_t *out_status, uint64_t *out_ndist,
+                  uint32_t *trace, uint32_t trace_cap, int nthreads, int rerank_list);
 int orc_max_threads(void);
 void orc_bruteforce_knn(const void *base, const void *queries, int dtype, uint64_t n,
                         uint32_t nq, uint32_t d, uint32_t k, uint32_t *ids, double *dists,

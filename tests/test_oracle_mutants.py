@@ -25,6 +25,11 @@ MUTANTS = [
     ("search_keeps_extra", "nl = (nl + nadd < Lsz) ? nl + nadd : Lsz;",
      "nl = (nl + nadd < Lsz + 1) ? nl + nadd : Lsz + 1;", 0),
     ("rerank_uses_pq", "C[nc].dist = orc_exact_dist(", "C[nc].dist = Lst[u].dist + 0 * orc_exact_dist(", 0),
+    ("rerank_list_uses_expanded", "} else if (rerank_list) {", "} else if (0 && rerank_list) {", 0),
+    ("rerank_list_uses_pq", "C[nc].dist = orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)Lst[i].id",
+     "C[nc].dist = Lst[i].dist + 0 * orc_exact_dist(q, (const unsigned char *)ix->base + (uint64_t)Lst[i].id", 0),
+    ("rerank_list_drops_last", "        for (i = 0; i < nl; i++) {\n            C[nc].id = Lst[i].id;",
+     "        for (i = 0; i + 1 < nl; i++) {\n            C[nc].id = Lst[i].id;", 0),
     ("medoid_no_mean", "for (j = 0; j < d; j++) mean[j] /= (double)n;", "", 0),
     ("kmeans_bad_mean", "sums[c * ds + j] / (double)cnt[c]", "sums[c * ds + j] / (double)(cnt[c] + 1)", 0),
     ("encode_ties_high", "if (acc < best) { best = acc; bc = c; }", "if (acc <= best) { best = acc; bc = c; }", 1),

@@ -583,6 +583,67 @@ def test_rerank_uses_exact_distances():
         assert all((ex[i], r["ids"][qi][i]) < (ex[i + 1], r["ids"][qi][i + 1]) for i in range(7))
 
 
+def test_rerank_of_the_final_worklist_hand_worked():
+    # Points 3i on a line, chain graph, query 87, L = 2, five expansions
+    # allowed.  By hand: expanding 0, 1, 2, 3, 4 moves the worklist to
+    # [5 (not expanded), 4], and the cap stops the search there.  Re-ranking
+    # the expanded nodes {0..4} gives 4, 3; re-ranking the final worklist
+    # {5, 4} gives 5 (72^2 = 5184), 4 (75^2 = 5625).
+    n = 30
+    X = np.arange(n, dtype=np.uint8)[:, None] * 3
+    adj = np.full((n, 2), NONE, np.uint32)
+    for i in range(n):
+        nb = [j for j in (i - 1, i + 1) if 0 <= j < n]
+        adj[i, :len(nb)] = nb
+    cb, codes = lossless_u8(X)
+    ix = oracle.Index(X, cb, codes, adj, 0, 1)
+    q = np.array([[87]], np.uint8)
+    r = ix.search(q, k=2, L=2, log2z=16, iter_cap=5, trace_cap=8)
+    assert r["trace"][0][:5].tolist() == [0, 1, 2, 3, 4] and r["status"][0] == 1
+    assert r["ids"][0].tolist() == [4, 3] and r["dist"][0].tolist() == [5625.0, 6084.0]
+    r = ix.search(q, k=2, L=2, log2z=16, iter_cap=5, rerank_list=True)
+    assert r["ids"][0].tolist() == [5, 4] and r["dist"][0].tolist() == [5184.0, 5625.0]
+
+
+def test_rerank_of_the_final_worklist_equals_the_exact_variant_on_lossless_codes():
+    # With lossless codes the PQ distance is the exact distance, so the PQ
+    # search and the Exact-distance variant (§5.2) visit the same nodes and
+    # end with the same worklist, whose first k entries that variant returns:
+    # re-ranking the final worklist must return exactly those, also when the
+    # cap leaves entries unexpanded
+    rng = np.random.default_rng(31)
+    n, d = 300, 6
+    X = rng.integers(0, 256, size=(n, d)).astype(np.uint8)
+    cb, codes = lossless_u8(X)
+    adj = np.stack([rng.choice(np.delete(np.arange(n), i), 8, replace=False)
+                    for i in range(n)]).astype(np.uint32)
+    ix = oracle.Index(X, cb, codes, adj, 0, d)
+    Q = rng.integers(0, 256, size=(12, d)).astype(np.uint8)
+    for cap in (None, 6):
+        lst = ix.search(Q, k=5, L=20, log2z=18, iter_cap=cap, rerank_list=True)
+        ex = ix.search(Q, k=5, L=20, log2z=18, iter_cap=cap, exact=True)
+        assert (lst["ids"] == ex["ids"]).all() and (lst["dist"] == ex["dist"]).all()
+        assert (lst["iters"] == ex["iters"]).all()
+
+
+def test_rerank_of_the_final_worklist_returns_exact_distances():
+    # lossy PQ: the final worklist is ordered by PQ distance, its re-rank by
+    # exact distance, which it also returns; with L >= n on a complete graph
+    # the final worklist holds every point, so the result is the brute force
+    rng = np.random.default_rng(32)
+    n, d, M = 60, 16, 4
+    X = rng.integers(0, 256, size=(n, d)).astype(np.uint8)
+    cb = rng.integers(0, 256, size=256 * d).astype(np.float32)
+    codes = oracle.pq_encode(X, M, cb)
+    ix = oracle.Index(X, cb, codes, complete_graph(n), 0, M)
+    Q = rng.integers(0, 256, size=(6, d)).astype(np.uint8)
+    r = ix.search(Q, k=10, L=n, log2z=18, rerank_list=True)
+    for qi in range(6):
+        ids, dd = brute_ids(X, Q[qi], 10)
+        assert r["ids"][qi].tolist() == ids.tolist()
+        assert r["dist"][qi].tolist() == dd.astype(np.float32).tolist()
+
+
 def test_rejects_L_below_k():
     X = np.zeros((4, 1), np.uint8)
     cb, codes = lossless_u8(X)
