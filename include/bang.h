@@ -126,8 +126,12 @@ typedef struct bang_search_params {
      * bytes per stream; iter_cap 0 counts as 8*L + 64), then a separate
      * kernel computes the candidates' exact distances and keeps the k
      * nearest.  Both return the k smallest (distance, id) keys of the same
-     * candidates in the same arithmetic: the results are identical.  Not
-     * accepted by bang_search_batched_noalloc.  Any other value: BANG_EINVAL. */
+     * candidates in the same arithmetic: the results are identical; 2 =
+     * staged over the final worklist only (its L entries, ordered by PQ
+     * distance, including entries a capped search left unexpanded): the
+     * reading of §4.8's candidates as the top-L, fewer candidates and so
+     * possibly lower recall than 0 and 1.  Not accepted by
+     * bang_search_batched_noalloc.  Any other value: BANG_EINVAL. */
     uint32_t rerank;
     /* Preferred share of each SM's unified L1/shared storage given to shared
      * memory, in percent (1..100; 0 = the driver's choice; above 100:

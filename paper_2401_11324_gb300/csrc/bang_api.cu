@@ -701,8 +701,8 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     if (p.trace && p.trace_cap == 0) return fail(BANG_EINVAL, "bang_search: trace_cap is 0");
 
     if (p.mode > 3) return fail(BANG_EINVAL, "bang_search: unknown mode %u", p.mode);
-    if (p.rerank > 1) return fail(BANG_EINVAL, "bang_search: unknown rerank %u", p.rerank);
-    if (p.rerank == 1 && p.mode == 2)
+    if (p.rerank > 2) return fail(BANG_EINVAL, "bang_search: unknown rerank %u", p.rerank);
+    if (p.rerank != 0 && p.mode == 2)
         return fail(BANG_EINVAL, "bang_search: mode 2 (exact distances) has no re-rank to stage");
     if (p.smem_carveout > 100) return fail(BANG_EINVAL, "bang_search: smem_carveout %u above 100", p.smem_carveout);
     if (p.table_source == 3 && p.mode != 0)
@@ -840,14 +840,16 @@ int search_impl(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, ui
     a.phase_cycles = static_cast<unsigned long long *>(dptr(7));
     a.carveout = p.smem_carveout;
     a.ntab = ntab;
-    if (p.rerank == 1) {       // staged re-rank: candidate lists sized by the iteration cap
-        const uint64_t cap = p.iter_cap ? p.iter_cap : 8ull * L + 64ull;
+    if (p.rerank != 0) {       // staged re-rank: lists sized by the iteration cap (or L)
+        uint64_t cap = p.iter_cap ? p.iter_cap : 8ull * L + 64ull;
+        if (cap < L) cap = L;
         const size_t lists = ((size_t)nq * cap * 4 + 255) & ~size_t(255);
         DevBuf &cb = ix->cands[st];
         CUDA_TRY(cb.ensure(lists + (size_t)nq * 4));
         a.cand = static_cast<uint32_t *>(cb.p);
         a.cand_cap = (uint32_t)cap;
         a.cand_n = reinterpret_cast<uint32_t *>(static_cast<char *>(cb.p) + lists);
+        a.cand_list = p.rerank == 2 ? 1u : 0u;
     }
 
     {

@@ -100,11 +100,13 @@ struct SearchArgs {
     // Staged re-rank (PQ modes): when `cand` is set the loop fetches no
     // vectors and keeps no top-k; it records every expanded node, the
     // candidate set of §4.8, in row q of `cand` (cand_cap >= the iteration
-    // cap, so no candidate is lost) and their number in cand_n[q], and
-    // rerank_kernel computes the exact distances and the top-k afterwards.
+    // cap, so no candidate is lost), or with cand_list the final worklist,
+    // and their number in cand_n[q]; the re-rank kernel computes the exact
+    // distances and the top-k afterwards.
     uint32_t *cand;
     uint32_t cand_cap;
     uint32_t *cand_n;
+    uint32_t cand_list;       // 1: the candidates are the final worklist instead (cand_cap >= L)
     uint32_t carveout;        // preferred shared-memory share of L1 in percent (0: the driver's choice)
     uint32_t ntab;            // kModeF32Lazy: subspaces (the first ones) whose entries stay in a table
 };
@@ -768,7 +770,7 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
                 Lk[first] = ukey | 1ull;
                 if (a.trace && iters < a.trace_cap)
                     a.trace[static_cast<uint64_t>(q) * a.trace_cap + iters] = u;
-                if (a.cand && iters < a.cand_cap)
+                if (a.cand && !a.cand_list && iters < a.cand_cap)
                     a.cand[static_cast<uint64_t>(q) * a.cand_cap + iters] = u;
             }
             ++iters;
@@ -1172,7 +1174,13 @@ __global__ void __launch_bounds__(32) search_kernel(const SearchArgs a)
         // k worklist entries (Alg. 1's result); padded.  With the staged
         // re-rank only the number of candidates.
         if (kPQ && a.cand) {
-            if (lane == 0) a.cand_n[q] = iters < a.cand_cap ? iters : a.cand_cap;
+            if (a.cand_list) {            // the final worklist (the top-L by PQ distance)
+                for (uint32_t i = lane; i < nl; i += kWarp)
+                    a.cand[static_cast<uint64_t>(q) * a.cand_cap + i] = key_id(Lk[i]);
+                if (lane == 0) a.cand_n[q] = nl;
+            } else if (lane == 0) {
+                a.cand_n[q] = iters < a.cand_cap ? iters : a.cand_cap;
+            }
         } else if (!kPQ) {
             for (uint32_t i = lane; i < kstride; i += kWarp) {
                 const uint64_t o = static_cast<uint64_t>(q) * kstride + i;

@@ -54,11 +54,11 @@ def gpu_search(w, Q, k, L, log2z=16, iter_cap=0, trace_cap=0, host=False, M=None
 
 
 def oracle_search(w, Q, k, L, log2z=16, iter_cap=None, trace_cap=0, M=None, exact=False, q8=False,
-                  bf16=False):
+                  bf16=False, rerank_list=False):
     M = M or w["M"]
     ix = oracle.Index(w["base"], w["codebook"], w["codes"], w["adj"], w["medoid"], M)
     return ix.search(Q, k, L, log2z=log2z, iter_cap=iter_cap, trace_cap=trace_cap, exact=exact,
-                     q8=q8, bf16=bf16)
+                     q8=q8, bf16=bf16, rerank_list=rerank_list)
 
 
 def assert_parity(g, o, trace_cap=0, exact_dist=True):
@@ -711,7 +711,8 @@ def test_staged_rerank_graph_capture_and_rejections(u8small):
         g.replay()
         torch.cuda.synchronize()
         assert (ids.cpu().numpy().view(np.uint32) == ref["ids"]).all()
-    for bad in (bang.make_params(rerank=2), bang.make_params(rerank=1, mode=bang.BANG_MODE_EXACT)):
+    for bad in (bang.make_params(rerank=3), bang.make_params(rerank=1, mode=bang.BANG_MODE_EXACT),
+                bang.make_params(rerank=2, mode=bang.BANG_MODE_EXACT)):
         with pytest.raises(bang.BangError):
             ix.search(q, 10, 64, ids, dist, bad)
     kd = torch.full((64,), 10, dtype=torch.int32, device="cuda")
@@ -828,3 +829,48 @@ def test_speculated_row_with_early_code_rows(u8small, cfg1, mode, flags):
         _same(g2, ref)
         o = oracle_search(w, Q, 10, L, trace_cap=600, q8=mode == 3, bf16=mode == 1)
         assert (g["ids"] == o["ids"]).all() and (g["iters"] == o["iters"]).all()
+
+
+# ---- staged re-rank of the final worklist only (rerank = 2)
+
+@pytest.mark.parametrize("mode", [0, 1, 3])
+@pytest.mark.parametrize("flags", [0, 3, 3 | 4, 16])
+def test_final_worklist_rerank_equals_oracle(u8small, cfg1, mode, flags):
+    for w, Q, L in ((u8small, u8small["queries"][:150], 64), (cfg1, cfg1["queries"], 48)):
+        g = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags, rerank=2)
+        o = oracle_search(w, Q, 10, L, trace_cap=400, q8=mode == 3, bf16=mode == 1, rerank_list=True)
+        assert_parity(g, o, trace_cap=400)
+        ref = gpu_search(w, Q, 10, L, trace_cap=400, mode=mode, placement=flags)
+        _same(g, ref, ("iters", "status", "ndist", "trace"))      # same search, other candidates
+
+
+@pytest.mark.parametrize("k,L,cap", [(1, 1, 0), (10, 64, 9), (32, 40, 0), (50, 100, 0), (100, 256, 30)])
+def test_final_worklist_rerank_k_and_cap(u8small, k, L, cap):
+    # registers and shared-memory top-k; a capped search re-ranks a worklist
+    # with unexpanded entries (the cap below L sizes the lists by L)
+    Q = u8small["queries"][:60]
+    g = gpu_search(u8small, Q, k, L, iter_cap=cap, rerank=2)
+    o = oracle_search(u8small, Q, k, L, iter_cap=cap or None, rerank_list=True)
+    assert_parity(g, o)
+
+
+def test_final_worklist_rerank_other_types_and_batched(u8small):
+    for spec in (dict(n=4_000, nq=30, ncomp=4, dtype="f32", d=96, M=48, R=68, centre="uniform255"),
+                 dict(n=4_000, nq=30, ncomp=4, dtype="i8", d=128, M=32, R=40, centre="uniform100")):
+        w = cases.clustered(**spec)
+        assert_parity(gpu_search(w, w["queries"], 10, 48, rerank=2),
+                      oracle_search(w, w["queries"], 10, 48, rerank_list=True))
+    Q = u8small["queries"][:120]
+    k, L = _mixed_kl(len(Q), 33)
+    ix = bang.Index(u8small["base"], u8small["codebook"], u8small["codes"], u8small["adj"],
+                    u8small["medoid"], u8small["M"])
+    kmax, Lmax = int(k.max()), int(L.max())
+    ids = np.zeros((len(Q), kmax), np.uint32)
+    dist = np.zeros((len(Q), kmax), np.float32)
+    ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist, bang.make_params(rerank=2))
+    ix.close()
+    for kk in np.unique(k):
+        for LL in np.unique(L[k == kk]):
+            sel = np.where((k == kk) & (L == LL))[0]
+            o = oracle_search(u8small, Q[sel], int(kk), int(LL), rerank_list=True)
+            assert (ids[sel, :kk] == o["ids"]).all()
