@@ -257,12 +257,13 @@ def measured_peaks():
         return {}
 
 
-def serving(bang, ix, w, L, mode, capacity_qps, log2z, seconds=2.0):
+def serving(bang, ix, w, L, mode, capacity_qps, log2z, seconds=2.0, early=0):
     """Continuous batching under Poisson arrivals of requests of 1..1024
     queries (uniform), k = 10, at fractions of the measured batch throughput:
     achieved queries/s and p50/p99 latency (submit to results on the host)."""
     import threading
-    srv = bang.Server(ix, K, L, max_batch=1024, streams=8, mode=mode, bloom_log2=log2z)
+    srv = bang.Server(ix, K, L, max_batch=1024, streams=8, mode=mode, bloom_log2=log2z,
+                      early_codes=early)
     rng = np.random.default_rng(7)
     nqall = w["queries"].shape[0]
     out = []
@@ -722,8 +723,8 @@ def run_large(args):
     serving_rec = serving_q8 = None
     bf = res["bf16_hbm"]
     if not args.no_serving:
-        serving_rec = serving(bang, ix, w, bf["L"], bf["mode"], bf["value"], bf["lz"])
-        serving_q8 = serving(bang, ix, w, q8["L"], q8["mode"], q8["value"], q8["lz"])
+        serving_rec = serving(bang, ix, w, bf["L"], bf["mode"], bf["value"], bf["lz"], early=bf["early"])
+        serving_q8 = serving(bang, ix, w, q8["L"], q8["mode"], q8["value"], q8["lz"], early=q8["early"])
 
     # rooflines: HBM binds the headline (graph, vectors and codes in HBM);
     # per expansion the row (R ids), the vector and one code row per new

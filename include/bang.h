@@ -505,6 +505,7 @@ typedef struct bang_server_config {
     uint64_t mem_bytes;      /* device bytes for batches in flight (0: room for `streams`
                                 full batches); a batch of nq queries takes about
                                 nq * (d * elem + 8 + 8 * k_max) bytes */
+    uint32_t early_codes;    /* as bang_search_params (0 or 1) */
 } bang_server_config;
 
 /* Start a server on the calling thread's current device for a fully loaded

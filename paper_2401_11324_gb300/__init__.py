@@ -58,7 +58,7 @@ class bang_server_config(ctypes.Structure):
     _fields_ = [("k_max", ctypes.c_uint32), ("L_max", ctypes.c_uint32),
                 ("max_batch", ctypes.c_uint32), ("streams", ctypes.c_uint32),
                 ("mode", ctypes.c_uint32), ("bloom_log2", ctypes.c_uint32),
-                ("mem_bytes", ctypes.c_uint64)]
+                ("mem_bytes", ctypes.c_uint64), ("early_codes", ctypes.c_uint32)]
 
 
 class bang_autotune_opts(ctypes.Structure):
@@ -377,10 +377,11 @@ class Server:
     request's ids, distances (nq x k_max) and latency in milliseconds."""
 
     def __init__(self, index, k_max, L_max, max_batch=1024, streams=8, mode=0, bloom_log2=0,
-                 mem_bytes=0):
+                 mem_bytes=0, early_codes=0):
         self.index = index
         self.k_max = k_max
-        cfg = bang_server_config(k_max, L_max, max_batch, streams, mode, bloom_log2, mem_bytes)
+        cfg = bang_server_config(k_max, L_max, max_batch, streams, mode, bloom_log2, mem_bytes,
+                                 early_codes)
         h = ctypes.c_void_p()
         _check(lib().bang_server_start(index.h, ctypes.byref(cfg), ctypes.byref(h)))
         self.h = h

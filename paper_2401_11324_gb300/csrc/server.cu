@@ -179,6 +179,7 @@ int start_launch(bang_server *s, Stream &st, Launch &ln)
     std::memset(&p, 0, sizeof p);
     p.mode = s->cfg.mode;
     p.bloom_log2 = s->cfg.bloom_log2;
+    p.early_codes = s->cfg.early_codes;
     int rc = bang_search_batched(s->ix, dv.q, nq, dv.k, dv.L, s->cfg.k_max, s->cfg.L_max, &p, dv.ids,
                                  dv.dist, st.stream);
     if (rc != BANG_OK) return rc;
@@ -324,6 +325,7 @@ int bang_server_start(bang_index *ix, const bang_server_config *cfg, bang_server
         std::memset(&p, 0, sizeof p);
         p.mode = cfg->mode;
         p.bloom_log2 = cfg->bloom_log2;
+        p.early_codes = cfg->early_codes;
         int rc = bang_search_batched(ix, dv.q, 1, dv.k, dv.L, cfg->k_max, cfg->L_max, &p, dv.ids, dv.dist,
                                      st.stream);
         if (rc != BANG_OK || cudaStreamSynchronize(st.stream) != cudaSuccess) {

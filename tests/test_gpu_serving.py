@@ -22,17 +22,21 @@ def index():
     ix.close()
 
 
-def _alone(ix, Q, k, L, kmax, Lmax):
+def _alone(ix, Q, k, L, kmax, Lmax, mode=0):
     ids = np.zeros((len(Q), kmax), np.uint32)
     dist = np.zeros((len(Q), kmax), np.float32)
-    ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist)
+    ix.search_batched(np.ascontiguousarray(Q), k, L, kmax, Lmax, ids, dist, bang.make_params(mode=mode))
     return ids, dist
 
 
-def test_each_result_same_alone_and_in_the_mix(index):
+@pytest.mark.parametrize("mode,early", [(0, 0), (0, 1), (1, 1)])
+def test_each_result_same_alone_and_in_the_mix(index, mode, early):
+    # FP32 and BF16 tables, code rows after the filter or early: the alone
+    # search is the allocating batched form with early code rows off, whose
+    # results early code rows do not change
     w, ix = index
     kmax, Lmax = 10, 128
-    srv = bang.Server(ix, kmax, Lmax, max_batch=96, streams=3)
+    srv = bang.Server(ix, kmax, Lmax, max_batch=96, streams=3, mode=mode, early_codes=early)
     rng = np.random.default_rng(11)
     reqs = []
     for _ in range(60):
@@ -55,7 +59,7 @@ def test_each_result_same_alone_and_in_the_mix(index):
     lat = []
     for i, (Q, k, L) in enumerate(reqs):
         ids, dist, ms = srv.wait(tickets[i], timeout_ms=60_000)
-        ids_a, dist_a = _alone(ix, Q, k, L, kmax, Lmax)
+        ids_a, dist_a = _alone(ix, Q, k, L, kmax, Lmax, mode)
         assert (ids == ids_a).all(), i
         fin = np.isfinite(dist_a)
         assert (dist[fin] == dist_a[fin]).all() and np.isinf(dist[~fin]).all()
