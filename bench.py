@@ -635,17 +635,21 @@ def run_large(args):
     t0 = time.perf_counter()
     try:
         tune = ix.autotune(q_dev, K, 0, truth=np.ascontiguousarray(w["gt_ids"][:, :K]),
-                           target_recall=TARGET_RECALL, bloom_min=14, bloom_max=17, stream=sptr)
+                           target_recall=TARGET_RECALL, bloom_min=14, bloom_max=17, try_structure=1,
+                           stream=sptr)
         tune["seconds"] = round(time.perf_counter() - t0, 2)
+        early[0], rerank[0], tsrc[0] = tune["early_codes"], tune["rerank"], tune["table_source"]
         search(tune["L"], tune["mode"], tune["bloom_log2"])
         stream.synchronize()
         tune_rec = rec_now()
         tv, tms, _ = timed(tune["L"], tune["mode"], tune["bloom_log2"], args.steps)
         tuned = dict(value=tv, ms_per_step=tms, L=tune["L"], mode=tune["mode"],
-                     bloom_log2=tune["bloom_log2"], recall=round(tune_rec, 4),
+                     bloom_log2=tune["bloom_log2"], table_source=tune["table_source"],
+                     early_codes=tune["early_codes"], rerank=tune["rerank"], recall=round(tune_rec, 4),
                      seconds=tune["seconds"], candidates=tune["candidates"])
     except bang.BangError as e:
         tuned = {"failed": str(e)}
+    early[0] = tsrc[0] = rerank[0] = 0
 
     # batched form: per-query k in {1, 10, 100} and L in {32, ..., 256} (at
     # least k), one persistent launch replayed from a CUDA graph

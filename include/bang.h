@@ -466,6 +466,8 @@ typedef struct bang_autotune_opts {
     uint32_t try_neighbor_codes; /* also try BANG_NEIGHBOR_CODES (where the index allows it) */
     uint32_t try_prefetch_depth; /* also time the winner with prefetch_depth 2 */
     uint32_t try_node_records;   /* also time the winner with BANG_NODE_RECORDS (host placement only) */
+    uint32_t try_structure;      /* also time the winner with early code rows, then with the
+                                    re-rank staged (rerank 1): both leave the results unchanged */
 } bang_autotune_opts;
 
 typedef struct bang_autotune_result {
@@ -478,6 +480,8 @@ typedef struct bang_autotune_result {
     uint32_t neighbor_codes;     /* 1: the choice uses the neighbour-code layout (set the flag) */
     uint32_t prefetch_depth;     /* 1 or 2 (bang_search_params.prefetch_depth) */
     uint32_t node_records;       /* 1: the choice reads node records (set BANG_NODE_RECORDS) */
+    uint32_t early_codes;        /* bang_search_params.early_codes of the choice */
+    uint32_t rerank;             /* bang_search_params.rerank of the choice (0 or 1) */
 } bang_autotune_result;
 
 int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, uint32_t k, uint32_t L,

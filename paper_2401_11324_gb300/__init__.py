@@ -68,7 +68,7 @@ class bang_autotune_opts(ctypes.Structure):
                 ("target_recall", ctypes.c_float), ("recall_tolerance", ctypes.c_float),
                 ("cache_path", ctypes.c_char_p), ("try_packed_graph", ctypes.c_uint32),
                 ("try_neighbor_codes", ctypes.c_uint32), ("try_prefetch_depth", ctypes.c_uint32),
-                ("try_node_records", ctypes.c_uint32)]
+                ("try_node_records", ctypes.c_uint32), ("try_structure", ctypes.c_uint32)]
 
 
 class bang_autotune_result(ctypes.Structure):
@@ -78,7 +78,8 @@ class bang_autotune_result(ctypes.Structure):
                 ("ref_ms", ctypes.c_float), ("ref_recall", ctypes.c_float),
                 ("candidates", ctypes.c_uint32), ("from_cache", ctypes.c_uint32),
                 ("graph_packed", ctypes.c_uint32), ("neighbor_codes", ctypes.c_uint32),
-                ("prefetch_depth", ctypes.c_uint32), ("node_records", ctypes.c_uint32)]
+                ("prefetch_depth", ctypes.c_uint32), ("node_records", ctypes.c_uint32),
+                ("early_codes", ctypes.c_uint32), ("rerank", ctypes.c_uint32)]
 
 
 def library_path():
@@ -233,13 +234,13 @@ def bang_pq_tables(ix, queries, nq, out, out_bf16=0, stream=None):
 def bang_autotune(ix, queries, nq, k, L, truth=None, modes=0, bloom_min=0, bloom_max=0,
                   try_tensor_tables=1, batched=0, reps=0, target_recall=0.0, recall_tolerance=0.0,
                   cache_path=None, try_packed_graph=0, try_neighbor_codes=0, try_prefetch_depth=0,
-                  try_node_records=0, stream=None):
+                  try_node_records=0, try_structure=0, stream=None):
     """Returns the chosen settings as a dict (fields of bang_autotune_result)."""
     s = ctypes.c_void_p(stream) if isinstance(stream, int) else stream
     o = bang_autotune_opts(modes, bloom_min, bloom_max, try_tensor_tables, batched, reps,
                            target_recall, recall_tolerance,
                            cache_path.encode() if cache_path else None, try_packed_graph,
-                           try_neighbor_codes, try_prefetch_depth, try_node_records)
+                           try_neighbor_codes, try_prefetch_depth, try_node_records, try_structure)
     t = None if truth is None else np.ascontiguousarray(truth, np.uint32)
     r = bang_autotune_result()
     _check(lib().bang_autotune(ix, _ptr(queries), nq, k, L, _ptr(t), ctypes.byref(o),

@@ -3,8 +3,8 @@
 // precision and where it is built (§4.1: FP32, BF16 or 8-bit; per warp or on
 // the tensor cores for the whole batch), the Bloom filter's size (§4.3, the
 // paper's z), the persistent grid of the batched form, whether the graph rows
-// are read packed, and optionally the worklist size L that reaches a target
-// recall.  Candidates are timed with
+// are read packed, early code rows and the staged re-rank, and optionally
+// the worklist size L that reaches a target recall.  Candidates are timed with
 // CUDA events on the caller's stream and judged by recall@k against the
 // caller's ground truth or, without one, against a high-accuracy FP32 search
 // (2L, Bloom 2^18).  Decisions can be cached as JSON lines keyed by the GPU
@@ -29,6 +29,7 @@ namespace {
 struct Cfg {
     uint32_t mode, log2z, tsrc, grid_mult, L, layout;    // layout: BANG_GRAPH_PACKED | BANG_NEIGHBOR_CODES bits
     uint32_t depth = 1;                                   // prefetch depth
+    uint32_t early = 0, rerank = 0;                       // early code rows, staged re-rank
 };
 
 struct Runner {
@@ -80,6 +81,8 @@ struct Runner {
         p.table_source = c.tsrc;
         p.grid_mult = c.grid_mult;
         p.prefetch_depth = c.depth;
+        p.early_codes = c.early;
+        p.rerank = c.rerank;
         if (!batched) return bang_search(ix, queries, nq, k, c.L, &p, d_ids, d_dist, st);
         std::vector<uint32_t> Lq(nq, c.L);
         if (cudaMemcpyAsync(d_Lq, Lq.data(), sizeof(uint32_t) * nq, cudaMemcpyHostToDevice, st) != cudaSuccess ||
@@ -154,7 +157,7 @@ std::string cache_key(bang_index *ix, uint32_t nq, uint32_t k, uint32_t L, const
       << o.bloom_max << "|tc=" << o.try_tensor_tables << "|batched=" << o.batched
       << "|packed=" << o.try_packed_graph << "|ncodes=" << o.try_neighbor_codes
       << "|depth=" << o.try_prefetch_depth << "|records=" << o.try_node_records
-      << "|truth=" << (truth ? 1 : 0);
+      << "|structure=" << o.try_structure << "|truth=" << (truth ? 1 : 0);
     std::string r = s.str();
     for (char &c : r)
         if (c == '"' || c == '\\' || c == '\n') c = '_';
@@ -180,11 +183,11 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     while (std::getline(f, line))
         if (line.compare(0, kpat.size(), kpat) == 0) hit = line;    // the last entry wins
     if (hit.empty()) return false;
-    double v[14];
-    const char *names[14] = {"mode", "bloom_log2", "table_source", "grid_mult", "L", "ms", "recall",
+    double v[16];
+    const char *names[16] = {"mode", "bloom_log2", "table_source", "grid_mult", "L", "ms", "recall",
                              "ref_ms", "ref_recall", "candidates", "graph_packed", "neighbor_codes",
-                             "prefetch_depth", "node_records"};
-    for (int i = 0; i < 14; ++i)
+                             "prefetch_depth", "node_records", "early_codes", "rerank"};
+    for (int i = 0; i < 16; ++i)
         if (!field(hit, names[i], &v[i])) return false;
     out->mode = static_cast<uint32_t>(v[0]);
     out->bloom_log2 = static_cast<uint32_t>(v[1]);
@@ -200,6 +203,8 @@ bool lookup(const char *path, const std::string &key, bang_autotune_result *out)
     out->neighbor_codes = static_cast<uint32_t>(v[11]);
     out->prefetch_depth = static_cast<uint32_t>(v[12]);
     out->node_records = static_cast<uint32_t>(v[13]);
+    out->early_codes = static_cast<uint32_t>(v[14]);
+    out->rerank = static_cast<uint32_t>(v[15]);
     out->from_cache = 1;
     return true;
 }
@@ -214,10 +219,10 @@ void store(const char *path, const std::string &key, const bang_autotune_result 
                   "\"mode\": %u, \"bloom_log2\": %u, \"table_source\": %u, \"grid_mult\": %u, "
                   "\"L\": %u, \"ms\": %.6g, \"recall\": %.6g, \"ref_ms\": %.6g, \"ref_recall\": %.6g, "
                   "\"candidates\": %u, \"graph_packed\": %u, \"neighbor_codes\": %u, "
-                  "\"prefetch_depth\": %u, \"node_records\": %u}",
+                  "\"prefetch_depth\": %u, \"node_records\": %u, \"early_codes\": %u, \"rerank\": %u}",
                   r.mode, r.bloom_log2, r.table_source, r.grid_mult, r.L, r.ms, r.recall, r.ref_ms,
                   r.ref_recall, r.candidates, r.graph_packed, r.neighbor_codes, r.prefetch_depth,
-                  r.node_records);
+                  r.node_records, r.early_codes, r.rerank);
     f << "{\"key\": \"" << key << "\", " << buf << "\n";
 }
 
@@ -412,6 +417,30 @@ extern "C" int bang_autotune(bang_index *ix, const void *queries, uint32_t nq, u
         if (ms2 < out->ms) {
             out->ms = ms2;
             out->prefetch_depth = 2;
+            best_c = c2;
+        }
+    }
+    if (o.try_structure && best_c.mode != BANG_MODE_EXACT) {
+        // the winner with early code rows, then with the re-rank staged
+        // (same results: each kept only if faster)
+        Cfg c3 = best_c;
+        c3.early = 1;
+        float ms3 = 0.f;
+        if ((rc = run.time(c3, o.reps, &ms3))) return rc;
+        ++out->candidates;
+        if (ms3 < out->ms) {
+            out->ms = ms3;
+            out->early_codes = 1;
+            best_c = c3;
+        }
+        Cfg c4 = best_c;
+        c4.rerank = 1;
+        float ms4 = 0.f;
+        if ((rc = run.time(c4, o.reps, &ms4))) return rc;
+        ++out->candidates;
+        if (ms4 < out->ms) {
+            out->ms = ms4;
+            out->rerank = 1;
         }
     }
     if (o.cache_path) store(o.cache_path, key, *out);

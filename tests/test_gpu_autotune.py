@@ -109,3 +109,26 @@ def test_rejects_bad_options(setup):
             ix.autotune(q, 10, 64, **kw)
     with pytest.raises(bang.BangError):
         ix.autotune(q, 10, 5)                    # L < k without a target recall
+
+
+def test_structure_timed_on_the_winner(setup, tmp_path):
+    # early code rows and the staged re-rank are timed on the winner; each
+    # leaves the results unchanged, so the chosen settings reproduce the
+    # reported recall with them set, and the cache returns them
+    w, ix, q = setup
+    truth = np.ascontiguousarray(w["gt_ids"][:, :10])
+    path = str(tmp_path / "tune.jsonl")
+    r = ix.autotune(q, 10, 64, truth=truth, bloom_min=15, bloom_max=16, try_structure=1, cache_path=path)
+    assert r["early_codes"] in (0, 1) and r["rerank"] in (0, 1)
+    assert r["candidates"] >= 8
+    ids = torch.empty((q.shape[0], 10), dtype=torch.int32, device="cuda")
+    dist = torch.empty((q.shape[0], 10), dtype=torch.float32, device="cuda")
+    p = bang.make_params(bloom_log2=r["bloom_log2"], mode=r["mode"], table_source=r["table_source"],
+                         early_codes=r["early_codes"], rerank=r["rerank"])
+    ix.search(q, 10, r["L"], ids, dist, p)
+    torch.cuda.synchronize()
+    assert abs(oracle.recall_at_k(ids.cpu().numpy().view(np.uint32), w["gt_ids"], 10) - r["recall"]) < 1e-6
+    r2 = ix.autotune(q, 10, 64, truth=truth, bloom_min=15, bloom_max=16, try_structure=1, cache_path=path)
+    assert r2["from_cache"] == 1
+    for f in ("mode", "bloom_log2", "L", "early_codes", "rerank"):
+        assert r2[f] == r[f], f
