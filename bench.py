@@ -822,11 +822,11 @@ def run_large(args):
         "batched_form": batched,
         "roofline": {"bound": "hbm", "achieved": hbm_gbs, "peak": hbm_peak, "unit": "GB/s",
                      "frac": hbm_gbs / hbm_peak, "traffic": None,
-                     "traffic_note": "not captured at this size (83 GB in HBM); the same kernel "
-                                     "at 8M points and L = 224 (before the compaction of new "
-                                     "neighbours across lanes) read 2.305 GB of DRAM per launch "
-                                     "for 1.543 GB algorithmic (1.49x: each 32-byte code row "
-                                     "costs a 64-byte DRAM access)",
+                     "traffic_note": "not captured at this size (83 GB in HBM); at 8M points "
+                                     "and L = 224 the staged headline's search read 1.917 GB and "
+                                     "its re-rank 0.303 GB of DRAM per step for 1.543 GB "
+                                     "algorithmic (1.44x: each 32-byte code row costs a 64-byte "
+                                     "DRAM access); the fused form's search read 2.305 GB",
                      "peak_source": "measured (MEASURED_PEAKS.json)" if "hbm_gbs" in peaks
                                     else "fallback",
                      "algorithmic_bytes_per_launch": hbm_bytes,
