@@ -403,14 +403,16 @@ def large_workload(args, device):
                     avail = int(line.split()[1]) * 1024
         n_req = int(min(workload.CONFIGS[args.config]["n"], 0.7 * avail / (world * 420)))
         n_req -= n_req % 1_000_000
-    w = workload.large_data(args.config, n=n_req, nq=args.nq, ncomp=args.ncomp, verbose=True)
+    # graph and vectors in host memory advised for huge pages (bang_host_alloc)
+    w = workload.large_data(args.config, n=n_req, nq=args.nq, ncomp=args.ncomp, verbose=True,
+                            alloc=bang.host_empty)
     c = w["params"]
     n = w["base"].shape[0]
     t0 = time.perf_counter()
     cb, codes = bang.bang_build_pq(w["base"], c["M"], w["pq_sample"],
                                    w["pq_init"].reshape(c["M"], 256), 10, device=device)
     t1 = time.perf_counter()
-    adj = workload.aligned_empty((n, c["R"]), np.uint32)          # read in place later
+    adj = bang.host_empty((n, c["R"]), np.uint32)                 # read in place later
     bang.bang_build_shard_graph(w["base"], w["shard_centres"], c["ell"], c["R"], c["Lb"], c["alpha"],
                                 c["batch_frac"], c["bloom_build"], adj=adj, device=device)
     t2 = time.perf_counter()

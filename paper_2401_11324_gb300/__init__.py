@@ -123,6 +123,10 @@ def _load():
                                 ctypes.POINTER(bang_autotune_result), vp]
     L.bang_probe_host_link.argtypes = [i32, u64, u32, ctypes.POINTER(bang_link_probe)]
     L.bang_probe_host_link.restype = i32
+    L.bang_host_alloc.argtypes = [u64, ctypes.POINTER(ctypes.c_void_p)]
+    L.bang_host_alloc.restype = i32
+    L.bang_host_free.argtypes = [vp]
+    L.bang_host_free.restype = i32
     L.bang_last_error.restype = ctypes.c_char_p
     for f in ("bang_create", "bang_load_pq", "bang_register_graph", "bang_register_vectors",
               "bang_search", "bang_destroy", "bang_set_placement", "bang_search_batched",
@@ -224,6 +228,22 @@ def bang_search_batched_noalloc(ix, queries, nq, k_per_q, L_per_q, k_max, L_max,
     return _check(lib().bang_search_batched_noalloc(ix, _ptr(queries), nq, _ptr(k_per_q),
                                                     _ptr(L_per_q), k_max, L_max, p, _ptr(out_ids),
                                                     _ptr(out_dist), s))
+
+
+def host_empty(shape, dtype):
+    """A numpy array in memory from bang_host_alloc (advised for transparent
+    huge pages, zero-filled), for the graph and vectors an index reads in
+    place from host memory; the memory is unmapped when the array and every
+    view of it are gone (destroy indexes that registered it first)."""
+    import weakref
+    dtype = np.dtype(dtype)
+    nbytes = max(1, int(np.prod(shape)) * dtype.itemsize)
+    ptr = ctypes.c_void_p()
+    _check(lib().bang_host_alloc(nbytes, ctypes.byref(ptr)))
+    holder = (ctypes.c_uint8 * nbytes).from_address(ptr.value)
+    fin = weakref.finalize(holder, lib().bang_host_free, ctypes.c_void_p(ptr.value))
+    fin.atexit = False                 # at exit the process's mappings go anyway
+    return np.frombuffer(holder, np.uint8)[:int(np.prod(shape)) * dtype.itemsize].view(dtype).reshape(shape)
 
 
 def bang_pq_tables(ix, queries, nq, out, out_bf16=0, stream=None):

@@ -4,6 +4,7 @@
 // host-resident graph and vectors (read in place by the kernel, Alg. 2's
 // FetchNeighbors), staging of host queries and results, and the launch.
 #include <cuda_runtime.h>
+#include <sys/mman.h>
 
 #include <algorithm>
 #include <atomic>
@@ -1024,6 +1025,64 @@ int bang_set_placement(bang_index *ix, uint32_t flags)
         ix->records.release();
     }
     ix->placement = flags;
+    return BANG_OK;
+}
+
+namespace {
+struct HostBlock {
+    void *raw;
+    size_t bytes;
+};
+std::mutex g_host_mu;
+std::map<void *, HostBlock> g_host_blocks;     // aligned address -> the whole mapping
+
+// The transparent-huge-page size (2 MB on 4 KB-page systems, 512 MB on
+// 64 KB-page arm64), or 2 MB when the system does not say.
+size_t thp_size()
+{
+    size_t sz = 2u << 20;
+    if (FILE *f = std::fopen("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size", "r")) {
+        unsigned long long v = 0;
+        if (std::fscanf(f, "%llu", &v) == 1 && v >= 4096 && (v & (v - 1)) == 0) sz = static_cast<size_t>(v);
+        std::fclose(f);
+    }
+    return sz;
+}
+}  // namespace
+
+int bang_host_alloc(uint64_t bytes, void **out)
+{
+    if (!out || bytes == 0) return fail(BANG_EINVAL, "bang_host_alloc: NULL output or zero bytes");
+    *out = nullptr;
+    const size_t align = thp_size();
+    const size_t total = static_cast<size_t>(bytes) + align;
+    void *raw = mmap(nullptr, total, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+    if (raw == MAP_FAILED) return fail(BANG_ENOMEM, "bang_host_alloc: mmap of %zu bytes failed", total);
+    const uintptr_t a = (reinterpret_cast<uintptr_t>(raw) + align - 1) & ~static_cast<uintptr_t>(align - 1);
+    void *p = reinterpret_cast<void *>(a);
+#ifdef MADV_HUGEPAGE
+    madvise(p, static_cast<size_t>(bytes), MADV_HUGEPAGE);     // a hint: refused means 4 KB pages
+#endif
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        g_host_blocks[p] = HostBlock{raw, total};
+    }
+    *out = p;
+    return BANG_OK;
+}
+
+int bang_host_free(void *p)
+{
+    if (!p) return BANG_OK;
+    HostBlock b;
+    {
+        std::lock_guard<std::mutex> lk(g_host_mu);
+        auto it = g_host_blocks.find(p);
+        if (it == g_host_blocks.end()) return fail(BANG_EINVAL, "bang_host_free: not from bang_host_alloc");
+        b = it->second;
+        g_host_blocks.erase(it);
+    }
+    munmap(b.raw, b.bytes);
     return BANG_OK;
 }
 

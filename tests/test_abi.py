@@ -89,3 +89,27 @@ def test_binding_structs_follow_the_header(struct):
             assert ctype in (ctypes.c_void_p, ctypes.c_char_p) or hasattr(ctype, "contents"), name
         else:
             assert ctype not in (ctypes.c_void_p,), name
+
+
+def test_host_alloc_aligned_zeroed_and_freed(lib):
+    # bang_host_alloc needs no GPU: an anonymous mapping aligned to the
+    # transparent-huge-page size, zero-filled; freed once, refused twice
+    import numpy as np
+    thp = 2 << 20
+    try:
+        thp = int(open("/sys/kernel/mm/transparent_hugepage/hpage_pmd_size").read())
+    except (OSError, ValueError):
+        pass
+    p = ctypes.c_void_p()
+    assert lib.bang_host_alloc(5 << 20, ctypes.byref(p)) == bang.BANG_OK
+    assert p.value % thp == 0
+    view = np.ctypeslib.as_array((ctypes.c_uint8 * (5 << 20)).from_address(p.value))
+    assert not view.any()
+    view[:] = 3
+    del view
+    assert lib.bang_host_free(p) == bang.BANG_OK
+    assert lib.bang_host_free(p) == bang.BANG_EINVAL
+    assert lib.bang_host_free(None) == bang.BANG_OK
+    assert lib.bang_host_alloc(0, ctypes.byref(p)) == bang.BANG_EINVAL
+    a = bang.host_empty((300, 7), np.float32)
+    assert a.shape == (300, 7) and a.dtype == np.float32 and not a.any()

@@ -369,13 +369,14 @@ def clustered_data(cfg=2, n=None, nq=None, ncomp=None, k=100, train_n=256_000, v
     return out
 
 
-def large_data(cfg, n=None, nq=None, ncomp=None, train_n=256_000, verbose=False, **over):
+def large_data(cfg, n=None, nq=None, ncomp=None, train_n=256_000, verbose=False, alloc=None, **over):
     """Data of a large configuration (4 or 5) from the counter-based generator
     (wl_mixture: same bytes for any thread count and on x86 and Arm hosts),
     with the inputs of its index build: the PQ training sample and initial
     centroids, the shard centres (seeded data points) and the global medoid.
     The index itself (PQ codes, overlapping-shard graph) and the ground truth
-    are built by the caller (on the GPU)."""
+    are built by the caller (on the GPU).  `alloc(shape, dtype)` allocates the
+    base vectors (default: page-aligned numpy memory)."""
     c = dict(CONFIGS[cfg])
     c.update(over)
     n = n or c["n"]
@@ -388,7 +389,7 @@ def large_data(cfg, n=None, nq=None, ncomp=None, train_n=256_000, verbose=False,
     fac = rng.standard_normal((ncomp, c["d"], c["rank"]), dtype=np.float32) * np.float32(
         c["sigma"] / np.sqrt(c["rank"]))
     fac = np.ascontiguousarray(fac.transpose(0, 2, 1))         # rank-major per component
-    base = aligned_empty((n, c["d"]), _DTN[c["dtype"]])
+    base = (alloc or aligned_empty)((n, c["d"]), _DTN[c["dtype"]])
     queries = aligned_empty((nq, c["d"]), _DTN[c["dtype"]])
     for arr, rows, seed in ((base, n, 1000 + cfg), (queries, nq, 2000 + cfg)):
         rc = lib().wl_mixture(_p(arr), _DTC[c["dtype"]], rows, c["d"], _p(cen), ncomp, _p(fac),
