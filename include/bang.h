@@ -134,7 +134,7 @@ typedef struct bang_search_params {
      * bang_search_batched_noalloc.  Any other value: BANG_EINVAL. */
     uint32_t rerank;
     /* Preferred share of each SM's unified L1/shared storage given to shared
-     * memory, in percent (1..100; 0 = the driver's choice; above 100:
+     * memory, in percent (1..100; 0 = the CUDA driver's choice; above 100:
      * BANG_EINVAL).  A hint that trades resident queries against L1 capacity
      * (the codebook, for table_source 3); results do not depend on it. */
     uint32_t smem_carveout;

@@ -107,7 +107,7 @@ struct SearchArgs {
     uint32_t cand_cap;
     uint32_t *cand_n;
     uint32_t cand_list;       // 1: the candidates are the final worklist instead (cand_cap >= L)
-    uint32_t carveout;        // preferred shared-memory share of L1 in percent (0: the driver's choice)
+    uint32_t carveout;        // preferred shared-memory share of L1 in percent (0: the CUDA driver's choice)
     uint32_t ntab;            // kModeF32Lazy: subspaces (the first ones) whose entries stay in a table
 };
 
@@ -1246,7 +1246,7 @@ cudaError_t launch_one(const SearchArgs &a, size_t smem, cudaStream_t st)
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     if (e != cudaSuccess) return e;
     // the carve-out is a hint that stays with the function: set it when the
-    // request changes (back to the driver's choice, -1, when it is 0)
+    // request changes (back to the CUDA driver's choice, -1, when it is 0)
     static std::atomic<uint32_t> carveout_set{0};
     if (carveout_set.load() != a.carveout) {
         e = cudaFuncSetAttribute(search_kernel<DT, RPL, DCH, MODE, CS, PH>,
