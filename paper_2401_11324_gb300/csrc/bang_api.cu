@@ -57,6 +57,31 @@ int fail(int code, const char *fmt, ...)
 // the host link as 8 sectors instead of 9.
 constexpr uintptr_t kHostAlign = 128;
 
+// Page-locked, mapped host memory for the library's own host copies (an
+// aligned copy of a caller's array, packed rows, node records): a mapping
+// advised for transparent huge pages (bang_host_alloc) registered with CUDA,
+// so that the GPU's reads of it need few address translations.
+cudaError_t huge_host_alloc(size_t bytes, void **out)
+{
+    void *p = nullptr;
+    *out = nullptr;
+    if (bang_host_alloc(bytes, &p) != BANG_OK) return cudaErrorMemoryAllocation;
+    cudaError_t e = cudaHostRegister(p, bytes, cudaHostRegisterMapped);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        bang_host_free(p);
+        return e;
+    }
+    *out = p;
+    return cudaSuccess;
+}
+
+void huge_host_free(void *p)
+{
+    cudaHostUnregister(p);
+    bang_host_free(p);
+}
+
 struct HostView {
     const void *host = nullptr;
     const void *dev = nullptr;
@@ -65,7 +90,7 @@ struct HostView {
 
     void release()
     {
-        if (copied && host) cudaFreeHost(const_cast<void *>(host));
+        if (copied && host) huge_host_free(const_cast<void *>(host));
         else if (registered_here && host) cudaHostUnregister(const_cast<void *>(host));
         host = dev = nullptr;
         registered_here = copied = false;
@@ -115,7 +140,7 @@ int map_host(const void *p, size_t bytes, int device, HostView &out)
     }
     if (reinterpret_cast<uintptr_t>(p) % kHostAlign != 0) {
         void *c = nullptr;
-        e = cudaHostAlloc(&c, bytes, cudaHostAllocMapped);
+        e = huge_host_alloc(bytes, &c);
         if (e != cudaSuccess) {
             cudaGetLastError();
             return fail(e == cudaErrorMemoryAllocation ? BANG_ENOMEM : BANG_ECUDA,
@@ -126,7 +151,7 @@ int map_host(const void *p, size_t bytes, int device, HostView &out)
         e = cudaHostGetDevicePointer(&dp, c, 0);
         if (e != cudaSuccess) {
             cudaGetLastError();
-            cudaFreeHost(c);
+            huge_host_free(c);
             return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
         }
         out.host = c;
@@ -405,7 +430,7 @@ int build_packed_rows(bang_index *ix)
     const uint32_t words = ((ix->R * b + 31u) / 32u + 7u) & ~7u;
     const size_t bytes = (size_t)ix->n * words * 4u;
     void *h = nullptr;
-    cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+    cudaError_t e = huge_host_alloc(bytes, &h);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(BANG_ENOMEM, "packed graph rows: %zu bytes of page-locked memory: %s", bytes,
@@ -435,7 +460,7 @@ int build_packed_rows(bang_index *ix)
     e = cudaHostGetDevicePointer(&dp, h, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeHost(h);
+        huge_host_free(h);
         return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
     }
     ix->adj_packed.host = h;
@@ -481,7 +506,7 @@ int build_records(bang_index *ix, bool packed)
     const uint32_t words = (uint32_t)((((size_t)rw * 4u + vb + 31u) / 32u) * 8u);
     const size_t bytes = (size_t)ix->n * words * 4u;
     void *h = nullptr;
-    cudaError_t e = cudaHostAlloc(&h, bytes, cudaHostAllocMapped);
+    cudaError_t e = huge_host_alloc(bytes, &h);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return fail(BANG_ENOMEM, "node records: %zu bytes of page-locked memory: %s", bytes,
@@ -507,7 +532,7 @@ int build_records(bang_index *ix, bool packed)
     e = cudaHostGetDevicePointer(&dp, h, 0);
     if (e != cudaSuccess) {
         cudaGetLastError();
-        cudaFreeHost(h);
+        huge_host_free(h);
         return fail(BANG_ECUDA, "cudaHostGetDevicePointer failed: %s", cudaGetErrorString(e));
     }
     ix->records.host = h;
