@@ -2,10 +2,12 @@
 //
 // One warp (a 32-thread CTA) runs the whole search of one query: the PQ
 // distance table (§4.1), the Bloom-filter seen set (§4.3), the worklist and
-// the re-rank candidates all live in shared memory, so the only global
-// traffic per iteration is the neighbour row and full vector of the expanded
-// node (read in place from page-locked host memory, Alg. 2 "FetchNeighbors")
-// and one PQ code row per new neighbour (HBM, §4.4).
+// the re-rank's running top-k all live in shared memory or registers, so the
+// only global traffic per iteration is the neighbour row and full vector of
+// the expanded node (read in place from page-locked host memory, Alg. 2
+// "FetchNeighbors", or from HBM) and one PQ code row per new neighbour (HBM,
+// §4.4).  With the staged re-rank the loop records the expanded nodes
+// instead and fetches no vectors; rerank.cu ranks them afterwards (§4.8).
 //
 // The paper splits every iteration into separate kernels with one CTA per
 // query and keeps the table and filter in global memory; here the iteration
