@@ -83,3 +83,15 @@ def test_mixed_cluster_links_of_configuration_4():
     # deterministic: the same inputs twice
     gi2 = workload.graph_inputs(4, w["base"], w["labels"], ng, nx, nh)
     assert (gi2["xclu"] == gi["xclu"]).all() and (gi2["hclu"] == gi["hclu"]).all()
+
+
+def test_large_data_same_bytes_in_huge_page_memory():
+    # the benchmark allocates configuration 5's base vectors with
+    # bang_host_alloc (no GPU needed); the generated bytes do not depend on
+    # where they are written
+    import paper_2401_11324_gb300 as bang
+    a = workload.large_data(5, n=20_000, nq=50, ncomp=64)
+    b = workload.large_data(5, n=20_000, nq=50, ncomp=64, alloc=bang.host_empty)
+    assert (a["base"] == b["base"]).all() and (a["queries"] == b["queries"]).all()
+    assert b["base"].ctypes.data % (2 << 20) == 0
+    assert a["medoid"] == b["medoid"]
